@@ -1,0 +1,135 @@
+"""Pins of the oracle's whole-image pipeline (cap and canonical order) and of
+its stereo matcher (Sec. III middle-end) by brute force and known-disparity
+scenes."""
+import numpy as np
+import pytest
+
+from paper_2410_04090_gb300 import scenes
+
+
+def _params(oracle, **kw):
+    p = oracle.FrontendParams()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_canonical_order_and_borders(oracle):
+    img = scenes.random_image(200, 260, seed=4)
+    p = _params(oracle, levels=4, max_feats=10000)
+    kp = oracle.extract_image(img, p)
+    n = kp["count"]
+    assert n > 50
+    key = kp["level"].astype(np.int64) << 32 | kp["y"].astype(np.int64) << 16 | kp["x"].astype(np.int64)
+    assert np.all(np.diff(key) > 0)
+    W, H, _ = oracle.level_geometry(260, 200, 4, 1.2, 32)
+    for i in range(n):
+        l = kp["level"][i]
+        assert 19 <= kp["x"][i] < W[l] - 19 and 19 <= kp["y"][i] < H[l] - 19
+        assert kp["X"][i] == oracle.project(int(kp["x"][i]), int(l), 1.2, 260)
+        assert kp["Y"][i] == oracle.project(int(kp["y"][i]), int(l), 1.2, 200)
+
+
+def test_cap_keeps_highest_priority(oracle):
+    img = scenes.random_image(240, 320, seed=9)
+    full = oracle.extract_image(img, _params(oracle, levels=5, max_feats=100000))
+    n = full["count"]
+    for cap in (1, 17, n // 2, n - 1):
+        capped = oracle.extract_image(img, _params(oracle, levels=5, max_feats=cap))
+        order = sorted(range(n), key=lambda i: (-int(full["k_levels"][i]), -int(full["k_resp"][i]),
+                                               -int(full["response"][i]), int(full["level"][i]),
+                                               int(full["y"][i]), int(full["x"][i])))
+        want = sorted(order[:cap])  # canonical order == index order of `full`
+        assert capped["count"] == cap
+        for f in ("x", "y", "level", "response", "k_levels", "k_resp", "angle_bin"):
+            assert np.array_equal(capped[f], full[f][want]), f
+        assert np.array_equal(capped["desc"], full["desc"][want])
+
+
+def test_fallback_threshold_adds_keypoints_in_empty_cells(oracle):
+    pair = scenes.workload_pair("euroc_752x480_L8", 0)
+    a = oracle.extract_image(pair.left, _params(oracle, levels=2, max_feats=100000))
+    b = oracle.extract_image(pair.left, _params(oracle, levels=2, max_feats=100000, fast_thresh_lo=7))
+    assert b["count"] >= a["count"]
+
+
+def test_pfa_reduces_keypoints_across_levels(oracle):
+    """Sec. IV (PFA evaluation): aggregation lowers the feature count."""
+    pair = scenes.workload_pair("kitti_1241x376_L8", 0)
+    on = oracle.extract_image(pair.left, _params(oracle, max_feats=100000))
+    off = oracle.extract_image(pair.left, _params(oracle, max_feats=100000, nms_q=1))
+    assert on["count"] < off["count"]
+
+
+def _brute_match(kl, kr, p, oracle):
+    out = []
+    for i in range(kl["count"]):
+        band = oracle.match_band(int(kl["level"][i]), p.scale, p.row_band_px)
+        best = None
+        for j in range(kr["count"]):
+            if abs(int(kr["level"][j]) - int(kl["level"][i])) > 1:
+                continue
+            if abs(int(kr["Y"][j]) - int(kl["Y"][i])) > band:
+                continue
+            d = int(kl["X"][i]) - int(kr["X"][j])
+            if not 0 <= d <= p.max_disp:
+                continue
+            h = sum(bin(int(a) ^ int(b)).count("1") for a, b in zip(kl["desc"][i], kr["desc"][j]))
+            cand = (h, d, j)
+            best = cand if best is None or cand < best else best
+        if best is None:
+            out.append((-1, 0, 0xFFFF))
+        elif best[0] <= p.match_max_dist:
+            out.append((best[2], best[1], best[0]))
+        else:
+            out.append((-1, 0, best[0]))
+    return out
+
+
+def test_match_brute_force(oracle):
+    pair = scenes.planes_pair(400, 220, 0, 17, 18)
+    p = _params(oracle, levels=3, max_feats=300, match_max_dist=90)
+    kl, kr, (idx, disp, dist) = oracle.extract_pair(pair.left, pair.right, p)
+    want = _brute_match(kl, kr, p, oracle)
+    assert list(zip(idx.tolist(), disp.tolist(), dist.tolist())) == want
+    assert (idx >= 0).sum() > 20
+
+
+def test_match_band_values(oracle):
+    # ceil(2 * zeta^n) for zeta = 1.2: 2, 3, 3, 4, 5, 5, 6, 8
+    assert [oracle.match_band(n, 1.2, 2) for n in range(8)] == [2, 3, 3, 4, 5, 5, 6, 8]
+
+
+def test_known_disparity_scene(oracle):
+    """Noise-free scene shifted by one cell (32 px): each cell of the left
+    image sees the content of a right cell, the same corners are selected,
+    and the matcher recovers the disparity."""
+    pair = scenes.checker_pair(640, 480, seed=11, disparity=32, sigma=0.0)
+    p = _params(oracle, levels=1, max_feats=300)
+    kl, kr, (idx, disp, dist) = oracle.extract_pair(pair.left, pair.right, p)
+    ok = idx >= 0
+    assert ok.sum() > 200
+    assert (disp[ok] == 32).mean() >= 0.97
+    # epipolar: every accepted match lies in the row band and search range
+    for i in np.nonzero(ok)[0]:
+        j = idx[i]
+        assert abs(int(kl["Y"][i]) - int(kr["Y"][j])) <= 2
+        assert 0 <= int(kl["X"][i]) - int(kr["X"][j]) <= 128
+
+
+def test_noisy_scene_low_distance_matches_are_right(oracle):
+    pair = scenes.workload_pair("single_640x480_L1", 0)
+    p = _params(oracle, levels=1, max_feats=300, match_max_dist=40)
+    kl, kr, (idx, disp, dist) = oracle.extract_pair(pair.left, pair.right, p)
+    ok = idx >= 0
+    assert ok.sum() > 80
+    assert (disp[ok] == 16).mean() >= 0.85
+
+
+@pytest.mark.parametrize("bad", [dict(levels=0), dict(levels=9), dict(scale=1.0), dict(p_min=10, p_max=9),
+                                 dict(cell=0), dict(nms_q=2), dict(border=10), dict(max_feats=0)])
+def test_parameter_checks(oracle, bad):
+    p = _params(oracle, **bad)
+    assert not oracle.check_params(640, 480, p)
+    assert oracle.check_params(640, 480, _params(oracle, levels=8))
+    assert not oracle.check_params(60, 60, _params(oracle, levels=8))  # levels too small
