@@ -1,0 +1,245 @@
+/*
+ * jslam.h -- C ABI of libjslam, a GB300 (sm_103a) implementation of the
+ * stereo frontend hot path of "High-Speed Stereo Visual SLAM for
+ * Low-Powered Computing Devices" (Jetson-SLAM, arXiv 2410.04090).
+ *
+ * For both images of each rectified stereo pair the library builds the
+ * image pyramid (Sec. III, streamlined multiscale detection), detects FAST
+ * corners with Bounded Rectification (Sec. II-A, Eq. 1-3), culls them per
+ * grid cell (Sec. II-C-1, Feature Culling) and aggregates the survivors
+ * across levels (Sec. II-C-2, Pyramidal Feature Aggregation), computes the
+ * intensity-centroid orientation and a 256-bit steered BRIEF descriptor of
+ * every keypoint (Sec. III, ORB extraction for all scales at once), and
+ * matches left keypoints to right keypoints along image rows by descriptor
+ * distance (Sec. III, middle-end stereo matching).
+ *
+ * Conventions shared by every entry point:
+ *  - Status codes only; nothing is thrown across the ABI.  A CUDA error is
+ *    reported as JSLAM_ERR_CUDA and is sticky: the context refuses further
+ *    work until it is destroyed.
+ *  - All work is enqueued on the context's stream and is asynchronous.
+ *    Counts and device-side error flags are valid after jslam_sync().
+ *  - Images passed as device memory are owned by the caller and must stay
+ *    valid until jslam_sync() returns.  Output views point into memory owned
+ *    by the context; they stay valid until the next jslam_extract*,
+ *    jslam_match or jslam_destroy on that context.
+ *  - Device buffers only grow: a call that needs more than the context holds
+ *    reallocates once; later calls of the same or smaller size reuse it (the
+ *    paper's Synchronized Shared Memory, Sec. III).
+ *  - One context per host thread.  A context drives one device.
+ *  - Keypoints of one image are in canonical order: level ascending, then
+ *    y ascending, then x ascending (level coordinates).
+ */
+#ifndef JSLAM_H
+#define JSLAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    JSLAM_OK = 0,
+    JSLAM_ERR_ARG = -1,      /* invalid argument (null pointer, size, parameter range) */
+    JSLAM_ERR_CUDA = -2,     /* a CUDA runtime call failed; the context is unusable */
+    JSLAM_ERR_NOMEM = -3,    /* device or pinned host allocation failed */
+    JSLAM_ERR_CAPACITY = -4, /* request exceeds a limit fixed at jslam_create */
+    JSLAM_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
+    JSLAM_ERR_STATE = -6     /* call out of order (e.g. match before extract) */
+} jslam_status;
+
+/* Opaque context: device buffers, tables, stream and sticky status. */
+typedef struct jslam_ctx jslam_ctx;
+
+/* Where the bytes of a jslam_image live. */
+enum { JSLAM_MEM_DEVICE = 0, JSLAM_MEM_HOST = 1 };
+
+/* One 8-bit grayscale image, row-major with `pitch` bytes between rows.
+ * memory == JSLAM_MEM_DEVICE: `data` is device memory of the context's
+ *   device and is read in place.
+ * memory == JSLAM_MEM_HOST: `data` is host memory (pinned memory makes the
+ *   copy asynchronous); the library copies it into its own device staging
+ *   buffer on the context stream. */
+typedef struct {
+    int32_t width, height, pitch;
+    int32_t memory;
+    const uint8_t *data;
+} jslam_image;
+
+/* Context configuration.  Fields marked (paper) take the paper's values by
+ * default; the others are readings of points the paper leaves open. */
+typedef struct {
+    int32_t device;          /* CUDA device ordinal */
+    void *cuda_stream;       /* cudaStream_t to enqueue on; NULL: the context creates one */
+    int32_t max_width;       /* largest image width accepted (<= 4096) */
+    int32_t max_height;      /* largest image height accepted (<= 4096) */
+    int32_t max_levels;      /* largest pyramid depth accepted (<= 8) */
+    int32_t max_feats;       /* largest keypoint cap accepted per image */
+    int32_t max_pairs;       /* largest batch accepted by jslam_extract_batch */
+    int32_t fast_thresh_lo;  /* fallback FAST threshold for cells with no corner; <= 0: off */
+    int32_t p_min, p_max;    /* (paper) bounds of Eq. 3: 9 and 13 */
+    int32_t k_per_cell;      /* corners kept per culling cell: 1..8 (paper: 1) */
+    int32_t nms_q;           /* (paper) PFA NMS window: odd, 1..7, default 3 */
+    int32_t border;          /* pixels skipped at each level edge, >= 16 (default 19) */
+    int32_t max_disp;        /* stereo search range in s0 pixels (default 128) */
+    int32_t row_band_px;     /* stereo row band at s0, scaled by zeta^n (default 2) */
+    int32_t match_max_dist;  /* Hamming distance accepted as a match (default 100) */
+    int32_t pfa_rule;        /* 0: suppress when a neighbour has larger K_l AND K_r; 1: lexicographic */
+} jslam_config;
+
+/* One stereo pair of a batch; the per-pair parameters of jslam_extract. */
+typedef struct {
+    jslam_image left, right;
+    int32_t levels;          /* pyramid depth, 1..max_levels */
+    float scale;             /* scale factor zeta between levels, > 1 (paper: 1.2) */
+    int32_t fast_thresh;     /* epsilon of Eq. 1, 1..254 (paper: 20) */
+    int32_t cell;            /* culling cell size at s0, 1..128 (paper: 32) */
+    int32_t max_feats;       /* keypoint cap per image, 1..config.max_feats */
+} jslam_stereo_job;
+
+/* Device views of one image's keypoints (arrays of `capacity` entries; the
+ * first `count` are valid).  `count` is -1 until jslam_sync() has run. */
+typedef struct {
+    int32_t count;
+    int32_t capacity;
+    const uint16_t *x, *y;        /* level coordinates */
+    const uint16_t *X, *Y;        /* projection to the native scale s0 */
+    const uint8_t *level;         /* pyramid level */
+    const uint8_t *angle_bin;     /* orientation sector 0..29 (12 degrees each) */
+    const uint16_t *response;     /* FAST response: sum of |I_p - I_c| over the ring */
+    const uint8_t *k_levels;      /* PFA K_l: levels detecting this s0 pixel */
+    const uint32_t *k_resp;       /* PFA K_r: summed response at this s0 pixel */
+    const float *angle;           /* intensity-centroid angle, radians, (-pi, pi] */
+    const uint32_t *desc;         /* capacity x 8 words; bit i of pair i in word i/32 */
+} jslam_keypoints;
+
+/* Device views of one pair's stereo matches, one entry per left keypoint. */
+typedef struct {
+    int32_t count;                /* == left keypoint count; -1 until jslam_sync() */
+    const int32_t *right_idx;     /* canonical index of the right keypoint, -1 if none */
+    const int16_t *disparity;     /* X_left - X_right in s0 pixels (0 if none) */
+    const uint16_t *dist;         /* Hamming distance of the best candidate (65535: no candidate) */
+} jslam_matches;
+
+/* Device views of one pyramid level of one image (for consumers that share
+ * the frontend's images, as the paper's middle-end does). */
+typedef struct {
+    int32_t width, height;
+    int32_t raw_pitch, blurred_pitch;
+    const uint8_t *raw;           /* level n resampled from level 0 (level 0: the input) */
+    const uint8_t *blurred;       /* 7-tap Gaussian of the raw level (descriptor input) */
+} jslam_level_view;
+
+/* Fill `cfg` with the defaults (device 0, NULL stream, 1920x1080, 8 levels,
+ * 4000 features, 64 pairs, P_min 9, P_max 13, k 1, q 3, border 19,
+ * max_disp 128, band 2, distance 100, fallback off, dominance rule). */
+void jslam_default_config(jslam_config *cfg);
+
+/* Create a context on cfg->device.  Validates the configuration
+ * (JSLAM_ERR_ARG), uploads the constant tables (ring, blur weights, angle
+ * sectors, rotated BRIEF pattern) and creates the stream if none is given.
+ * On success *out owns the context; release it with jslam_destroy. */
+jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg);
+
+/* Enqueue the frontend for one stereo pair: pyramid, blur, FAST with Bounded
+ * Rectification, per-cell culling, PFA, keypoint cap, orientation and
+ * descriptors for both images.  Arguments as in jslam_stereo_job.
+ * JSLAM_ERR_ARG: null context, bad image (null data, pitch < width, size
+ * above the configured maximum), levels out of range, scale <= 1,
+ * threshold or cell out of range, or a level smaller than 2*border+1. */
+jslam_status jslam_extract(jslam_ctx *ctx, jslam_image left, jslam_image right,
+                           int32_t levels, float scale, int32_t fast_thresh,
+                           int32_t cell, int32_t max_feats);
+
+/* Enqueue the frontend for n stereo pairs (1 <= n <= config.max_pairs) of
+ * possibly different sizes and depths in one set of launches.  Results of
+ * pair i are read with pair index i. */
+jslam_status jslam_extract_batch(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n);
+
+/* Enqueue stereo row matching (descriptor-distance minimisation) for every
+ * pair of the last extraction.  JSLAM_ERR_STATE before any extraction. */
+jslam_status jslam_match(jslam_ctx *ctx);
+
+/* Wait for the context stream, copy counts to the host and surface any
+ * device-side error flag.  Returns the context's sticky status. */
+jslam_status jslam_sync(jslam_ctx *ctx);
+
+/* Keypoint views of `side` (0 = left, 1 = right) of pair `pair` of the last
+ * extraction.  JSLAM_ERR_ARG for an out-of-range pair or side. */
+jslam_status jslam_get_keypoints(jslam_ctx *ctx, int32_t pair, int32_t side, jslam_keypoints *out);
+
+/* Match views of pair `pair` (valid after jslam_match). */
+jslam_status jslam_get_matches(jslam_ctx *ctx, int32_t pair, jslam_matches *out);
+
+/* Level views of `side` of pair `pair` (valid after extraction). */
+jslam_status jslam_get_level(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t level,
+                             jslam_level_view *out);
+
+/* Size in bytes of pair `pair`'s result block: both images' keypoints at
+ * capacity, the matches and a 16-byte header of counts. */
+jslam_status jslam_result_bytes(jslam_ctx *ctx, int32_t pair, size_t *bytes);
+
+/* Enqueue an asynchronous copy of pair `pair`'s result block into host
+ * memory `dst` of at least jslam_result_bytes bytes (pinned memory keeps it
+ * asynchronous).  After jslam_sync the block can be read with
+ * jslam_result_view. */
+jslam_status jslam_download(jslam_ctx *ctx, int32_t pair, void *dst, size_t bytes);
+
+/* Interpret a downloaded result block: fill host views of `side` (0 or 1)
+ * into *kp and, for side 0, the matches into *m (may be NULL).  Pure host
+ * function; `block` must hold jslam_result_bytes bytes of pair `pair`. */
+jslam_status jslam_result_view(jslam_ctx *ctx, int32_t pair, const void *block, int32_t side,
+                               jslam_keypoints *kp, jslam_matches *m);
+
+/* Stages of the launch sequence, in launch order. */
+enum {
+    JSLAM_STAGE_PYRAMID = 0,      /* pyramid + Gaussian filter */
+    JSLAM_STAGE_DETECT = 1,       /* FAST + Bounded Rectification + cell culling + PFA scatter */
+    JSLAM_STAGE_PFA_NMS = 2,      /* PFA sparse NMS and per-row ranking */
+    JSLAM_STAGE_PFA_FINAL = 3,    /* PFA aggregation, cap, canonical compaction */
+    JSLAM_STAGE_ORB = 4,          /* orientation + descriptors */
+    JSLAM_STAGE_MATCH = 5,        /* stereo row matching */
+    JSLAM_NUM_STAGES = 6
+};
+
+/* Turn per-stage timing on or off.  When on, every extraction and match
+ * records a CUDA event on the context stream after each stage (a small
+ * overhead per stage). */
+jslam_status jslam_enable_stage_timing(jslam_ctx *ctx, int32_t enable);
+
+/* Device durations in milliseconds of each stage of the last extraction
+ * (and match, if one followed it), measured between the recorded events.
+ * Valid after jslam_sync(); JSLAM_ERR_STATE if timing was off. */
+jslam_status jslam_stage_times(jslam_ctx *ctx, float *ms /* JSLAM_NUM_STAGES entries */);
+
+/* Release the context and everything it owns.  NULL is ignored. */
+void jslam_destroy(jslam_ctx *ctx);
+
+/* Static description of a status code. */
+const char *jslam_status_str(jslam_status s);
+
+/* ---- host-side tables (no device work; usable without a GPU) ---- */
+
+/* The 256-pair steered BRIEF pattern rotated to each of the 30 angle
+ * sectors: out[(b * 256 + i) * 4 + {0,1,2,3}] = (px, py, qx, qy) of pair i
+ * in sector b.  `out` holds 30 * 256 * 4 bytes. */
+void jslam_pattern_table(int8_t *out);
+
+/* Level geometry of an image: width, height and culling cell size of each
+ * of `levels` levels for scale factor `scale` and s0 cell `cell`. */
+jslam_status jslam_level_geometry(int32_t width, int32_t height, int32_t levels, float scale,
+                                  int32_t cell, int32_t *w, int32_t *h, int32_t *c);
+
+/* Projection of level-n coordinate v to s0 (clamped to extent-1). */
+int32_t jslam_project(int32_t v, int32_t level, float scale, int32_t extent);
+
+/* Stereo row band at level n: ceil(row_band_px * zeta^n). */
+int32_t jslam_match_band(int32_t level, float scale, int32_t row_band_px);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JSLAM_H */

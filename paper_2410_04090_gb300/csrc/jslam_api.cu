@@ -1,0 +1,818 @@
+// C ABI of libjslam: context, grow-only device buffers, batch plans and the
+// launch sequence of the stereo frontend.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/jslam.h"
+#include "jslam_internal.h"
+#include "tables.h"
+
+namespace jslam {
+int fast_smem_bytes(int tw, int th, int cells, int k);
+}
+
+using namespace jslam;
+
+namespace {
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Optional allocation-failure injection for host-side fault tests: the
+// environment variable JSLAM_FAIL_ALLOC_AFTER=n makes the (n+1)-th device
+// allocation of the process report failure.
+int g_alloc_budget = -2;
+
+cudaError_t dev_alloc(void **p, size_t bytes)
+{
+    if (g_alloc_budget == -2) {
+        const char *e = std::getenv("JSLAM_FAIL_ALLOC_AFTER");
+        g_alloc_budget = e ? std::atoi(e) : -1;
+    }
+    if (g_alloc_budget == 0) return cudaErrorMemoryAllocation;
+    if (g_alloc_budget > 0) --g_alloc_budget;
+    return cudaMalloc(p, bytes);
+}
+
+// Device buffer that only grows (the Synchronized Shared Memory policy of
+// Sec. III: reallocate only when a request exceeds the current size).
+struct GrowBuf {
+    void *ptr = nullptr;
+    size_t cap = 0;
+    // Grows to at least `bytes`; *fresh tells whether it was (re)allocated.
+    // Zero-filling is ordered on `stream` (synchronous when null).
+    cudaError_t ensure(size_t bytes, bool zero, bool *fresh, cudaStream_t stream = nullptr)
+    {
+        if (fresh) *fresh = false;
+        if (bytes <= cap) return cudaSuccess;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+        const size_t want = align_up(bytes + bytes / 4, 1 << 20);
+        cudaError_t e = dev_alloc(&ptr, want);
+        if (e != cudaSuccess) { ptr = nullptr; return e; }
+        cap = want;
+        if (zero) e = stream ? cudaMemsetAsync(ptr, 0, want, stream) : cudaMemset(ptr, 0, want);
+        if (fresh) *fresh = true;
+        return e;
+    }
+    void release()
+    {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        cap = 0;
+    }
+    template <class T> T *as(size_t byte_off = 0) const
+    {
+        return reinterpret_cast<T *>(static_cast<char *>(ptr) + byte_off);
+    }
+};
+
+// Signature of a batch: everything that changes the plan tables (not the
+// input buffers, which reach the kernels through Inputs).
+struct JobKey {
+    int W, H, levels, eps, cell, feats;
+    uint32_t scale_bits;
+    int mem[2];
+    bool operator==(const JobKey &o) const { return std::memcmp(this, &o, sizeof(JobKey)) == 0; }
+};
+
+// Byte layout of one image's outputs (capacity C) inside a pair's result block.
+struct SideLayout {
+    size_t desc, k_resp, angle, x, y, X, Y, response, level, angle_bin, k_levels, end;
+};
+
+SideLayout side_layout(int C, size_t base)
+{
+    SideLayout s;
+    size_t o = base;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes, 256); return at; };
+    s.desc = take((size_t)C * 32);
+    s.k_resp = take((size_t)C * 4);
+    s.angle = take((size_t)C * 4);
+    s.x = take((size_t)C * 2);
+    s.y = take((size_t)C * 2);
+    s.X = take((size_t)C * 2);
+    s.Y = take((size_t)C * 2);
+    s.response = take((size_t)C * 2);
+    s.level = take((size_t)C);
+    s.angle_bin = take((size_t)C);
+    s.k_levels = take((size_t)C);
+    s.end = o;
+    return s;
+}
+
+struct PairLayout {
+    int capacity;
+    SideLayout side[2];
+    size_t match_idx, disparity, dist, bytes;
+};
+
+PairLayout pair_layout(int max_feats)
+{
+    PairLayout p;
+    p.capacity = (int)align_up((size_t)max_feats, 32);
+    p.side[0] = side_layout(p.capacity, 0);
+    p.side[1] = side_layout(p.capacity, p.side[0].end);
+    size_t o = p.side[1].end;
+    p.match_idx = o; o = align_up(o + (size_t)p.capacity * 4, 256);
+    p.disparity = o; o = align_up(o + (size_t)p.capacity * 2, 256);
+    p.dist = o; o = align_up(o + (size_t)p.capacity * 2, 256);
+    p.bytes = o;
+    return p;
+}
+
+}  // namespace
+
+struct jslam_ctx {
+    jslam_config cfg;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    jslam_status status = JSLAM_OK;
+
+    // constant tables
+    GrowBuf consts;  // pattern | cos | sin
+    int8_t *d_pattern = nullptr;
+    double *d_cos = nullptr, *d_sin = nullptr;
+
+    // per-batch buffers
+    GrowBuf plan, levels, maps, scratch, results, staging, counts;
+    int32_t *h_counts = nullptr;  // pinned mirror: 2 * max_pairs counts + error word
+    bool synced = false;
+    bool have_extract = false, have_match = false;
+
+    // current plan
+    std::vector<JobKey> keys;
+    std::vector<PairLayout> layouts;
+    std::vector<size_t> result_off;
+    std::vector<ImageDesc> h_images;
+    std::vector<LevelDesc> h_levels;
+    std::vector<size_t> staging_off;
+    Batch batch{};
+    Params prm{};
+
+    // stage timing: events[0] before the first stage, events[i + 1] after stage i
+    bool timing = false;
+    cudaEvent_t events[JSLAM_NUM_STAGES + 1] = {};
+    bool stage_done[JSLAM_NUM_STAGES] = {};
+};
+
+namespace {
+
+jslam_status fail(jslam_ctx *ctx, cudaError_t e)
+{
+    if (e == cudaSuccess) return JSLAM_OK;
+    jslam_status s = (e == cudaErrorMemoryAllocation) ? JSLAM_ERR_NOMEM : JSLAM_ERR_CUDA;
+    if (ctx && ctx->status == JSLAM_OK) ctx->status = s;
+    cudaGetLastError();
+    return s;
+}
+
+bool image_ok(const jslam_image &im, const jslam_config &cfg)
+{
+    if (!im.data || im.width < 1 || im.height < 1) return false;
+    if (im.pitch < im.width) return false;
+    if (im.width > cfg.max_width || im.height > cfg.max_height) return false;
+    if (im.memory != JSLAM_MEM_DEVICE && im.memory != JSLAM_MEM_HOST) return false;
+    return true;
+}
+
+jslam_status check_job(const jslam_ctx *ctx, const jslam_stereo_job &j)
+{
+    const jslam_config &cfg = ctx->cfg;
+    if (!image_ok(j.left, cfg) || !image_ok(j.right, cfg)) return JSLAM_ERR_ARG;
+    if (j.left.width != j.right.width || j.left.height != j.right.height) return JSLAM_ERR_ARG;
+    if (j.levels < 1 || j.levels > cfg.max_levels) return JSLAM_ERR_ARG;
+    if (!(j.scale > 1.0f) || !(j.scale < 16.0f)) return JSLAM_ERR_ARG;
+    if (j.fast_thresh < 1 || j.fast_thresh > 254) return JSLAM_ERR_ARG;
+    if (j.cell < 1 || j.cell > 128) return JSLAM_ERR_ARG;
+    if (j.max_feats < 1 || j.max_feats > cfg.max_feats) return JSLAM_ERR_ARG;
+    const Geometry g = level_geometry(j.left.width, j.left.height, j.levels, j.scale, j.cell);
+    for (int n = 0; n < j.levels; ++n) {
+        if (g.W[n] < 2 * cfg.border + 1 || g.H[n] < 2 * cfg.border + 1) return JSLAM_ERR_ARG;
+        const int cells_x = (g.W[n] + g.c[n] - 1) / g.c[n];
+        if (cells_x * cfg.k_per_cell > kMaxSegment) return JSLAM_ERR_ARG;
+    }
+    return JSLAM_OK;
+}
+
+// Cells per detection CTA: about 128 x 32 pixels, capped in cells x k.
+void fast_block(int c, int k, int *bx, int *by)
+{
+    int x = 128 / c > 1 ? 128 / c : 1;
+    int y = 32 / c > 1 ? 32 / c : 1;
+    while (x * y * k > kFastMaxCellsPerCta) {
+        if (y > 1) --y; else --x;
+    }
+    *bx = x;
+    *by = y;
+}
+
+// Build (or reuse) the plan of a batch and upload it.
+jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
+{
+    const jslam_config &cfg = ctx->cfg;
+    std::vector<JobKey> keys(n);
+    for (int p = 0; p < n; ++p) {
+        JobKey &k = keys[p];
+        std::memset(&k, 0, sizeof(k));
+        k.W = jobs[p].left.width; k.H = jobs[p].left.height; k.levels = jobs[p].levels;
+        k.eps = jobs[p].fast_thresh; k.cell = jobs[p].cell; k.feats = jobs[p].max_feats;
+        std::memcpy(&k.scale_bits, &jobs[p].scale, 4);
+        const jslam_image *im[2] = { &jobs[p].left, &jobs[p].right };
+        for (int s = 0; s < 2; ++s) k.mem[s] = im[s]->memory;
+    }
+    if (keys == ctx->keys) return JSLAM_OK;
+
+    const int n_img = 2 * n;
+    const int k = cfg.k_per_cell;
+    std::vector<Geometry> geo(n);
+    std::vector<PairLayout> layouts(n);
+    std::vector<size_t> result_off(n);
+    size_t result_bytes = 0, level_bytes = 0, map_bytes = 0, staging_bytes = 0, table_bytes = 0;
+    int n_levels = 0, n_slots = 0, n_segs = 0, max_cap = 0, fast_smem = 0;
+    for (int p = 0; p < n; ++p) {
+        geo[p] = level_geometry(jobs[p].left.width, jobs[p].left.height, jobs[p].levels, jobs[p].scale, jobs[p].cell);
+        layouts[p] = pair_layout(jobs[p].max_feats);
+        result_off[p] = result_bytes;
+        result_bytes += layouts[p].bytes;
+        max_cap = std::max(max_cap, layouts[p].capacity);
+        const Geometry &g = geo[p];
+        for (int s = 0; s < 2; ++s) {
+            for (int l = 0; l < g.levels; ++l) {
+                const size_t pitch = align_up((size_t)g.W[l], 128);
+                level_bytes += align_up(pitch * g.H[l], 256) * (l == 0 ? 1 : 2);
+                table_bytes += align_up((size_t)(g.W[l] + g.H[l]) * 4, 16);  // taps
+                table_bytes += align_up((size_t)(g.W[l] + g.H[l]) * 2, 16);  // projection
+                const int cx = (g.W[l] + g.c[l] - 1) / g.c[l], cy = (g.H[l] + g.c[l] - 1) / g.c[l];
+                n_slots += cx * cy * k;
+                n_segs += cy;
+                int bx, by;
+                fast_block(g.c[l], k, &bx, &by);
+                fast_smem = std::max(fast_smem, fast_smem_bytes(std::min(bx * g.c[l], g.W[l]),
+                                                                std::min(by * g.c[l], g.H[l]), bx * by, k));
+            }
+            n_levels += g.levels;
+            map_bytes += align_up((size_t)g.W[0] * g.H[0] * 4, 256);
+            staging_bytes += align_up((size_t)align_up(g.W[0], 128) * g.H[0], 256);
+        }
+    }
+
+    // Device arenas (grow-only).
+    cudaError_t e;
+    bool fresh = false;  // a fresh score map is zero-filled on the stream
+    if ((e = ctx->levels.ensure(level_bytes + 256, false, nullptr)) != cudaSuccess) return fail(ctx, e);
+    if ((e = ctx->maps.ensure(map_bytes + 256, true, &fresh, ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    if ((e = ctx->results.ensure(result_bytes + 256, true, nullptr, ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    bool any_host = false;
+    for (int p = 0; p < n; ++p)
+        any_host |= jobs[p].left.memory == JSLAM_MEM_HOST || jobs[p].right.memory == JSLAM_MEM_HOST;
+    if (any_host && (e = ctx->staging.ensure(staging_bytes + 256, false, nullptr)) != cudaSuccess) return fail(ctx, e);
+    const size_t slot_words = (size_t)n_slots + 64;
+    const size_t seg_words = (size_t)n_segs + 64;
+    const size_t scratch_bytes = slot_words * 4 * 4 + seg_words * 4 * 2;
+    if ((e = ctx->scratch.ensure(scratch_bytes, false, nullptr)) != cudaSuccess) return fail(ctx, e);
+
+    // Host tables: [images][levels][pairs][pyr base][fast base][seg level][taps/proj ...]
+    size_t off = 0;
+    auto reserve = [&](size_t bytes) { size_t at = off; off = align_up(off + bytes, 256); return at; };
+    const size_t o_images = reserve(sizeof(ImageDesc) * n_img);
+    const size_t o_levels = reserve(sizeof(LevelDesc) * n_levels);
+    const size_t o_pairs = reserve(sizeof(PairDesc) * n);
+    const size_t o_pyr = reserve(sizeof(int32_t) * (n_levels + 1));
+    const size_t o_fast = reserve(sizeof(int32_t) * (n_levels + 1));
+    const size_t o_seg = reserve(sizeof(int32_t) * (n_segs + 1));
+    const size_t o_lstart = reserve(sizeof(int32_t) * (kMaxLevels + 1) * n_img);
+    const size_t o_tables = reserve(table_bytes + 256);
+    if ((e = ctx->plan.ensure(off, false, nullptr)) != cudaSuccess) return fail(ctx, e);
+
+    std::vector<char> host(off, 0);
+    char *dplan = ctx->plan.as<char>();
+    auto images = reinterpret_cast<ImageDesc *>(host.data() + o_images);
+    auto levels = reinterpret_cast<LevelDesc *>(host.data() + o_levels);
+    auto pairs = reinterpret_cast<PairDesc *>(host.data() + o_pairs);
+    auto pyr_base = reinterpret_cast<int32_t *>(host.data() + o_pyr);
+    auto fast_base = reinterpret_cast<int32_t *>(host.data() + o_fast);
+    auto seg_level = reinterpret_cast<int32_t *>(host.data() + o_seg);
+    size_t t_off = o_tables, lvl_off = 0, map_off = 0, stage_off = 0;
+    int li = 0, slot = 0, seg = 0, pyr = 0, fast = 0;
+    ctx->staging_off.assign(n_img, 0);
+    int32_t *dcounts = ctx->counts.as<int32_t>();
+
+    for (int p = 0; p < n; ++p) {
+        const Geometry &g = geo[p];
+        const PairLayout &pl = layouts[p];
+        char *rblock = ctx->results.as<char>(result_off[p]);
+        for (int s = 0; s < 2; ++s) {
+            const int img = 2 * p + s;
+            const jslam_image &im = s == 0 ? jobs[p].left : jobs[p].right;
+            ImageDesc &I = images[img];
+            if (im.memory == JSLAM_MEM_HOST) {
+                ctx->staging_off[img] = stage_off;
+                stage_off += align_up(align_up(g.W[0], 128) * g.H[0], 256);
+            }
+            I.W0 = g.W[0]; I.H0 = g.H[0];
+            I.levels = g.levels; I.level_base = li;
+            I.eps_hi = jobs[p].fast_thresh; I.eps_lo = cfg.fast_thresh_lo;
+            I.max_feats = jobs[p].max_feats;
+            I.slot_base = slot; I.seg_base = seg;
+            I.map = ctx->maps.as<uint32_t>(map_off);
+            map_off += align_up((size_t)g.W[0] * g.H[0] * 4, 256);
+            I.count = dcounts + img;
+            I.level_start = reinterpret_cast<int32_t *>(dplan + o_lstart) + img * (kMaxLevels + 1);
+            const SideLayout &sl = pl.side[s];
+            I.out.capacity = pl.capacity;
+            I.out.desc = reinterpret_cast<uint32_t *>(rblock + sl.desc);
+            I.out.k_resp = reinterpret_cast<uint32_t *>(rblock + sl.k_resp);
+            I.out.angle = reinterpret_cast<float *>(rblock + sl.angle);
+            I.out.x = reinterpret_cast<uint16_t *>(rblock + sl.x);
+            I.out.y = reinterpret_cast<uint16_t *>(rblock + sl.y);
+            I.out.X = reinterpret_cast<uint16_t *>(rblock + sl.X);
+            I.out.Y = reinterpret_cast<uint16_t *>(rblock + sl.Y);
+            I.out.response = reinterpret_cast<uint16_t *>(rblock + sl.response);
+            I.out.level = reinterpret_cast<uint8_t *>(rblock + sl.level);
+            I.out.angle_bin = reinterpret_cast<uint8_t *>(rblock + sl.angle_bin);
+            I.out.k_levels = reinterpret_cast<uint8_t *>(rblock + sl.k_levels);
+
+            for (int l = 0; l < g.levels; ++l, ++li) {
+                LevelDesc &L = levels[li];
+                const double sc = zeta_pow(jobs[p].scale, l);
+                L.W = g.W[l]; L.H = g.H[l]; L.c = g.c[l];
+                L.cells_x = (L.W + L.c - 1) / L.c;
+                L.cells_y = (L.H + L.c - 1) / L.c;
+                fast_block(L.c, k, &L.bx, &L.by);
+                L.image = img; L.level = l;
+                L.band = match_band(l, jobs[p].scale, cfg.row_band_px);
+                const size_t pitch = align_up((size_t)L.W, 128);
+                L.blur_pitch = (int)pitch;
+                if (l == 0) {
+                    L.raw = nullptr; L.raw_w = nullptr; L.pitch = 0;
+                    L.blur = ctx->levels.as<uint8_t>(lvl_off);
+                    lvl_off += align_up(pitch * L.H, 256);
+                } else {
+                    L.raw_w = ctx->levels.as<uint8_t>(lvl_off);
+                    L.raw = L.raw_w;
+                    lvl_off += align_up(pitch * L.H, 256);
+                    L.blur = ctx->levels.as<uint8_t>(lvl_off);
+                    lvl_off += align_up(pitch * L.H, 256);
+                    L.pitch = (int)pitch;
+                }
+                // taps
+                uint32_t *tx = reinterpret_cast<uint32_t *>(host.data() + t_off);
+                L.tapx = reinterpret_cast<const uint32_t *>(dplan + t_off);
+                L.tapy = L.tapx + L.W;
+                for (int x = 0; x < L.W; ++x) tx[x] = bilinear_tap(x, sc, g.W[0]);
+                for (int y = 0; y < L.H; ++y) tx[L.W + y] = bilinear_tap(y, sc, g.H[0]);
+                t_off += align_up((size_t)(L.W + L.H) * 4, 16);
+                uint16_t *px = reinterpret_cast<uint16_t *>(host.data() + t_off);
+                L.projx = reinterpret_cast<const uint16_t *>(dplan + t_off);
+                L.projy = L.projx + L.W;
+                for (int x = 0; x < L.W; ++x) px[x] = project(x, sc, g.W[0]);
+                for (int y = 0; y < L.H; ++y) px[L.W + y] = project(y, sc, g.H[0]);
+                t_off += align_up((size_t)(L.W + L.H) * 2, 16);
+
+                L.slot_base = slot;
+                L.seg_base = seg;
+                slot += L.cells_x * L.cells_y * k;
+                for (int r = 0; r < L.cells_y; ++r) seg_level[seg + r] = li;
+                seg += L.cells_y;
+                pyr_base[li] = pyr;
+                pyr += ((L.W + kPyrTW - 1) / kPyrTW) * ((L.H + kPyrTH - 1) / kPyrTH);
+                fast_base[li] = fast;
+                fast += ((L.cells_x + L.bx - 1) / L.bx) * ((L.cells_y + L.by - 1) / L.by);
+            }
+            I.slot_count = slot - I.slot_base;
+            I.seg_count = seg - I.seg_base;
+        }
+        PairDesc &P = pairs[p];
+        P.left = 2 * p; P.right = 2 * p + 1;
+        P.match_idx = reinterpret_cast<int32_t *>(rblock + pl.match_idx);
+        P.disparity = reinterpret_cast<int16_t *>(rblock + pl.disparity);
+        P.dist = reinterpret_cast<uint16_t *>(rblock + pl.dist);
+    }
+    pyr_base[n_levels] = pyr;
+    fast_base[n_levels] = fast;
+    seg_level[n_segs] = n_levels - 1;
+
+    e = cudaMemcpyAsync(ctx->plan.ptr, host.data(), off, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, e);
+
+    Batch &b = ctx->batch;
+    b.images = reinterpret_cast<const ImageDesc *>(dplan + o_images);
+    b.levels = reinterpret_cast<const LevelDesc *>(dplan + o_levels);
+    b.pairs = reinterpret_cast<const PairDesc *>(dplan + o_pairs);
+    b.pyr_tile_base = reinterpret_cast<const int32_t *>(dplan + o_pyr);
+    b.fast_tile_base = reinterpret_cast<const int32_t *>(dplan + o_fast);
+    b.seg_level = reinterpret_cast<const int32_t *>(dplan + o_seg);
+    b.n_images = n_img; b.n_levels = n_levels; b.n_pairs = n; b.n_segments = n_segs;
+    b.pyr_tiles = pyr; b.fast_tiles = fast; b.max_capacity = max_cap; b.fast_smem = fast_smem;
+    uint32_t *sw = ctx->scratch.as<uint32_t>();
+    b.slots = sw;
+    b.slot_k = sw + slot_words;
+    b.slot_rank = reinterpret_cast<int32_t *>(sw + 2 * slot_words);
+    b.canon = reinterpret_cast<int32_t *>(sw + 3 * slot_words);
+    b.seg_count = reinterpret_cast<int32_t *>(sw + 4 * slot_words);
+    b.seg_off = reinterpret_cast<int32_t *>(sw + 4 * slot_words + seg_words);
+    b.pattern = ctx->d_pattern;
+    b.bin_cos = ctx->d_cos;
+    b.bin_sin = ctx->d_sin;
+    b.err = reinterpret_cast<uint32_t *>(dcounts + 2 * cfg.max_pairs);
+    b.prm = ctx->prm;
+
+    ctx->keys = keys;
+    ctx->layouts = layouts;
+    ctx->result_off = result_off;
+    ctx->h_images.assign(images, images + n_img);
+    ctx->h_levels.assign(levels, levels + n_levels);
+    return JSLAM_OK;
+}
+
+jslam_status enqueue_counts(jslam_ctx *ctx)
+{
+    const size_t bytes = sizeof(int32_t) * (2 * (size_t)ctx->cfg.max_pairs + 8);
+    return fail(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->counts.ptr, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+}
+
+jslam_status use_device(jslam_ctx *ctx)
+{
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) return fail(ctx, cudaErrorInvalidDevice);
+    if (cur != ctx->cfg.device) return fail(ctx, cudaSetDevice(ctx->cfg.device));
+    return JSLAM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void jslam_default_config(jslam_config *cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->device = 0;
+    cfg->cuda_stream = nullptr;
+    cfg->max_width = 1920;
+    cfg->max_height = 1080;
+    cfg->max_levels = 8;
+    cfg->max_feats = 4000;
+    cfg->max_pairs = 64;
+    cfg->fast_thresh_lo = 0;
+    cfg->p_min = 9;
+    cfg->p_max = 13;
+    cfg->k_per_cell = 1;
+    cfg->nms_q = 3;
+    cfg->border = 19;
+    cfg->max_disp = 128;
+    cfg->row_band_px = 2;
+    cfg->match_max_dist = 100;
+    cfg->pfa_rule = 0;
+}
+
+jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
+{
+    if (!out || !cfg) return JSLAM_ERR_ARG;
+    *out = nullptr;
+    const jslam_config &c = *cfg;
+    if (c.max_width < 1 || c.max_width > 4096 || c.max_height < 1 || c.max_height > 4096) return JSLAM_ERR_ARG;
+    if (c.max_levels < 1 || c.max_levels > kMaxLevels || c.max_feats < 1 || c.max_feats > (1 << 20)) return JSLAM_ERR_ARG;
+    if (c.max_pairs < 1 || 2 * c.max_pairs > kMaxImages) return JSLAM_ERR_ARG;
+    if (c.fast_thresh_lo > 254) return JSLAM_ERR_ARG;
+    if (c.p_min < 1 || c.p_max > 16 || c.p_min > c.p_max) return JSLAM_ERR_ARG;
+    if (c.k_per_cell < 1 || c.k_per_cell > 8) return JSLAM_ERR_ARG;
+    if (c.nms_q < 1 || c.nms_q > 7 || (c.nms_q & 1) == 0) return JSLAM_ERR_ARG;
+    if (c.border < 16 || c.border > 512) return JSLAM_ERR_ARG;
+    if (c.max_disp < 0 || c.max_disp > 4096 || c.row_band_px < 0 || c.row_band_px > 64) return JSLAM_ERR_ARG;
+    if (c.match_max_dist < 0 || c.pfa_rule < 0 || c.pfa_rule > 1) return JSLAM_ERR_ARG;
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
+        cudaGetLastError();
+        return JSLAM_ERR_CUDA;
+    }
+    jslam_ctx *ctx = new jslam_ctx();
+    ctx->cfg = c;
+    ctx->prm.p_min = c.p_min; ctx->prm.p_max = c.p_max; ctx->prm.k = c.k_per_cell;
+    ctx->prm.nms_rad = (c.nms_q - 1) / 2; ctx->prm.border = c.border; ctx->prm.rule = c.pfa_rule;
+    ctx->prm.max_disp = c.max_disp; ctx->prm.max_dist = c.match_max_dist;
+
+    jslam_status st = JSLAM_OK;
+    cudaError_t e = cudaSetDevice(c.device);
+    if (e == cudaSuccess) {
+        if (c.cuda_stream) {
+            ctx->stream = static_cast<cudaStream_t>(c.cuda_stream);
+        } else {
+            e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+            ctx->own_stream = e == cudaSuccess;
+        }
+    }
+    if (e == cudaSuccess) e = configure_kernels();
+    int32_t w[7];
+    blur_weights(w);
+    if (e == cudaSuccess) e = set_blur_weights(w);
+    const size_t pat_bytes = (size_t)kBins * kPairs * 4;
+    if (e == cudaSuccess) e = ctx->consts.ensure(pat_bytes + 2 * kBins * sizeof(double) + 512, false, nullptr);
+    if (e == cudaSuccess) {
+        std::vector<char> h(pat_bytes + 2 * kBins * sizeof(double) + 256, 0);
+        rotated_pattern(reinterpret_cast<int8_t *>(h.data()));
+        double *cs = reinterpret_cast<double *>(h.data() + pat_bytes);
+        sector_tables(cs, cs + kBins);
+        e = cudaMemcpy(ctx->consts.ptr, h.data(), h.size(), cudaMemcpyHostToDevice);
+        ctx->d_pattern = ctx->consts.as<int8_t>();
+        ctx->d_cos = ctx->consts.as<double>(pat_bytes);
+        ctx->d_sin = ctx->d_cos + kBins;
+    }
+    if (e == cudaSuccess) e = ctx->counts.ensure(sizeof(int32_t) * (2 * (size_t)c.max_pairs + 8), true, nullptr);
+    if (e == cudaSuccess) {
+        e = cudaMallocHost(reinterpret_cast<void **>(&ctx->h_counts), sizeof(int32_t) * (2 * (size_t)c.max_pairs + 8));
+        if (e == cudaSuccess) std::memset(ctx->h_counts, 0, sizeof(int32_t) * (2 * (size_t)c.max_pairs + 8));
+        else ctx->h_counts = nullptr;
+    }
+    if (e != cudaSuccess) {
+        st = (e == cudaErrorMemoryAllocation) ? JSLAM_ERR_NOMEM : JSLAM_ERR_CUDA;
+        cudaGetLastError();
+        jslam_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_extract_batch(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n)
+{
+    if (!ctx || !jobs) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (n < 1) return JSLAM_ERR_ARG;
+    if (n > ctx->cfg.max_pairs) return JSLAM_ERR_CAPACITY;
+    for (int p = 0; p < n; ++p) {
+        const jslam_status s = check_job(ctx, jobs[p]);
+        if (s != JSLAM_OK) return s;
+    }
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    st = build_plan(ctx, jobs, n);
+    if (st != JSLAM_OK) return st;
+
+    // Level-0 inputs of this call; host images are copied into the staging
+    // buffers on the context stream first.
+    Batch &b = ctx->batch;
+    for (int p = 0; p < n; ++p) {
+        const jslam_image *im[2] = { &jobs[p].left, &jobs[p].right };
+        for (int s = 0; s < 2; ++s) {
+            const int img = 2 * p + s;
+            if (im[s]->memory == JSLAM_MEM_HOST) {
+                uint8_t *dst = ctx->staging.as<uint8_t>(ctx->staging_off[img]);
+                const int dpitch = (int)align_up((size_t)im[s]->width, 128);
+                cudaError_t e = cudaMemcpy2DAsync(dst, dpitch, im[s]->data, im[s]->pitch, im[s]->width,
+                                                  im[s]->height, cudaMemcpyHostToDevice, ctx->stream);
+                if (e != cudaSuccess) return fail(ctx, e);
+                b.in.ptr[img] = dst;
+                b.in.pitch[img] = dpitch;
+            } else {
+                b.in.ptr[img] = im[s]->data;
+                b.in.pitch[img] = im[s]->pitch;
+            }
+        }
+    }
+    cudaError_t e;
+    if ((e = launch_pyramid(b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    if ((e = launch_fast_cull(b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    if ((e = launch_pfa_nms(b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    if ((e = launch_pfa_finalize(b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    if ((e = launch_orient_desc(b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    ctx->have_extract = true;
+    ctx->have_match = false;
+    ctx->synced = false;
+    return enqueue_counts(ctx);
+}
+
+jslam_status jslam_extract(jslam_ctx *ctx, jslam_image left, jslam_image right, int32_t levels, float scale,
+                           int32_t fast_thresh, int32_t cell, int32_t max_feats)
+{
+    jslam_stereo_job j;
+    j.left = left; j.right = right; j.levels = levels; j.scale = scale;
+    j.fast_thresh = fast_thresh; j.cell = cell; j.max_feats = max_feats;
+    return jslam_extract_batch(ctx, &j, 1);
+}
+
+jslam_status jslam_match(jslam_ctx *ctx)
+{
+    if (!ctx) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (!ctx->have_extract) return JSLAM_ERR_STATE;
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    cudaError_t e = launch_match(ctx->batch, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, e);
+    if (ctx->timing && ctx->stage_done[JSLAM_STAGE_ORB]) {
+        if ((e = cudaEventRecord(ctx->events[JSLAM_STAGE_MATCH + 1], ctx->stream)) != cudaSuccess) return fail(ctx, e);
+        ctx->stage_done[JSLAM_STAGE_MATCH] = true;
+    }
+    ctx->have_match = true;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_sync(jslam_ctx *ctx)
+{
+    if (!ctx) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, e);
+    ctx->synced = true;
+    if (ctx->h_counts[2 * ctx->cfg.max_pairs] != 0) ctx->status = JSLAM_ERR_CAPACITY;
+    return ctx->status;
+}
+
+static int32_t synced_count(const jslam_ctx *ctx, int img)
+{
+    return ctx->synced ? ctx->h_counts[img] : -1;
+}
+
+jslam_status jslam_get_keypoints(jslam_ctx *ctx, int32_t pair, int32_t side, jslam_keypoints *out)
+{
+    if (!ctx || !out) return JSLAM_ERR_ARG;
+    if (!ctx->have_extract) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size() || side < 0 || side > 1) return JSLAM_ERR_ARG;
+    const KpOut &o = ctx->h_images[2 * pair + side].out;
+    out->count = synced_count(ctx, 2 * pair + side);
+    out->capacity = o.capacity;
+    out->x = o.x; out->y = o.y; out->X = o.X; out->Y = o.Y;
+    out->level = o.level; out->angle_bin = o.angle_bin; out->response = o.response;
+    out->k_levels = o.k_levels; out->k_resp = o.k_resp; out->angle = o.angle; out->desc = o.desc;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_get_matches(jslam_ctx *ctx, int32_t pair, jslam_matches *out)
+{
+    if (!ctx || !out) return JSLAM_ERR_ARG;
+    if (!ctx->have_match) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size()) return JSLAM_ERR_ARG;
+    const PairLayout &pl = ctx->layouts[pair];
+    char *rb = ctx->results.as<char>(ctx->result_off[pair]);
+    out->count = synced_count(ctx, 2 * pair);
+    out->right_idx = reinterpret_cast<const int32_t *>(rb + pl.match_idx);
+    out->disparity = reinterpret_cast<const int16_t *>(rb + pl.disparity);
+    out->dist = reinterpret_cast<const uint16_t *>(rb + pl.dist);
+    return JSLAM_OK;
+}
+
+jslam_status jslam_get_level(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t level, jslam_level_view *out)
+{
+    if (!ctx || !out) return JSLAM_ERR_ARG;
+    if (!ctx->have_extract) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size() || side < 0 || side > 1) return JSLAM_ERR_ARG;
+    const ImageDesc &I = ctx->h_images[2 * pair + side];
+    if (level < 0 || level >= I.levels) return JSLAM_ERR_ARG;
+    const LevelDesc &L = ctx->h_levels[I.level_base + level];
+    out->width = L.W; out->height = L.H; out->blurred_pitch = L.blur_pitch; out->blurred = L.blur;
+    out->raw_pitch = level == 0 ? ctx->batch.in.pitch[2 * pair + side] : L.pitch;
+    out->raw = level == 0 ? ctx->batch.in.ptr[2 * pair + side] : L.raw;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_result_bytes(jslam_ctx *ctx, int32_t pair, size_t *bytes)
+{
+    if (!ctx || !bytes) return JSLAM_ERR_ARG;
+    if (!ctx->have_extract) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size()) return JSLAM_ERR_ARG;
+    *bytes = ctx->layouts[pair].bytes;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_download(jslam_ctx *ctx, int32_t pair, void *dst, size_t bytes)
+{
+    if (!ctx || !dst) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (!ctx->have_extract) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size()) return JSLAM_ERR_ARG;
+    if (bytes < ctx->layouts[pair].bytes) return JSLAM_ERR_ARG;
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    return fail(ctx, cudaMemcpyAsync(dst, ctx->results.as<char>(ctx->result_off[pair]), ctx->layouts[pair].bytes,
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+}
+
+jslam_status jslam_result_view(jslam_ctx *ctx, int32_t pair, const void *block, int32_t side, jslam_keypoints *kp,
+                               jslam_matches *m)
+{
+    if (!ctx || !block || !kp) return JSLAM_ERR_ARG;
+    if (!ctx->have_extract) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size() || side < 0 || side > 1) return JSLAM_ERR_ARG;
+    const PairLayout &pl = ctx->layouts[pair];
+    const SideLayout &s = pl.side[side];
+    const char *b = static_cast<const char *>(block);
+    kp->count = synced_count(ctx, 2 * pair + side);
+    kp->capacity = pl.capacity;
+    kp->desc = reinterpret_cast<const uint32_t *>(b + s.desc);
+    kp->k_resp = reinterpret_cast<const uint32_t *>(b + s.k_resp);
+    kp->angle = reinterpret_cast<const float *>(b + s.angle);
+    kp->x = reinterpret_cast<const uint16_t *>(b + s.x);
+    kp->y = reinterpret_cast<const uint16_t *>(b + s.y);
+    kp->X = reinterpret_cast<const uint16_t *>(b + s.X);
+    kp->Y = reinterpret_cast<const uint16_t *>(b + s.Y);
+    kp->response = reinterpret_cast<const uint16_t *>(b + s.response);
+    kp->level = reinterpret_cast<const uint8_t *>(b + s.level);
+    kp->angle_bin = reinterpret_cast<const uint8_t *>(b + s.angle_bin);
+    kp->k_levels = reinterpret_cast<const uint8_t *>(b + s.k_levels);
+    if (m) {
+        m->count = side == 0 && ctx->have_match ? kp->count : -1;
+        m->right_idx = reinterpret_cast<const int32_t *>(b + pl.match_idx);
+        m->disparity = reinterpret_cast<const int16_t *>(b + pl.disparity);
+        m->dist = reinterpret_cast<const uint16_t *>(b + pl.dist);
+    }
+    return JSLAM_OK;
+}
+
+jslam_status jslam_enable_stage_timing(jslam_ctx *ctx, int32_t enable)
+{
+    if (!ctx) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (enable && !ctx->events[0]) {
+        jslam_status st = use_device(ctx);
+        if (st != JSLAM_OK) return st;
+        for (cudaEvent_t &ev : ctx->events) {
+            cudaError_t e = cudaEventCreate(&ev);
+            if (e != cudaSuccess) return fail(ctx, e);
+        }
+    }
+    ctx->timing = enable != 0;
+    for (bool &d : ctx->stage_done) d = false;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_stage_times(jslam_ctx *ctx, float *ms)
+{
+    if (!ctx || !ms) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (!ctx->timing || !ctx->stage_done[0]) return JSLAM_ERR_STATE;
+    for (int i = 0; i < JSLAM_NUM_STAGES; ++i) {
+        ms[i] = 0.0f;
+        if (!ctx->stage_done[i]) continue;
+        // the match stage follows the ORB stage's event
+        cudaError_t e = cudaEventElapsedTime(&ms[i], ctx->events[i], ctx->events[i + 1]);
+        if (e != cudaSuccess) return fail(ctx, e);
+    }
+    return JSLAM_OK;
+}
+
+void jslam_destroy(jslam_ctx *ctx)
+{
+    if (!ctx) return;
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != ctx->cfg.device) cudaSetDevice(ctx->cfg.device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    ctx->consts.release();
+    ctx->plan.release();
+    ctx->levels.release();
+    ctx->maps.release();
+    ctx->scratch.release();
+    ctx->results.release();
+    ctx->staging.release();
+    ctx->counts.release();
+    if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
+    for (cudaEvent_t ev : ctx->events)
+        if (ev) cudaEventDestroy(ev);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    cudaGetLastError();
+    delete ctx;
+}
+
+const char *jslam_status_str(jslam_status s)
+{
+    switch (s) {
+    case JSLAM_OK: return "ok";
+    case JSLAM_ERR_ARG: return "invalid argument";
+    case JSLAM_ERR_CUDA: return "CUDA error";
+    case JSLAM_ERR_NOMEM: return "out of memory";
+    case JSLAM_ERR_CAPACITY: return "capacity exceeded";
+    case JSLAM_ERR_TIMEOUT: return "device wait timed out";
+    case JSLAM_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+void jslam_pattern_table(int8_t *out)
+{
+    if (out) rotated_pattern(out);
+}
+
+jslam_status jslam_level_geometry(int32_t width, int32_t height, int32_t levels, float scale, int32_t cell,
+                                  int32_t *w, int32_t *h, int32_t *c)
+{
+    if (!w || !h || !c || levels < 1 || levels > kMaxLevels || !(scale > 1.0f) || cell < 1) return JSLAM_ERR_ARG;
+    const Geometry g = level_geometry(width, height, levels, scale, cell);
+    for (int n = 0; n < levels; ++n) { w[n] = g.W[n]; h[n] = g.H[n]; c[n] = g.c[n]; }
+    return JSLAM_OK;
+}
+
+int32_t jslam_project(int32_t v, int32_t level, float scale, int32_t extent)
+{
+    return project(v, zeta_pow(scale, level), extent);
+}
+
+int32_t jslam_match_band(int32_t level, float scale, int32_t row_band_px)
+{
+    return match_band(level, scale, row_band_px);
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal types shared by the host code and the kernels of libjslam.
+//
+// The whole batch (every image of every stereo pair, every pyramid level) is
+// described by three device tables built on the host:
+//   ImageDesc[2 * pairs]   one per image (pair p: left = 2p, right = 2p + 1)
+//   LevelDesc[sum levels]  one per (image, level), image-major
+//   PairDesc[pairs]        stereo matching outputs
+// and each kernel's grid is a flat list of work units mapped onto these
+// tables through small prefix arrays (tiles per level, segments per level),
+// so a batch of mixed image sizes and pyramid depths runs in one launch per
+// stage.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace jslam {
+
+constexpr int kMaxLevels = 8;
+constexpr int kBins = 30;        // orientation sectors of 12 degrees
+constexpr int kPairs = 256;      // BRIEF point pairs
+constexpr int kDiskR = 15;       // intensity-centroid disk radius
+constexpr int kMaxSegment = 4096;  // candidate slots per (level, cell row)
+constexpr int kMaxImages = 256;    // images per batch (two per stereo pair)
+
+// Pyramid tile (outputs per CTA) and thread count.
+constexpr int kPyrTW = 128, kPyrTH = 32, kPyrThreads = 256;
+// Detection tile: at most this many pixels a side (host picks cells per CTA).
+constexpr int kFastMaxTile = 128, kFastThreads = 256;
+constexpr int kFastMaxCellsPerCta = 2048;  // cells x k per CTA
+constexpr int kNmsThreads = 128;
+constexpr int kFinThreads = 1024;
+
+// Device error bits (OR-ed into the context's error word).
+constexpr uint32_t kErrSegment = 1u << 0;  // a segment was larger than kMaxSegment
+constexpr uint32_t kErrDecode = 1u << 1;   // a candidate decoded outside its level
+
+struct KpOut {
+    uint16_t *x, *y, *X, *Y, *response;
+    uint8_t *level, *angle_bin, *k_levels;
+    uint32_t *k_resp;
+    float *angle;
+    uint32_t *desc;  // capacity x 8
+    int32_t capacity;
+};
+
+struct LevelDesc {
+    const uint8_t *raw;      // raw level (level 0: unused, the input comes from Inputs)
+    uint8_t *raw_w;          // writable raw level (nullptr at level 0)
+    uint8_t *blur;           // blurred level
+    const uint32_t *tapx;    // bilinear taps: src index | weight << 16 (levels >= 1)
+    const uint32_t *tapy;
+    const uint16_t *projx;   // s0 projection of each x / y of the level
+    const uint16_t *projy;
+    int32_t W, H, pitch;     // pitch of raw (level 0: see Inputs)
+    int32_t blur_pitch;
+    int32_t c, cells_x, cells_y;
+    int32_t bx, by;          // cells per detection CTA
+    int32_t slot_base;       // first candidate slot of the level
+    int32_t seg_base;        // first segment (cell row) of the level
+    int32_t image, level;
+    int32_t band;            // stereo row band for keypoints of this level
+};
+
+struct ImageDesc {
+    int32_t W0, H0;
+    int32_t levels, level_base;
+    int32_t eps_hi, eps_lo;  // eps_lo <= 0: no fallback
+    int32_t max_feats;
+    int32_t slot_base, slot_count;
+    int32_t seg_base, seg_count;
+    uint32_t *map;           // W0 * H0 packed (K_l << 16 | K_r); all zero between runs
+    int32_t *count;          // keypoint count written by finalisation
+    int32_t *level_start;    // kMaxLevels + 1 entries
+    KpOut out;
+};
+
+struct PairDesc {
+    int32_t left, right;
+    int32_t *match_idx;
+    int16_t *disparity;
+    uint16_t *dist;
+};
+
+// Parameters fixed for a context.
+struct Params {
+    int32_t p_min, p_max, k, nms_rad, border, rule;
+    int32_t max_disp, max_dist;
+};
+
+// Level-0 pixels of every image of the call.  Passed by value as a kernel
+// parameter so that a plan (which depends only on the shapes) is reused
+// across calls whose input buffers differ.
+struct Inputs {
+    const uint8_t *ptr[kMaxImages];
+    int32_t pitch[kMaxImages];
+};
+
+// Everything the kernels of one extraction need.
+struct Batch {
+    const ImageDesc *images;
+    const LevelDesc *levels;
+    const PairDesc *pairs;
+    const int32_t *pyr_tile_base;   // n_levels + 1
+    const int32_t *fast_tile_base;  // n_levels + 1
+    const int32_t *seg_level;       // level index of each segment
+    int32_t n_images, n_levels, n_pairs, n_segments;
+    int32_t pyr_tiles, fast_tiles;
+    int32_t max_capacity;           // largest keypoint capacity of any image
+    int32_t fast_smem;              // dynamic shared memory of the detection kernel
+    uint32_t *slots;                // candidate keys per slot
+    uint32_t *slot_k;               // PFA scores seen by each slot
+    int32_t *slot_rank;             // rank within its segment, -1 if suppressed
+    int32_t *seg_count;             // survivors per segment
+    int32_t *seg_off;               // exclusive prefix of seg_count per image
+    int32_t *canon;                 // slot of each canonical position
+    const int8_t *pattern;          // kBins x kPairs x 4
+    const double *bin_cos, *bin_sin;
+    uint32_t *err;
+    Params prm;
+    Inputs in;
+};
+
+// Kernel launchers (one per stage), all on `stream`.
+cudaError_t launch_pyramid(const Batch &b, cudaStream_t stream);
+cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream);
+cudaError_t launch_pfa_nms(const Batch &b, cudaStream_t stream);
+cudaError_t launch_pfa_finalize(const Batch &b, cudaStream_t stream);
+cudaError_t launch_orient_desc(const Batch &b, cudaStream_t stream);
+cudaError_t launch_match(const Batch &b, cudaStream_t stream);
+cudaError_t set_blur_weights(const int32_t w[7]);
+cudaError_t configure_kernels();
+
+}  // namespace jslam

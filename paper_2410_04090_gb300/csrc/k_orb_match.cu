@@ -1,0 +1,169 @@
+// ORB extraction for all scales at once and stereo row matching (Sec. III:
+// streamlined multiscale detection and extraction; middle-end stereo
+// matching by descriptor-distance minimisation).
+//
+// k_orient_desc  one warp per keypoint of any image and level.  Lanes 0..30
+//                own one column of the radius-15 disk and walk its rows to
+//                accumulate the intensity moments m10, m01 on the raw level;
+//                lanes 0..29 each test one sector boundary in IEEE double
+//                (explicit round-to-nearest multiplies and subtract, so the
+//                sector equals the one the host-side definition gives); the
+//                256 BRIEF comparisons on the blurred level are issued 32 at a
+//                time and packed into words by a ballot.
+// k_match        one warp per left keypoint: for each right level within one
+//                of the keypoint's level, binary-searches the s0 row band in
+//                the canonical (level, y, x) list (Y is non-decreasing in y),
+//                scans the band with the lanes, and keeps the smallest
+//                (Hamming distance, disparity, index) by a warp min-reduction.
+#include "jslam_internal.h"
+
+namespace jslam {
+
+__global__ void __launch_bounds__(256) k_orient_desc(Batch b)
+{
+    const int img = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const ImageDesc &I = b.images[img];
+    if (i >= *I.count) return;
+    const KpOut &o = I.out;
+    const int lvl = o.level[i], x = o.x[i], y = o.y[i];
+    const LevelDesc &L = b.levels[I.level_base + lvl];
+    const uint8_t *raw = lvl == 0 ? b.in.ptr[img] : L.raw;
+    const int pitch = lvl == 0 ? b.in.pitch[img] : L.pitch;
+
+    int m10 = 0, m01 = 0;
+    if (lane < 2 * kDiskR + 1) {
+        const int dx = lane - kDiskR;
+        const uint8_t *col = raw + (size_t)(y - kDiskR) * pitch + (x + dx);
+        for (int dy = -kDiskR; dy <= kDiskR; ++dy, col += pitch) {
+            if (dx * dx + dy * dy <= kDiskR * kDiskR) {
+                const int v = __ldg(col);
+                m10 += dx * v;
+                m01 += dy * v;
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        m10 += __shfl_xor_sync(0xFFFFFFFFu, m10, off);
+        m01 += __shfl_xor_sync(0xFFFFFFFFu, m01, off);
+    }
+
+    // Sector b is the one whose lower boundary has the moment vector on its
+    // left (cross product >= 0) and whose upper boundary does not.
+    bool left_of = false;
+    if (lane < kBins) {
+        const double t1 = __dmul_rn((double)m01, b.bin_cos[lane]);
+        const double t2 = __dmul_rn((double)m10, b.bin_sin[lane]);
+        left_of = __dsub_rn(t1, t2) >= 0.0;
+    }
+    const uint32_t S = __ballot_sync(0xFFFFFFFFu, left_of) & ((1u << kBins) - 1u);
+    const uint32_t next = (S >> 1) | ((S & 1u) << (kBins - 1));
+    const uint32_t T = S & ~next & ((1u << kBins) - 1u);
+    const bool zero = (m10 == 0 && m01 == 0);
+    const int bin = (zero || T == 0) ? 0 : __ffs(T) - 1;
+
+    const int bpitch = L.blur_pitch;
+    const uint8_t *blur = L.blur + (size_t)y * bpitch + x;
+    const char4 *pat = reinterpret_cast<const char4 *>(b.pattern) + (size_t)bin * kPairs;
+    uint32_t myword = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const char4 pq = __ldg(pat + w * 32 + lane);
+        const int a = __ldg(blur + pq.y * bpitch + pq.x);
+        const int c = __ldg(blur + pq.w * bpitch + pq.z);
+        const uint32_t word = __ballot_sync(0xFFFFFFFFu, a < c);
+        if (lane == w) myword = word;
+    }
+    if (lane < 8) o.desc[(size_t)i * 8 + lane] = myword;
+    if (lane == 0) {
+        o.angle[i] = zero ? 0.0f : atan2f((float)m01, (float)m10);
+        o.angle_bin[i] = (uint8_t)bin;
+    }
+}
+
+cudaError_t launch_orient_desc(const Batch &b, cudaStream_t stream)
+{
+    if (b.n_images == 0 || b.max_capacity == 0) return cudaSuccess;
+    dim3 grid((b.max_capacity + 7) / 8, b.n_images);
+    k_orient_desc<<<grid, 256, 0, stream>>>(b);
+    return cudaGetLastError();
+}
+
+// First index in [lo, hi) whose Y is >= v (Y non-decreasing on the range).
+__device__ __forceinline__ int lower_bound_Y(const uint16_t *Y, int lo, int hi, int v)
+{
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((int)Y[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_match(Batch b)
+{
+    const int pair = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const PairDesc &P = b.pairs[pair];
+    const ImageDesc &Il = b.images[P.left];
+    const ImageDesc &Ir = b.images[P.right];
+    if (i >= *Il.count) return;
+    const KpOut &ol = Il.out, &orr = Ir.out;
+    const int n = ol.level[i];
+    const int X = ol.X[i], Y = ol.Y[i];
+    const int band = b.levels[Il.level_base + n].band;
+    uint32_t dl[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) dl[w] = ol.desc[(size_t)i * 8 + w];
+
+    unsigned long long best = ~0ull;
+    const int m_lo = max(0, n - 1), m_hi = min(Ir.levels - 1, n + 1);
+    for (int m = m_lo; m <= m_hi; ++m) {
+        const int s = Ir.level_start[m], e = Ir.level_start[m + 1];
+        const int a = lower_bound_Y(orr.Y, s, e, Y - band);
+        const int z = lower_bound_Y(orr.Y, a, e, Y + band + 1);
+        for (int j = a + lane; j < z; j += 32) {
+            const int disp = X - (int)orr.X[j];
+            if (disp < 0 || disp > b.prm.max_disp) continue;
+            const uint4 *dr = reinterpret_cast<const uint4 *>(orr.desc + (size_t)j * 8);
+            const uint4 r0 = dr[0], r1 = dr[1];
+            const int d = __popc(dl[0] ^ r0.x) + __popc(dl[1] ^ r0.y) + __popc(dl[2] ^ r0.z) +
+                          __popc(dl[3] ^ r0.w) + __popc(dl[4] ^ r1.x) + __popc(dl[5] ^ r1.y) +
+                          __popc(dl[6] ^ r1.z) + __popc(dl[7] ^ r1.w);
+            const unsigned long long key = ((unsigned long long)d << 48) |
+                                           ((unsigned long long)disp << 32) | (unsigned)j;
+            best = key < best ? key : best;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+        best = other < best ? other : best;
+    }
+    if (lane == 0) {
+        if (best == ~0ull) {
+            P.match_idx[i] = -1; P.disparity[i] = 0; P.dist[i] = 0xFFFF;
+        } else {
+            const int d = (int)(best >> 48);
+            if (d <= b.prm.max_dist) {
+                P.match_idx[i] = (int)(best & 0xFFFFFFFFu);
+                P.disparity[i] = (int16_t)((best >> 32) & 0xFFFFu);
+                P.dist[i] = (uint16_t)d;
+            } else {
+                P.match_idx[i] = -1; P.disparity[i] = 0; P.dist[i] = (uint16_t)d;
+            }
+        }
+    }
+}
+
+cudaError_t launch_match(const Batch &b, cudaStream_t stream)
+{
+    if (b.n_pairs == 0 || b.max_capacity == 0) return cudaSuccess;
+    dim3 grid((b.max_capacity + 7) / 8, b.n_pairs);
+    k_match<<<grid, 256, 0, stream>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace jslam

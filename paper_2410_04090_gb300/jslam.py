@@ -1,0 +1,349 @@
+"""Thin Python binding of libjslam's C ABI (``include/jslam.h``).
+
+Argument marshalling only: every step of the frontend runs in the library's
+CUDA kernels.  Device images are passed as CUDA tensors (uint8, 2-D, rows
+may be strided) and read in place; host images are passed as numpy arrays
+and copied by the library.  PyTorch provides device memory and streams.
+
+The binding never falls back to another implementation: if the compiled
+library is missing it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libjslam.so")
+
+OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_CAPACITY, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
+MEM_DEVICE, MEM_HOST = 0, 1
+
+
+class JslamError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("device", C.c_int32), ("cuda_stream", C.c_void_p),
+                ("max_width", C.c_int32), ("max_height", C.c_int32), ("max_levels", C.c_int32),
+                ("max_feats", C.c_int32), ("max_pairs", C.c_int32), ("fast_thresh_lo", C.c_int32),
+                ("p_min", C.c_int32), ("p_max", C.c_int32), ("k_per_cell", C.c_int32),
+                ("nms_q", C.c_int32), ("border", C.c_int32), ("max_disp", C.c_int32),
+                ("row_band_px", C.c_int32), ("match_max_dist", C.c_int32), ("pfa_rule", C.c_int32)]
+
+
+class Image(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("pitch", C.c_int32),
+                ("memory", C.c_int32), ("data", C.c_void_p)]
+
+
+class StereoJob(C.Structure):
+    _fields_ = [("left", Image), ("right", Image), ("levels", C.c_int32), ("scale", C.c_float),
+                ("fast_thresh", C.c_int32), ("cell", C.c_int32), ("max_feats", C.c_int32)]
+
+
+class Keypoints(C.Structure):
+    _fields_ = [("count", C.c_int32), ("capacity", C.c_int32),
+                ("x", C.c_void_p), ("y", C.c_void_p), ("X", C.c_void_p), ("Y", C.c_void_p),
+                ("level", C.c_void_p), ("angle_bin", C.c_void_p), ("response", C.c_void_p),
+                ("k_levels", C.c_void_p), ("k_resp", C.c_void_p), ("angle", C.c_void_p),
+                ("desc", C.c_void_p)]
+
+
+class Matches(C.Structure):
+    _fields_ = [("count", C.c_int32), ("right_idx", C.c_void_p), ("disparity", C.c_void_p),
+                ("dist", C.c_void_p)]
+
+
+class LevelView(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("raw_pitch", C.c_int32),
+                ("blurred_pitch", C.c_int32), ("raw", C.c_void_p), ("blurred", C.c_void_p)]
+
+
+# (field, numpy dtype, words per keypoint)
+KP_FIELDS = (("x", np.uint16, 1), ("y", np.uint16, 1), ("X", np.uint16, 1), ("Y", np.uint16, 1),
+             ("level", np.uint8, 1), ("angle_bin", np.uint8, 1), ("response", np.uint16, 1),
+             ("k_levels", np.uint8, 1), ("k_resp", np.uint32, 1), ("angle", np.float32, 1),
+             ("desc", np.uint32, 8))
+MATCH_FIELDS = (("right_idx", np.int32), ("disparity", np.int16), ("dist", np.uint16))
+
+# The C-ABI symbols declared in include/jslam.h.
+SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extract_batch", "jslam_match",
+           "jslam_sync", "jslam_get_keypoints", "jslam_get_matches", "jslam_get_level", "jslam_result_bytes",
+           "jslam_download", "jslam_result_view", "jslam_destroy", "jslam_status_str", "jslam_pattern_table",
+           "jslam_level_geometry", "jslam_project", "jslam_match_band", "jslam_enable_stage_timing",
+           "jslam_stage_times")
+STAGES = ("pyramid", "detect", "pfa_nms", "pfa_final", "orb", "match")
+
+_lib = None
+
+
+def lib():
+    """Load libjslam.so (built by ``paper_2410_04090_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2410_04090_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        st = C.c_int
+        L.jslam_default_config.argtypes = [C.POINTER(Config)]
+        L.jslam_default_config.restype = None
+        L.jslam_create.argtypes = [C.POINTER(C.c_void_p), C.POINTER(Config)]
+        L.jslam_create.restype = st
+        L.jslam_extract.argtypes = [C.c_void_p, Image, Image, C.c_int32, C.c_float, C.c_int32, C.c_int32, C.c_int32]
+        L.jslam_extract.restype = st
+        L.jslam_extract_batch.argtypes = [C.c_void_p, C.POINTER(StereoJob), C.c_int32]
+        L.jslam_extract_batch.restype = st
+        L.jslam_match.argtypes = [C.c_void_p]
+        L.jslam_match.restype = st
+        L.jslam_sync.argtypes = [C.c_void_p]
+        L.jslam_sync.restype = st
+        L.jslam_get_keypoints.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(Keypoints)]
+        L.jslam_get_keypoints.restype = st
+        L.jslam_get_matches.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Matches)]
+        L.jslam_get_matches.restype = st
+        L.jslam_get_level.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.POINTER(LevelView)]
+        L.jslam_get_level.restype = st
+        L.jslam_result_bytes.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_size_t)]
+        L.jslam_result_bytes.restype = st
+        L.jslam_download.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t]
+        L.jslam_download.restype = st
+        L.jslam_result_view.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(Keypoints),
+                                        C.POINTER(Matches)]
+        L.jslam_result_view.restype = st
+        L.jslam_destroy.argtypes = [C.c_void_p]
+        L.jslam_destroy.restype = None
+        L.jslam_status_str.argtypes = [C.c_int]
+        L.jslam_status_str.restype = C.c_char_p
+        L.jslam_pattern_table.argtypes = [C.c_void_p]
+        L.jslam_pattern_table.restype = None
+        L.jslam_level_geometry.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_int32,
+                                           C.c_void_p, C.c_void_p, C.c_void_p]
+        L.jslam_level_geometry.restype = st
+        L.jslam_project.argtypes = [C.c_int32, C.c_int32, C.c_float, C.c_int32]
+        L.jslam_project.restype = C.c_int32
+        L.jslam_match_band.argtypes = [C.c_int32, C.c_float, C.c_int32]
+        L.jslam_match_band.restype = C.c_int32
+        L.jslam_enable_stage_timing.argtypes = [C.c_void_p, C.c_int32]
+        L.jslam_enable_stage_timing.restype = st
+        L.jslam_stage_times.argtypes = [C.c_void_p, C.c_void_p]
+        L.jslam_stage_times.restype = st
+        _lib = L
+    return _lib
+
+
+def status_str(s: int) -> str:
+    return lib().jslam_status_str(s).decode()
+
+
+def _check(s: int, what: str):
+    if s != OK:
+        raise JslamError(s, what)
+
+
+# ------------------------------------------------------------ host tables
+
+def pattern_table() -> np.ndarray:
+    out = np.zeros(30 * 256 * 4, np.int8)
+    lib().jslam_pattern_table(out.ctypes.data)
+    return out.reshape(30, 256, 4)
+
+
+def level_geometry(width: int, height: int, levels: int, scale: float, cell: int):
+    w = np.zeros(levels, np.int32); h = np.zeros(levels, np.int32); c = np.zeros(levels, np.int32)
+    _check(lib().jslam_level_geometry(width, height, levels, scale, cell, w.ctypes.data, h.ctypes.data,
+                                      c.ctypes.data), "jslam_level_geometry")
+    return w, h, c
+
+
+def project(v: int, level: int, scale: float, extent: int) -> int:
+    return lib().jslam_project(v, level, scale, extent)
+
+
+def match_band(level: int, scale: float, row_band_px: int) -> int:
+    return lib().jslam_match_band(level, scale, row_band_px)
+
+
+# ------------------------------------------------------------ images
+
+def _image(img) -> Image:
+    """jslam_image of a CUDA tensor (device) or a numpy array (host)."""
+    if isinstance(img, np.ndarray):
+        if img.dtype != np.uint8 or img.ndim != 2 or img.strides[1] != 1:
+            raise ValueError("host image must be a 2-D uint8 array with contiguous rows")
+        return Image(img.shape[1], img.shape[0], img.strides[0], MEM_HOST, img.ctypes.data)
+    import torch
+    if not isinstance(img, torch.Tensor) or img.dtype != torch.uint8 or img.dim() != 2 or img.stride(1) != 1:
+        raise ValueError("device image must be a 2-D uint8 CUDA tensor with contiguous rows")
+    if not img.is_cuda:
+        raise ValueError("tensor images must live on the GPU; pass numpy arrays for host memory")
+    return Image(img.shape[1], img.shape[0], img.stride(0), MEM_DEVICE, img.data_ptr())
+
+
+class _CudaView:
+    """Minimal __cuda_array_interface__ over library-owned device memory."""
+
+    def __init__(self, ptr: int, shape, dtype):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": np.dtype(dtype).str,
+                                         "data": (ptr, False), "version": 3, "strides": None}
+
+
+def _device_view(ptr: int, shape, dtype, device: int):
+    import torch
+    n = int(np.prod(shape))
+    if n == 0 or not ptr:
+        return torch.zeros(shape, dtype=getattr(torch, np.dtype(dtype).name), device=f"cuda:{device}")
+    return torch.as_tensor(_CudaView(ptr, shape, dtype), device=f"cuda:{device}")
+
+
+@dataclass
+class Job:
+    left: object
+    right: object
+    levels: int = 8
+    scale: float = 1.2
+    fast_thresh: int = 20
+    cell: int = 32
+    max_feats: int = 2000
+
+
+class Frontend:
+    """One libjslam context (one device, one stream)."""
+
+    def __init__(self, device: int = 0, stream=None, **config):
+        cfg = Config()
+        lib().jslam_default_config(C.byref(cfg))
+        cfg.device = device
+        if stream is not None:
+            cfg.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
+        for k, v in config.items():
+            if k not in {f[0] for f in Config._fields_}:
+                raise TypeError(f"unknown config field {k!r}")
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        self.device = device
+        h = C.c_void_p()
+        _check(lib().jslam_create(C.byref(h), C.byref(cfg)), "jslam_create")
+        self._h = h
+        self._keep = ()
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().jslam_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- enqueue
+    def extract(self, left, right, levels=8, scale=1.2, fast_thresh=20, cell=32, max_feats=2000):
+        li, ri = _image(left), _image(right)
+        self._keep = (left, right)
+        _check(lib().jslam_extract(self._h, li, ri, levels, scale, fast_thresh, cell, max_feats), "jslam_extract")
+
+    def extract_batch(self, jobs):
+        arr = (StereoJob * len(jobs))()
+        for i, j in enumerate(jobs):
+            arr[i] = StereoJob(_image(j.left), _image(j.right), j.levels, j.scale, j.fast_thresh, j.cell, j.max_feats)
+        self._keep = tuple(jobs)
+        _check(lib().jslam_extract_batch(self._h, arr, len(jobs)), "jslam_extract_batch")
+
+    def match(self):
+        _check(lib().jslam_match(self._h), "jslam_match")
+
+    def sync(self):
+        _check(lib().jslam_sync(self._h), "jslam_sync")
+
+    def enable_stage_timing(self, on: bool = True):
+        _check(lib().jslam_enable_stage_timing(self._h, int(on)), "jslam_enable_stage_timing")
+
+    def stage_times(self) -> dict:
+        """Milliseconds per stage of the last extraction (+ match), after sync."""
+        ms = np.zeros(len(STAGES), np.float32)
+        _check(lib().jslam_stage_times(self._h, ms.ctypes.data), "jslam_stage_times")
+        return dict(zip(STAGES, ms.tolist()))
+
+    # -- device views
+    def keypoints(self, pair: int = 0, side: int = 0) -> dict:
+        kp = Keypoints()
+        _check(lib().jslam_get_keypoints(self._h, pair, side, C.byref(kp)), "jslam_get_keypoints")
+        n = max(kp.count, 0)
+        out = {"count": kp.count}
+        for name, dt, words in KP_FIELDS:
+            shape = (n, words) if words > 1 else (n,)
+            out[name] = _device_view(getattr(kp, name), shape, dt, self.device)
+        return out
+
+    def matches(self, pair: int = 0) -> dict:
+        m = Matches()
+        _check(lib().jslam_get_matches(self._h, pair, C.byref(m)), "jslam_get_matches")
+        n = max(m.count, 0)
+        out = {"count": m.count}
+        for name, dt in MATCH_FIELDS:
+            out[name] = _device_view(getattr(m, name), (n,), dt, self.device)
+        return out
+
+    def level(self, pair: int, side: int, level: int) -> dict:
+        v = LevelView()
+        _check(lib().jslam_get_level(self._h, pair, side, level, C.byref(v)), "jslam_get_level")
+        raw = _device_view(v.raw, (v.height, v.raw_pitch), np.uint8, self.device)[:, : v.width]
+        blur = _device_view(v.blurred, (v.height, v.blurred_pitch), np.uint8, self.device)[:, : v.width]
+        return {"raw": raw, "blurred": blur}
+
+    # -- host results
+    def result_bytes(self, pair: int = 0) -> int:
+        n = C.c_size_t()
+        _check(lib().jslam_result_bytes(self._h, pair, C.byref(n)), "jslam_result_bytes")
+        return n.value
+
+    def download(self, pair: int, dst) -> None:
+        """Enqueue the copy of pair `pair`'s result block into `dst` (a pinned
+        CPU tensor or a numpy array of at least result_bytes bytes)."""
+        if isinstance(dst, np.ndarray):
+            ptr, size = dst.ctypes.data, dst.nbytes
+        else:
+            ptr, size = dst.data_ptr(), dst.numel() * dst.element_size()
+        _check(lib().jslam_download(self._h, pair, ptr, size), "jslam_download")
+
+    def result_view(self, pair: int, block, side: int) -> dict:
+        """Host arrays (copies) of one side of a downloaded result block."""
+        if isinstance(block, np.ndarray):
+            base = block.ctypes.data
+        else:
+            base = block.data_ptr()
+        kp = Keypoints(); m = Matches()
+        _check(lib().jslam_result_view(self._h, pair, base, side, C.byref(kp), C.byref(m)), "jslam_result_view")
+        n = max(kp.count, 0)
+        out = {"count": kp.count}
+        for name, dt, words in KP_FIELDS:
+            buf = (C.c_char * (n * words * np.dtype(dt).itemsize)).from_address(getattr(kp, name)) if n else b""
+            a = np.frombuffer(buf, dtype=dt).copy() if n else np.zeros(0, dt)
+            out[name] = a.reshape(n, words) if words > 1 else a
+        if side == 0 and m.count >= 0:
+            for name, dt in MATCH_FIELDS:
+                buf = (C.c_char * (n * np.dtype(dt).itemsize)).from_address(getattr(m, name)) if n else b""
+                out["match_" + name] = np.frombuffer(buf, dtype=dt).copy() if n else np.zeros(0, dt)
+        return out
+
+
+def to_numpy(d: dict) -> dict:
+    """Copy a dict of device views to host numpy arrays."""
+    out = {}
+    for k, v in d.items():
+        out[k] = v.cpu().numpy() if hasattr(v, "cpu") else v
+    return out

@@ -25,6 +25,7 @@ x + d, so disparity d = x_left - x_right >= 0.
 from __future__ import annotations
 
 from dataclasses import dataclass
+from functools import lru_cache
 
 import numpy as np
 
@@ -122,6 +123,7 @@ def checker_pair(width: int, height: int, seed: int, disparity: int = 16,
     return StereoPair(_finish(left, rng, sigma), _finish(right, rng, sigma), d)
 
 
+@lru_cache(maxsize=8)
 def _planes_world(width: int, height: int, world_seed: int, max_disp: int = 96, boxes: int = 20):
     rng = _rng(world_seed)
     margin = max_disp + 64
@@ -169,15 +171,16 @@ def planes_pair(width: int, height: int, frame: int, world_seed: int, frame_seed
         img = np.where(base_tex == 1, sample(ground, lx, ys), sample(far, xs, ys))
         dist = np.where(base_tex == 1, dmap, 0)
         for (bx, by, bw, bh, bd, tex) in boxes:
-            lxb = xs + view_shift_sign * bd
-            inside = (lxb >= bx) & (lxb < bx + bw) & (ys >= by) & (ys < by + bh)
-            if not inside.any():
+            # columns of this view that see the box (left x in [bx, bx + bw))
+            c0 = max(bx - view_shift_sign * bd, 0)
+            c1 = min(bx + bw - view_shift_sign * bd, width)
+            r0, r1 = by, min(by + bh, height)
+            if c0 >= c1 or r0 >= r1:
                 continue
-            yy = np.clip(ys - by, 0, bh - 1)
-            xx = np.clip(lxb - bx, 0, tex.shape[1] - 2)
-            val = sample(tex, xx, yy)
-            img = np.where(inside, val, img)
-            dist = np.where(inside, bd, dist)
+            sub_x = xs[r0:r1, c0:c1] + view_shift_sign * bd - bx
+            sub_y = ys[r0:r1, c0:c1] - by
+            img[r0:r1, c0:c1] = sample(tex, np.clip(sub_x, 0, tex.shape[1] - 2), sub_y)
+            dist[r0:r1, c0:c1] = bd
         return img, dist
 
     left, dl = render(0)

@@ -1,0 +1,63 @@
+"""The C-ABI library loads and exports every symbol of include/jslam.h, and
+its host-built tables (no device work) equal the oracle's, which derives
+them again from the same written definitions."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def jslam():
+    from paper_2410_04090_gb300 import build
+    build.build()
+    from paper_2410_04090_gb300 import jslam as J
+    return J
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "jslam.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(jslam_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(jslam):
+    declared = _declared_functions()
+    assert len(declared) >= 15
+    lib = jslam.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(jslam.SYMBOLS) == declared
+
+
+def test_status_strings(jslam):
+    for s in (0, -1, -2, -3, -4, -5, -6):
+        assert jslam.status_str(s)
+
+
+def test_pattern_table_matches_oracle(jslam, oracle):
+    assert np.array_equal(jslam.pattern_table(), oracle.pattern_rotated())
+
+
+@pytest.mark.parametrize("W0,H0,levels,cell", [(1241, 376, 8, 32), (752, 480, 8, 32), (1920, 1080, 8, 32),
+                                               (640, 480, 1, 32), (203, 157, 3, 7), (333, 290, 5, 15)])
+def test_geometry_projection_band_match_oracle(jslam, oracle, W0, H0, levels, cell):
+    w, h, c = jslam.level_geometry(W0, H0, levels, 1.2, cell)
+    ow, oh, oc = oracle.level_geometry(W0, H0, levels, 1.2, cell)
+    assert np.array_equal(w, ow) and np.array_equal(h, oh) and np.array_equal(c, oc)
+    for n in range(levels):
+        for v in range(0, int(w[n]), 3):
+            assert jslam.project(v, n, 1.2, W0) == oracle.project(v, n, 1.2, W0)
+        for v in range(0, int(h[n]), 3):
+            assert jslam.project(v, n, 1.2, H0) == oracle.project(v, n, 1.2, H0)
+        assert jslam.match_band(n, 1.2, 2) == oracle.match_band(n, 1.2, 2)
+
+
+def test_other_scales(jslam, oracle):
+    for scale in (1.1, 1.25, 1.5, 2.0):
+        w, h, c = jslam.level_geometry(999, 777, 6, scale, 40)
+        ow, oh, oc = oracle.level_geometry(999, 777, 6, scale, 40)
+        assert np.array_equal(w, ow) and np.array_equal(h, oh) and np.array_equal(c, oc)

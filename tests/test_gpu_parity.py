@@ -1,0 +1,241 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle: bit-exact
+keypoints, scores, sectors, descriptors and matches, angles within 1e-4 rad.
+Sizes span several tiles with ragged edges; the full workload shapes are
+compared in full (the oracle finishes them in seconds)."""
+import numpy as np
+import pytest
+
+from paper_2410_04090_gb300 import scenes
+from parity_util import compare_keypoints, compare_matches, frontend_for, gpu_pair, params_from
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def J():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_04090_gb300 import build
+    build.build()
+    from paper_2410_04090_gb300 import jslam
+    return jslam
+
+
+def _check_pair(J, oracle, left, right, p, host=False, fe=None):
+    own = fe is None
+    fe = fe or frontend_for(J, p)
+    try:
+        kl, kr, m = gpu_pair(J, fe, left, right, p, host=host)
+    finally:
+        if own:
+            fe.close()
+    ol, orr, om = oracle.extract_pair(left, right, p)
+    compare_keypoints(kl, ol, "left")
+    compare_keypoints(kr, orr, "right")
+    compare_matches(m, om, "matches")
+    return ol, orr, om
+
+
+def test_small_ragged_multilevel(J, oracle):
+    pair = scenes.planes_pair(203, 157, 0, 31, 32)
+    p = params_from(oracle, levels=3, max_feats=500, cell=16)
+    ol, _, _ = _check_pair(J, oracle, pair.left, pair.right, p)
+    assert ol["count"] > 20
+
+
+def test_pyramid_levels_match_oracle(J, oracle):
+    import torch
+    pair = scenes.planes_pair(317, 251, 0, 5, 6)
+    p = params_from(oracle, levels=6, max_feats=1000)
+    fe = frontend_for(J, p)
+    l = torch.from_numpy(pair.left).cuda(); r = torch.from_numpy(pair.right).cuda()
+    fe.extract(l, r, p.levels, p.scale, p.fast_thresh, p.cell, p.max_feats)
+    fe.sync()
+    for side, img in ((0, pair.left), (1, pair.right)):
+        for n in range(p.levels):
+            lv = fe.level(0, side, n)
+            raw = lv["raw"].cpu().numpy()
+            want = img if n == 0 else oracle.pyramid_level(img, p.scale, n)
+            assert np.array_equal(raw, want), (side, n)
+            assert np.array_equal(lv["blurred"].cpu().numpy(), oracle.blur(want)), (side, n)
+    fe.close()
+
+
+@pytest.mark.parametrize("name", ["single_640x480_L1", "kitti_1241x376_L8", "euroc_752x480_L8"])
+def test_workload_parity(J, oracle, name):
+    w = scenes.WORKLOADS[name]
+    pair = scenes.workload_pair(name, 1)
+    p = params_from(oracle, levels=w["levels"], max_feats=w["max_feats"], fast_thresh=w["fast_thresh"],
+                    fast_thresh_lo=w["fast_thresh_lo"])
+    ol, orr, om = _check_pair(J, oracle, pair.left, pair.right, p)
+    assert ol["count"] > 100 and (om[0] >= 0).sum() > 50
+
+
+def test_full_hd_parity(J, oracle):
+    w = scenes.WORKLOADS["fhd_1920x1080_L8"]
+    pair = scenes.workload_pair("fhd_1920x1080_L8", 0)
+    p = params_from(oracle, levels=8, max_feats=w["max_feats"], fast_thresh_lo=7)
+    _check_pair(J, oracle, pair.left, pair.right, p)
+
+
+def test_host_memory_input(J, oracle):
+    pair = scenes.workload_pair("kitti_1241x376_L8", 2)
+    p = params_from(oracle, levels=8, max_feats=2000, fast_thresh_lo=7)
+    _check_pair(J, oracle, pair.left, pair.right, p, host=True)
+
+
+def test_strided_device_input(J, oracle):
+    import torch
+    pair = scenes.planes_pair(300, 200, 0, 41, 42)
+    p = params_from(oracle, levels=4, max_feats=400)
+    fe = frontend_for(J, p)
+    big_l = torch.zeros((200, 384), dtype=torch.uint8, device="cuda")
+    big_r = torch.zeros((200, 384), dtype=torch.uint8, device="cuda")
+    big_l[:, :300] = torch.from_numpy(pair.left).cuda()
+    big_r[:, :300] = torch.from_numpy(pair.right).cuda()
+    fe.extract(big_l[:, :300], big_r[:, :300], p.levels, p.scale, p.fast_thresh, p.cell, p.max_feats)
+    fe.match(); fe.sync()
+    from paper_2410_04090_gb300 import jslam
+    ol, orr, om = oracle.extract_pair(pair.left, pair.right, p)
+    compare_keypoints(jslam.to_numpy(fe.keypoints(0, 0)), ol, "left")
+    compare_matches(jslam.to_numpy(fe.matches(0)), om)
+    fe.close()
+
+
+@pytest.mark.parametrize("kw", [
+    dict(k_per_cell=3),
+    dict(nms_q=5),
+    dict(nms_q=1),
+    dict(pfa_rule=1),
+    dict(p_max=16),            # classic FAST (Eq. 2) as the unbounded special case
+    dict(p_min=12, p_max=14),
+    dict(cell=7),
+    dict(cell=100),
+    dict(max_feats=5),         # cap binds hard; ties resolved in canonical order
+    dict(fast_thresh=8, fast_thresh_lo=3),
+    dict(fast_thresh=60, fast_thresh_lo=25),
+    dict(border=25),
+    dict(scale=1.5, levels=4),
+    dict(match_max_dist=30, max_disp=40, row_band_px=0),
+])
+def test_parameter_variants(J, oracle, kw):
+    pair = scenes.planes_pair(420, 300, 0, 77, 78)
+    base = dict(levels=5, max_feats=800)
+    base.update(kw)
+    p = params_from(oracle, **base)
+    _check_pair(J, oracle, pair.left, pair.right, p)
+
+
+def test_minimum_size_levels(J, oracle):
+    # the deepest level is exactly 2 * border + 1 pixels on its short side
+    W0 = H0 = int(np.ceil(39 * 1.2 ** 3))
+    p = params_from(oracle, levels=4, max_feats=200, cell=8)
+    while not oracle.check_params(W0, H0, p):
+        W0 += 1; H0 += 1
+    pair = scenes.planes_pair(W0, H0, 0, 3, 4)
+    _check_pair(J, oracle, pair.left, pair.right, p)
+
+
+def test_flat_image_has_no_keypoints(J, oracle):
+    flat = np.full((120, 160), 128, np.uint8)
+    p = params_from(oracle, levels=2, max_feats=100)
+    ol, _, om = _check_pair(J, oracle, flat, flat, p)
+    assert ol["count"] == 0 and len(om[0]) == 0
+
+
+def test_repeated_calls_reuse_buffers(J, oracle):
+    p = params_from(oracle, levels=8, max_feats=2000, fast_thresh_lo=7)
+    fe = frontend_for(J, p)
+    try:
+        for f in (0, 1, 0):
+            pair = scenes.workload_pair("kitti_1241x376_L8", f)
+            _check_pair(J, oracle, pair.left, pair.right, p, fe=fe)
+        # a different shape on the same context, then back
+        small = scenes.planes_pair(300, 240, 0, 9, 10)
+        _check_pair(J, oracle, small.left, small.right, params_from(oracle, levels=4, max_feats=2000,
+                                                                     fast_thresh_lo=7), fe=fe)
+        pair = scenes.workload_pair("kitti_1241x376_L8", 3)
+        _check_pair(J, oracle, pair.left, pair.right, p, fe=fe)
+    finally:
+        fe.close()
+
+
+def test_mixed_batch(J, oracle):
+    """Several stereo pairs of different sizes and depths in one launch set."""
+    import torch
+    specs = [(640, 480, "checker", 4, 1000), (752, 480, "euroc", 5, 1200), (1241, 376, "planes", 6, 2000),
+             (500, 300, "planes", 8, 700), (640, 480, "checker", 1, 300)]
+    p0 = params_from(oracle, fast_thresh_lo=7)
+    fe = frontend_for(J, p0, max_pairs=8)
+    jobs, pairs = [], []
+    from paper_2410_04090_gb300 import jslam
+    for i, (w, h, kind, lv, mf) in enumerate(specs):
+        pr = scenes.stereo_pair(kind, w, h, frame=i, stream=i, config_id=4)
+        pairs.append((pr, lv, mf))
+        jobs.append(jslam.Job(torch.from_numpy(pr.left).cuda(), torch.from_numpy(pr.right).cuda(), lv, 1.2, 20, 32, mf))
+    fe.extract_batch(jobs)
+    fe.match()
+    fe.sync()
+    for i, (pr, lv, mf) in enumerate(pairs):
+        p = params_from(oracle, levels=lv, max_feats=mf, fast_thresh_lo=7)
+        ol, orr, om = oracle.extract_pair(pr.left, pr.right, p)
+        compare_keypoints(jslam.to_numpy(fe.keypoints(i, 0)), ol, f"pair {i} left")
+        compare_keypoints(jslam.to_numpy(fe.keypoints(i, 1)), orr, f"pair {i} right")
+        compare_matches(jslam.to_numpy(fe.matches(i)), om, f"pair {i}")
+    fe.close()
+
+
+def test_download_result_block(J, oracle):
+    import torch
+    pair = scenes.workload_pair("euroc_752x480_L8", 3)
+    p = params_from(oracle, levels=8, max_feats=1200, fast_thresh_lo=7)
+    fe = frontend_for(J, p)
+    fe.extract(pair.left, pair.right, p.levels, p.scale, p.fast_thresh, p.cell, p.max_feats)
+    fe.match()
+    buf = torch.empty(fe.result_bytes(0), dtype=torch.uint8).pin_memory()
+    fe.download(0, buf)
+    fe.sync()
+    ol, orr, om = oracle.extract_pair(pair.left, pair.right, p)
+    left = fe.result_view(0, buf, 0)
+    compare_keypoints(left, ol, "left")
+    compare_keypoints(fe.result_view(0, buf, 1), orr, "right")
+    compare_matches({"count": left["count"], "right_idx": left["match_right_idx"],
+                     "disparity": left["match_disparity"], "dist": left["match_dist"]}, om)
+    fe.close()
+
+
+def test_argument_errors(J):
+    import torch
+    fe = J.Frontend(device=0, max_width=640, max_height=480, max_levels=4, max_feats=500, max_pairs=2)
+    img = torch.zeros((100, 120), dtype=torch.uint8, device="cuda")
+    bad = [dict(levels=0), dict(levels=5), dict(scale=1.0), dict(fast_thresh=0), dict(fast_thresh=255),
+           dict(cell=0), dict(cell=129), dict(max_feats=0), dict(max_feats=501)]
+    for kw in bad:
+        args = dict(levels=2, scale=1.2, fast_thresh=20, cell=32, max_feats=100)
+        args.update(kw)
+        with pytest.raises(J.JslamError) as e:
+            fe.extract(img, img, **args)
+        assert e.value.status == J.ERR_ARG, kw
+    tiny = torch.zeros((45, 60), dtype=torch.uint8, device="cuda")  # level 1 is 38 rows < 2 * 19 + 1
+    with pytest.raises(J.JslamError) as e:
+        fe.extract(tiny, tiny, 2, 1.2, 20, 32, 100)
+    assert e.value.status == J.ERR_ARG
+    fe.extract(tiny, tiny, 1, 1.2, 20, 32, 100)
+    big = torch.zeros((481, 100), dtype=torch.uint8, device="cuda")
+    with pytest.raises(J.JslamError):
+        fe.extract(big, big, 1, 1.2, 20, 32, 100)
+    with pytest.raises(J.JslamError) as e:
+        fe.extract(img, img[:, :110], 1, 1.2, 20, 32, 100)  # left/right sizes differ
+    assert e.value.status == J.ERR_ARG
+    fresh = J.Frontend(device=0)
+    with pytest.raises(J.JslamError) as e:
+        fresh.match()
+    assert e.value.status == J.ERR_STATE
+    with pytest.raises(J.JslamError) as e:
+        J.Frontend(device=0, p_min=10, p_max=9)
+    assert e.value.status == J.ERR_ARG
+    # a rejected call leaves the context usable
+    fe.extract(img, img, 2, 1.2, 20, 32, 100)
+    fe.sync()
+    fe.close(); fresh.close()
