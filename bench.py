@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--mode", choices=["batched", "plain"], default="batched")
     ap.add_argument("--cpu-pairs", type=int, default=12, help="pairs in the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="time the batched mode only (no plain mode, no e2e): the launch sequence ncu captures")
     return ap.parse_args()
 
 
@@ -276,7 +278,8 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     lefts = [torch.from_numpy(f.left).to(dev) for f in frames]
     rights = [torch.from_numpy(f.right).to(dev) for f in frames]
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)  # torch work (flush, events) and the library share this stream
     fe = jslam.Frontend(device=dev.index, stream=stream, max_width=W0, max_height=H0, max_levels=8,
                         max_feats=jp["max_feats"], max_pairs=args.frames, fast_thresh_lo=w["fast_thresh_lo"])
     jobs = [jslam.Job(l, r, **jp) for l, r in zip(lefts, rights)]
@@ -307,6 +310,9 @@ def main():
         return total  # ms
 
     modes = {"batched": step_batched, "plain": step_plain}
+    if args.only_batched:
+        args.mode = "batched"
+        modes = {"batched": step_batched}
     main_step = modes[args.mode]
     for _ in range(args.warmup):
         for s in modes.values():
@@ -329,7 +335,7 @@ def main():
         total_ms = timed(main_step, args.steps, grab)
     fe.enable_stage_timing(False)
     other = "plain" if args.mode == "batched" else "batched"
-    other_ms = timed(modes[other], args.steps)
+    other_ms = timed(modes[other], args.steps) if other in modes else float("nan")
 
     t = torch.tensor([total_ms, other_ms], dtype=torch.float64, device=dev)
     if dist:
@@ -337,13 +343,28 @@ def main():
     total_ms, other_ms = t.tolist()
     pairs = args.frames * args.steps * world
     value = pairs / (total_ms / 1e3)
-    mode_values = {args.mode: value, other: pairs / (other_ms / 1e3)}
+    mode_values = {args.mode: value}
+    if other in modes:
+        mode_values[other] = pairs / (other_ms / 1e3)
 
     # keypoint counts of the last batch (for algorithmic bytes)
     fe.extract_batch(jobs); fe.match(); fe.sync()
     counts = [fe.keypoints(p, s)["count"] for p in range(args.frames) for s in (0, 1)]
 
     # end to end: pinned host images through the C ABI, result blocks back
+    e2e_value, h2d, d2h = None, 0, 0
+    if not args.only_batched:
+        e2e_value, h2d, d2h = run_e2e(args, fe, frames, jp, jslam, torch, dist, dev, pairs)
+    if rank == 0:
+        emit(args, world, value, total_ms, mode_values, stage_acc, counts, W0, H0, jp, frames, w, e2e_value,
+             h2d, d2h, clocks)
+    fe.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(args, fe, frames, jp, jslam, torch, dist, dev, pairs):
     host_l = [torch.from_numpy(f.left).pin_memory() for f in frames]
     host_r = [torch.from_numpy(f.right).pin_memory() for f in frames]
     hjobs = [jslam.Job(l.numpy(), r.numpy(), **jp) for l, r in zip(host_l, host_r)]
@@ -372,40 +393,41 @@ def main():
     e2e_value = pairs / te.item()
     h2d = sum(f.left.nbytes + f.right.nbytes for f in frames)
     d2h = sum(rb)
+    return e2e_value, h2d, d2h
 
-    if rank == 0:
-        peak, peak_kind = measured_peaks()
-        stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
-        roof = None
-        if args.mode == "batched" and any(stage_ms.values()):
-            dom = max((k for k in stage_ms if algorithmic_bytes(k, W0, H0, jp, 1, [1]) is not None),
-                      key=lambda k: stage_ms[k])
-            alg = algorithmic_bytes(dom, W0, H0, jp, args.frames, counts)
-            ach = alg / (stage_ms[dom] / 1e3) / 1e9
-            roof = {"bound": "hbm", "kernel": KERNELS[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                    "algorithmic_bytes_per_launch": alg,
-                    "traffic": profiled_traffic(KERNELS[dom], args.workload),
-                    "stage_ms_per_launch": stage_ms}
-        cpu = None if args.no_cpu_baseline else cpu_baseline(args, frames, jp, w)
-        launches_per_call = 6
-        gpu_launches = launches_per_call * args.steps * (1 if args.mode == "batched" else args.frames)
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-                "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
-                           "frames_per_step": args.frames, "mode": args.mode,
-                           "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
-                "modes": mode_values,
-                "roofline": roof, "cpu_baseline": cpu,
-                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "clocks": clocks.summary(), "gpu_launches": gpu_launches,
-                "keypoints_per_image_mean": float(np.mean(counts))}
-        print(json.dumps(line), flush=True)
-    fe.close()
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+
+def emit(args, world, value, total_ms, mode_values, stage_acc, counts, W0, H0, jp, frames, w, e2e_value, h2d,
+     d2h, clocks):
+    import numpy as np
+    peak, peak_kind = measured_peaks()
+    stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
+    roof = None
+    if args.mode == "batched" and any(stage_ms.values()):
+        dom = max((k for k in stage_ms if algorithmic_bytes(k, W0, H0, jp, 1, [1]) is not None),
+                  key=lambda k: stage_ms[k])
+        alg = algorithmic_bytes(dom, W0, H0, jp, args.frames, counts)
+        ach = alg / (stage_ms[dom] / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": KERNELS[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                "algorithmic_bytes_per_launch": alg,
+                "traffic": profiled_traffic(KERNELS[dom], args.workload),
+                "stage_ms_per_launch": stage_ms}
+    cpu = None if args.no_cpu_baseline else cpu_baseline(args, frames, jp, w)
+    launches_per_call = 6
+    gpu_launches = launches_per_call * args.steps * (1 if args.mode == "batched" else args.frames)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
+                       "frames_per_step": args.frames, "mode": args.mode,
+                       "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
+            "modes": mode_values,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": None if e2e_value is None else
+                   {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clocks.summary(), "gpu_launches": gpu_launches,
+            "keypoints_per_image_mean": float(np.mean(counts))}
+    print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

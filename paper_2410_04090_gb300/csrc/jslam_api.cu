@@ -575,11 +575,17 @@ jslam_status jslam_extract_batch(jslam_ctx *ctx, const jslam_stereo_job *jobs, i
         }
     }
     cudaError_t e;
-    if ((e = launch_pyramid(b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
-    if ((e = launch_fast_cull(b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
-    if ((e = launch_pfa_nms(b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
-    if ((e = launch_pfa_finalize(b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
-    if ((e = launch_orient_desc(b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    cudaError_t (*const stages[])(const Batch &, cudaStream_t) = {
+        launch_pyramid, launch_fast_cull, launch_pfa_nms, launch_pfa_finalize, launch_orient_desc };
+    for (bool &d : ctx->stage_done) d = false;
+    if (ctx->timing && (e = cudaEventRecord(ctx->events[0], ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    for (int i = 0; i < JSLAM_STAGE_MATCH; ++i) {
+        if ((e = stages[i](b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
+        if (ctx->timing) {
+            if ((e = cudaEventRecord(ctx->events[i + 1], ctx->stream)) != cudaSuccess) return fail(ctx, e);
+            ctx->stage_done[i] = true;
+        }
+    }
     ctx->have_extract = true;
     ctx->have_match = false;
     ctx->synced = false;

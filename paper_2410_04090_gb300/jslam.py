@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libjslam.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOMEM, ERR_CAPACITY, ERR_TIMEOUT, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 MEM_DEVICE, MEM_HOST = 0, 1
+CUDA_STREAM_LEGACY = 0x1  # cudaStreamLegacy
 
 
 class JslamError(RuntimeError):
@@ -221,7 +222,10 @@ class Frontend:
         lib().jslam_default_config(C.byref(cfg))
         cfg.device = device
         if stream is not None:
-            cfg.cuda_stream = stream if isinstance(stream, int) else stream.cuda_stream
+            handle = stream if isinstance(stream, int) else stream.cuda_stream
+            # handle 0 is the legacy default stream; NULL in the config means
+            # "create a stream", so name the legacy stream explicitly
+            cfg.cuda_stream = handle if handle else CUDA_STREAM_LEGACY
         for k, v in config.items():
             if k not in {f[0] for f in Config._fields_}:
                 raise TypeError(f"unknown config field {k!r}")

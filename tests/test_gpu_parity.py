@@ -239,3 +239,49 @@ def test_argument_errors(J):
     fe.extract(img, img, 2, 1.2, 20, 32, 100)
     fe.sync()
     fe.close(); fresh.close()
+
+
+def test_stage_timing(J, oracle):
+    import torch
+    pair = scenes.workload_pair("kitti_1241x376_L8", 0)
+    p = params_from(oracle, levels=8, max_feats=2000, fast_thresh_lo=7)
+    fe = frontend_for(J, p)
+    with pytest.raises(J.JslamError):
+        fe.stage_times()
+    fe.enable_stage_timing(True)
+    l = torch.from_numpy(pair.left).cuda(); r = torch.from_numpy(pair.right).cuda()
+    fe.extract(l, r, p.levels, p.scale, p.fast_thresh, p.cell, p.max_feats)
+    fe.match()
+    fe.sync()
+    t = fe.stage_times()
+    assert set(t) == set(J.STAGES) and all(v > 0 for v in t.values()), t
+    fe.enable_stage_timing(False)
+    fe.close()
+
+
+def test_shared_torch_streams(J, oracle):
+    """The context runs on a stream the caller passes, including torch's
+    default stream; events on that stream bracket the library's work."""
+    import torch
+    pair = scenes.workload_pair("kitti_1241x376_L8", 4)
+    p = params_from(oracle, levels=8, max_feats=2000, fast_thresh_lo=7)
+    ol, orr, om = oracle.extract_pair(pair.left, pair.right, p)
+    from paper_2410_04090_gb300 import jslam
+    for stream in (torch.cuda.default_stream(), torch.cuda.Stream()):
+        fe = J.Frontend(device=0, stream=stream, max_width=1241, max_height=376, max_feats=2000,
+                        fast_thresh_lo=7, max_pairs=1)
+        fe.enable_stage_timing(True)
+        with torch.cuda.stream(stream):
+            l = torch.from_numpy(pair.left).cuda(); r = torch.from_numpy(pair.right).cuda()
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fe.extract(l, r, p.levels, p.scale, p.fast_thresh, p.cell, p.max_feats)
+            fe.match()
+            e1.record(stream)
+        e1.synchronize()  # no jslam_sync: the event alone must cover the work
+        t = fe.stage_times()
+        assert e0.elapsed_time(e1) >= 0.9 * sum(t.values())
+        fe.sync()
+        compare_keypoints(jslam.to_numpy(fe.keypoints(0, 0)), ol, "left")
+        compare_matches(jslam.to_numpy(fe.matches(0)), om)
+        fe.close()
