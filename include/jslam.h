@@ -214,6 +214,39 @@ jslam_status jslam_enable_stage_timing(jslam_ctx *ctx, int32_t enable);
  * Valid after jslam_sync(); JSLAM_ERR_STATE if timing was off. */
 jslam_status jslam_stage_times(jslam_ctx *ctx, float *ms /* JSLAM_NUM_STAGES entries */);
 
+/* PFA scores of one image's culled corners, computed without allocating
+ * device memory.  No counterpart in the paper: it exists for callers that
+ * cannot call cudaMalloc -- a real-time loop that forbids allocation after
+ * start-up, a plug-in running inside another framework's enqueue hook, a
+ * process whose device memory comes from a fixed pool.
+ *
+ * For the n corners (level[i], x[i], y[i], response[i]) (device arrays, level
+ * coordinates, distinct (level, x, y), level < levels, response <= 4080) it
+ * writes, per corner, its s0 projection X[i], Y[i], the number of levels
+ * k_levels[i] and summed response k_resp[i] at that s0 pixel, and alive[i] =
+ * 1 when no occupied pixel of the nms_q x nms_q window dominates it (pfa_rule
+ * as in jslam_config) -- the k_levels / k_resp that jslam_extract reports for
+ * the corners it keeps.  Outputs are device arrays of n entries, owned by the
+ * caller.  Runs asynchronously on `cuda_stream` (NULL: legacy default stream)
+ * of `device`; the calling thread's current device is restored on return.
+ *
+ * Scratch: a 256 KB table in a statically allocated device array that every
+ * GPU loading the library holds until the process exits.  Every call clears
+ * and reuses it, so calls whose work overlaps on a GPU race and give wrong
+ * results: serialise them (one stream, or events).  The first call on a
+ * device looks up the table's device address; make that first call before
+ * any stream capture.  Nothing is allocated, ever.
+ *
+ * JSLAM_ERR_CAPACITY when n > 16384; JSLAM_ERR_ARG for a null array with
+ * n > 0, a size outside 1..4096, levels outside 1..8, scale <= 1, nms_q not
+ * odd in 1..7, a bad rule or device; JSLAM_ERR_CUDA if the table's address
+ * or the launch fails.  n == 0 returns JSLAM_OK without work. */
+jslam_status jslam_pfa_scores_static(const uint8_t *level, const uint16_t *x, const uint16_t *y,
+                                     const uint16_t *response, int32_t n, int32_t width0, int32_t height0,
+                                     int32_t levels, float scale, int32_t nms_q, int32_t pfa_rule,
+                                     uint16_t *X, uint16_t *Y, uint8_t *k_levels, uint32_t *k_resp,
+                                     uint8_t *alive, int32_t device, void *cuda_stream);
+
 /* Release the context and everything it owns.  NULL is ignored. */
 void jslam_destroy(jslam_ctx *ctx);
 

@@ -79,7 +79,7 @@ SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extra
            "jslam_sync", "jslam_get_keypoints", "jslam_get_matches", "jslam_get_level", "jslam_result_bytes",
            "jslam_download", "jslam_result_view", "jslam_destroy", "jslam_status_str", "jslam_pattern_table",
            "jslam_level_geometry", "jslam_project", "jslam_match_band", "jslam_enable_stage_timing",
-           "jslam_stage_times")
+           "jslam_stage_times", "jslam_pfa_scores_static")
 STAGES = ("pyramid", "detect", "pfa_nms", "pfa_final", "orb", "match")
 
 _lib = None
@@ -135,6 +135,10 @@ def lib():
         L.jslam_enable_stage_timing.restype = st
         L.jslam_stage_times.argtypes = [C.c_void_p, C.c_void_p]
         L.jslam_stage_times.restype = st
+        vp = C.c_void_p
+        L.jslam_pfa_scores_static.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                              C.c_float, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, C.c_int32, vp]
+        L.jslam_pfa_scores_static.restype = st
         _lib = L
     return _lib
 
@@ -169,6 +173,29 @@ def project(v: int, level: int, scale: float, extent: int) -> int:
 
 def match_band(level: int, scale: float, row_band_px: int) -> int:
     return lib().jslam_match_band(level, scale, row_band_px)
+
+
+# ------------------------------------------------------------ no-allocation PFA scores
+
+def pfa_scores_static(level, x, y, response, width0: int, height0: int, levels: int, scale: float = 1.2,
+                      nms_q: int = 3, pfa_rule: int = 0, stream=None) -> dict:
+    """PFA scores of culled corners (CUDA tensors: level u8, x/y/response
+    u16) through jslam_pfa_scores_static, which allocates no device memory.
+    The output tensors are allocated here, by the caller side."""
+    import torch
+    n = int(level.numel())
+    dev = level.device
+    out = {"X": torch.empty(n, dtype=torch.uint16, device=dev), "Y": torch.empty(n, dtype=torch.uint16, device=dev),
+           "k_levels": torch.empty(n, dtype=torch.uint8, device=dev),
+           "k_resp": torch.empty(n, dtype=torch.uint32, device=dev),
+           "alive": torch.empty(n, dtype=torch.uint8, device=dev)}
+    handle = (stream if isinstance(stream, int) else stream.cuda_stream) if stream is not None else \
+        torch.cuda.current_stream(dev).cuda_stream
+    _check(lib().jslam_pfa_scores_static(level.data_ptr(), x.data_ptr(), y.data_ptr(), response.data_ptr(), n,
+                                         width0, height0, levels, scale, nms_q, pfa_rule, out["X"].data_ptr(),
+                                         out["Y"].data_ptr(), out["k_levels"].data_ptr(), out["k_resp"].data_ptr(),
+                                         out["alive"].data_ptr(), dev.index, handle), "jslam_pfa_scores_static")
+    return out
 
 
 # ------------------------------------------------------------ images
