@@ -268,6 +268,11 @@ jslam_status jslam_level_geometry(int32_t width, int32_t height, int32_t levels,
 /* Projection of level-n coordinate v to s0 (clamped to extent-1). */
 int32_t jslam_project(int32_t v, int32_t level, float scale, int32_t extent);
 
+/* Corner look-up table of Sec. III for Eq. 3: bit m of out[m / 32] (bit
+ * m % 32) is set when the 16-bit ring mask m has its longest circular run of
+ * set bits in [p_min, p_max].  `out` holds 2048 words. */
+jslam_status jslam_corner_table(int32_t p_min, int32_t p_max, uint32_t *out);
+
 /* Stereo row band at level n: ceil(row_band_px * zeta^n). */
 int32_t jslam_match_band(int32_t level, float scale, int32_t row_band_px);
 

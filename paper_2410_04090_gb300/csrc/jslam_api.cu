@@ -5,12 +5,14 @@
 #include <cstring>
 #include <vector>
 
-#include "../../include/jslam.h"
+#include <cudaTypedefs.h>
+
+#include "jslam.h"
 #include "jslam_internal.h"
 #include "tables.h"
 
 namespace jslam {
-int fast_smem_bytes(int tw, int th, int cells, int k);
+int fast_smem_bytes(int max_box, int max_px, int max_cells, int k);
 }
 
 using namespace jslam;
@@ -18,6 +20,35 @@ using namespace jslam;
 namespace {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link-time dependency on the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Detection tile box of a level: rows of box_w bytes (a multiple of 16 that
+// covers the tile, its 4-pixel halo on both sides and up to 12 bytes of
+// alignment slack on the left) and box_h rows (3-row halo above and below).
+void detect_box(int tw, int th, int *box_w, int *box_h)
+{
+    *box_w = (int)align_up((size_t)(tw + 8 + 12), 16);
+    *box_h = th + 6;
+}
+
+constexpr size_t kLevelSlack = 256;  // bytes after each level buffer
 
 // Optional allocation-failure injection for host-side fault tests: the
 // environment variable JSLAM_FAIL_ALLOC_AFTER=n makes the (n+1)-th device
@@ -132,9 +163,10 @@ struct jslam_ctx {
     jslam_status status = JSLAM_OK;
 
     // constant tables
-    GrowBuf consts;  // pattern | cos | sin
+    GrowBuf consts;  // pattern | cos | sin | corner table
     int8_t *d_pattern = nullptr;
     double *d_cos = nullptr, *d_sin = nullptr;
+    uint32_t *d_lut = nullptr;
 
     // per-batch buffers
     GrowBuf plan, levels, maps, scratch, results, staging, counts;
@@ -197,11 +229,15 @@ jslam_status check_job(const jslam_ctx *ctx, const jslam_stereo_job &j)
     return JSLAM_OK;
 }
 
-// Cells per detection CTA: about 128 x 32 pixels, capped in cells x k.
+// Cells per detection tile: about 128 x 64 pixels, capped in cells x k; the
+// tile width is kept a multiple of 4 pixels where possible so that tiles
+// start on word boundaries.
 void fast_block(int c, int k, int *bx, int *by)
 {
     int x = 128 / c > 1 ? 128 / c : 1;
-    int y = 32 / c > 1 ? 32 / c : 1;
+    for (int cand = x; cand >= 1; --cand)
+        if ((cand * c) % 4 == 0) { x = cand; break; }
+    int y = 64 / c > 1 ? 64 / c : 1;
     while (x * y * k > kFastMaxCellsPerCta) {
         if (y > 1) --y; else --x;
     }
@@ -231,7 +267,8 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     std::vector<PairLayout> layouts(n);
     std::vector<size_t> result_off(n);
     size_t result_bytes = 0, level_bytes = 0, map_bytes = 0, staging_bytes = 0, table_bytes = 0;
-    int n_levels = 0, n_slots = 0, n_segs = 0, max_cap = 0, fast_smem = 0;
+    int n_levels = 0, n_slots = 0, n_segs = 0, max_cap = 0;
+    int max_box = 0, max_px = 0, max_cells = 0;
     for (int p = 0; p < n; ++p) {
         geo[p] = level_geometry(jobs[p].left.width, jobs[p].left.height, jobs[p].levels, jobs[p].scale, jobs[p].cell);
         layouts[p] = pair_layout(jobs[p].max_feats);
@@ -242,7 +279,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
         for (int s = 0; s < 2; ++s) {
             for (int l = 0; l < g.levels; ++l) {
                 const size_t pitch = align_up((size_t)g.W[l], 128);
-                level_bytes += align_up(pitch * g.H[l], 256) * (l == 0 ? 1 : 2);
+                level_bytes += 2 * align_up(pitch * g.H[l] + kLevelSlack, 256);
                 table_bytes += align_up((size_t)(g.W[l] + g.H[l]) * 4, 16);  // taps
                 table_bytes += align_up((size_t)(g.W[l] + g.H[l]) * 2, 16);  // projection
                 const int cx = (g.W[l] + g.c[l] - 1) / g.c[l], cy = (g.H[l] + g.c[l] - 1) / g.c[l];
@@ -250,8 +287,12 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 n_segs += cy;
                 int bx, by;
                 fast_block(g.c[l], k, &bx, &by);
-                fast_smem = std::max(fast_smem, fast_smem_bytes(std::min(bx * g.c[l], g.W[l]),
-                                                                std::min(by * g.c[l], g.H[l]), bx * by, k));
+                const int tw = std::min(bx * g.c[l], g.W[l]), th = std::min(by * g.c[l], g.H[l]);
+                int bw, bh;
+                detect_box(tw, th, &bw, &bh);
+                max_box = std::max(max_box, bw * bh);
+                max_px = std::max(max_px, tw * th);
+                max_cells = std::max(max_cells, bx * by);
             }
             n_levels += g.levels;
             map_bytes += align_up((size_t)g.W[0] * g.H[0] * 4, 256);
@@ -283,7 +324,17 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     const size_t o_pyr = reserve(sizeof(int32_t) * (n_levels + 1));
     const size_t o_fast = reserve(sizeof(int32_t) * (n_levels + 1));
     const size_t o_seg = reserve(sizeof(int32_t) * (n_segs + 1));
+    size_t n_fast_tiles = 0;
+    for (int p = 0; p < n; ++p)
+        for (int l = 0; l < geo[p].levels; ++l) {
+            int bx, by;
+            fast_block(geo[p].c[l], k, &bx, &by);
+            const int cx = (geo[p].W[l] + geo[p].c[l] - 1) / geo[p].c[l], cy = (geo[p].H[l] + geo[p].c[l] - 1) / geo[p].c[l];
+            n_fast_tiles += 2 * (size_t)(((cx + bx - 1) / bx) * ((cy + by - 1) / by));
+        }
+    const size_t o_ftl = reserve(sizeof(int32_t) * (n_fast_tiles + 1));
     const size_t o_lstart = reserve(sizeof(int32_t) * (kMaxLevels + 1) * n_img);
+    const size_t o_tmaps = reserve(sizeof(CUtensorMap) * (size_t)n_levels);
     const size_t o_tables = reserve(table_bytes + 256);
     if ((e = ctx->plan.ensure(off, false, nullptr)) != cudaSuccess) return fail(ctx, e);
 
@@ -295,6 +346,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     auto pyr_base = reinterpret_cast<int32_t *>(host.data() + o_pyr);
     auto fast_base = reinterpret_cast<int32_t *>(host.data() + o_fast);
     auto seg_level = reinterpret_cast<int32_t *>(host.data() + o_seg);
+    auto ftile_level = reinterpret_cast<int32_t *>(host.data() + o_ftl);
     size_t t_off = o_tables, lvl_off = 0, map_off = 0, stage_off = 0;
     int li = 0, slot = 0, seg = 0, pyr = 0, fast = 0;
     ctx->staging_off.assign(n_img, 0);
@@ -342,22 +394,20 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 L.cells_x = (L.W + L.c - 1) / L.c;
                 L.cells_y = (L.H + L.c - 1) / L.c;
                 fast_block(L.c, k, &L.bx, &L.by);
+                L.cinv = (65536 + L.c - 1) / L.c;
+                detect_box(std::min(L.bx * L.c, L.W), std::min(L.by * L.c, L.H), &L.box_w, &L.box_h);
                 L.image = img; L.level = l;
                 L.band = match_band(l, jobs[p].scale, cfg.row_band_px);
                 const size_t pitch = align_up((size_t)L.W, 128);
+                // raw and blurred level, each padded so that whole-word and
+                // halo reads past the last row stay inside the buffer
                 L.blur_pitch = (int)pitch;
-                if (l == 0) {
-                    L.raw = nullptr; L.raw_w = nullptr; L.pitch = 0;
-                    L.blur = ctx->levels.as<uint8_t>(lvl_off);
-                    lvl_off += align_up(pitch * L.H, 256);
-                } else {
-                    L.raw_w = ctx->levels.as<uint8_t>(lvl_off);
-                    L.raw = L.raw_w;
-                    lvl_off += align_up(pitch * L.H, 256);
-                    L.blur = ctx->levels.as<uint8_t>(lvl_off);
-                    lvl_off += align_up(pitch * L.H, 256);
-                    L.pitch = (int)pitch;
-                }
+                L.pitch = (int)pitch;
+                L.raw_w = ctx->levels.as<uint8_t>(lvl_off);
+                L.raw = L.raw_w;
+                lvl_off += align_up(pitch * L.H + kLevelSlack, 256);
+                L.blur = ctx->levels.as<uint8_t>(lvl_off);
+                lvl_off += align_up(pitch * L.H + kLevelSlack, 256);
                 // taps
                 uint32_t *tx = reinterpret_cast<uint32_t *>(host.data() + t_off);
                 L.tapx = reinterpret_cast<const uint32_t *>(dplan + t_off);
@@ -372,6 +422,23 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 for (int y = 0; y < L.H; ++y) px[L.W + y] = project(y, sc, g.H[0]);
                 t_off += align_up((size_t)(L.W + L.H) * 2, 16);
 
+                // TMA map of the raw level when every tile starts on a word
+                // boundary (the box x is rounded down to 16 bytes)
+                L.tmap = nullptr;
+                PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+                if (encode && (L.bx * L.c) % 4 == 0) {
+                    CUtensorMap map;  // encoded into an aligned object, then copied into the plan
+                    const cuuint64_t dims[2] = { (cuuint64_t)L.W, (cuuint64_t)L.H };
+                    const cuuint64_t strides[1] = { (cuuint64_t)L.pitch };
+                    const cuuint32_t box[2] = { (cuuint32_t)L.box_w, (cuuint32_t)L.box_h };
+                    const cuuint32_t estr[2] = { 1, 1 };
+                    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, L.raw_w, dims, strides, box, estr,
+                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+                        std::memcpy(host.data() + o_tmaps + sizeof(CUtensorMap) * li, &map, sizeof(CUtensorMap));
+                        L.tmap = reinterpret_cast<const CUtensorMap *>(dplan + o_tmaps) + li;
+                    }
+                }
                 L.slot_base = slot;
                 L.seg_base = seg;
                 slot += L.cells_x * L.cells_y * k;
@@ -380,7 +447,9 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 pyr_base[li] = pyr;
                 pyr += ((L.W + kPyrTW - 1) / kPyrTW) * ((L.H + kPyrTH - 1) / kPyrTH);
                 fast_base[li] = fast;
-                fast += ((L.cells_x + L.bx - 1) / L.bx) * ((L.cells_y + L.by - 1) / L.by);
+                const int ftiles = ((L.cells_x + L.bx - 1) / L.bx) * ((L.cells_y + L.by - 1) / L.by);
+                for (int q = 0; q < ftiles; ++q) ftile_level[fast + q] = li;
+                fast += ftiles;
             }
             I.slot_count = slot - I.slot_base;
             I.seg_count = seg - I.seg_base;
@@ -405,8 +474,12 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.pyr_tile_base = reinterpret_cast<const int32_t *>(dplan + o_pyr);
     b.fast_tile_base = reinterpret_cast<const int32_t *>(dplan + o_fast);
     b.seg_level = reinterpret_cast<const int32_t *>(dplan + o_seg);
+    b.fast_tile_level = reinterpret_cast<const int32_t *>(dplan + o_ftl);
     b.n_images = n_img; b.n_levels = n_levels; b.n_pairs = n; b.n_segments = n_segs;
-    b.pyr_tiles = pyr; b.fast_tiles = fast; b.max_capacity = max_cap; b.fast_smem = fast_smem;
+    b.pyr_tiles = pyr; b.fast_tiles = fast; b.max_capacity = max_cap;
+    b.fast_max_box = max_box; b.fast_max_px = max_px; b.fast_max_cells = max_cells;
+    b.fast_smem = fast_smem_bytes(max_box, max_px, max_cells, k);
+    b.corner_lut = ctx->d_lut;
     uint32_t *sw = ctx->scratch.as<uint32_t>();
     b.slots = sw;
     b.slot_k = sw + slot_words;
@@ -511,16 +584,20 @@ jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
     blur_weights(w);
     if (e == cudaSuccess) e = set_blur_weights(w);
     const size_t pat_bytes = (size_t)kBins * kPairs * 4;
-    if (e == cudaSuccess) e = ctx->consts.ensure(pat_bytes + 2 * kBins * sizeof(double) + 512, false, nullptr);
+    const size_t lut_off = pat_bytes + 2 * kBins * sizeof(double);
+    const size_t const_bytes = lut_off + kLutWords * sizeof(uint32_t);
+    if (e == cudaSuccess) e = ctx->consts.ensure(const_bytes + 512, false, nullptr);
     if (e == cudaSuccess) {
-        std::vector<char> h(pat_bytes + 2 * kBins * sizeof(double) + 256, 0);
+        std::vector<char> h(const_bytes, 0);
         rotated_pattern(reinterpret_cast<int8_t *>(h.data()));
         double *cs = reinterpret_cast<double *>(h.data() + pat_bytes);
         sector_tables(cs, cs + kBins);
+        corner_table(c.p_min, c.p_max, reinterpret_cast<uint32_t *>(h.data() + lut_off));
         e = cudaMemcpy(ctx->consts.ptr, h.data(), h.size(), cudaMemcpyHostToDevice);
         ctx->d_pattern = ctx->consts.as<int8_t>();
         ctx->d_cos = ctx->consts.as<double>(pat_bytes);
         ctx->d_sin = ctx->d_cos + kBins;
+        ctx->d_lut = ctx->consts.as<uint32_t>(lut_off);
     }
     if (e == cudaSuccess) e = ctx->counts.ensure(sizeof(int32_t) * (2 * (size_t)c.max_pairs + 8), true, nullptr);
     if (e == cudaSuccess) {
@@ -625,7 +702,9 @@ jslam_status jslam_sync(jslam_ctx *ctx)
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return fail(ctx, e);
     ctx->synced = true;
-    if (ctx->h_counts[2 * ctx->cfg.max_pairs] != 0) ctx->status = JSLAM_ERR_CAPACITY;
+    const uint32_t err = static_cast<uint32_t>(ctx->h_counts[2 * ctx->cfg.max_pairs]);
+    if (err & kErrTimeout) ctx->status = JSLAM_ERR_TIMEOUT;
+    else if (err) ctx->status = JSLAM_ERR_CAPACITY;
     return ctx->status;
 }
 
@@ -671,8 +750,8 @@ jslam_status jslam_get_level(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t
     if (level < 0 || level >= I.levels) return JSLAM_ERR_ARG;
     const LevelDesc &L = ctx->h_levels[I.level_base + level];
     out->width = L.W; out->height = L.H; out->blurred_pitch = L.blur_pitch; out->blurred = L.blur;
-    out->raw_pitch = level == 0 ? ctx->batch.in.pitch[2 * pair + side] : L.pitch;
-    out->raw = level == 0 ? ctx->batch.in.ptr[2 * pair + side] : L.raw;
+    out->raw_pitch = L.pitch;
+    out->raw = L.raw;
     return JSLAM_OK;
 }
 
@@ -814,6 +893,13 @@ jslam_status jslam_level_geometry(int32_t width, int32_t height, int32_t levels,
 int32_t jslam_project(int32_t v, int32_t level, float scale, int32_t extent)
 {
     return project(v, zeta_pow(scale, level), extent);
+}
+
+jslam_status jslam_corner_table(int32_t p_min, int32_t p_max, uint32_t *out)
+{
+    if (!out || p_min < 1 || p_max > 16 || p_min > p_max) return JSLAM_ERR_ARG;
+    corner_table(p_min, p_max, out);
+    return JSLAM_OK;
 }
 
 int32_t jslam_match_band(int32_t level, float scale, int32_t row_band_px)

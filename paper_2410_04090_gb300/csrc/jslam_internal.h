@@ -12,6 +12,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace jslam {
@@ -28,12 +29,14 @@ constexpr int kPyrTW = 128, kPyrTH = 32, kPyrThreads = 256;
 // Detection tile: at most this many pixels a side (host picks cells per CTA).
 constexpr int kFastMaxTile = 128, kFastThreads = 256;
 constexpr int kFastMaxCellsPerCta = 2048;  // cells x k per CTA
+constexpr int kLutWords = 2048;            // 2^16-entry corner bit table
 constexpr int kNmsThreads = 128;
 constexpr int kFinThreads = 1024;
 
 // Device error bits (OR-ed into the context's error word).
 constexpr uint32_t kErrSegment = 1u << 0;  // a segment was larger than kMaxSegment
 constexpr uint32_t kErrDecode = 1u << 1;   // a candidate decoded outside its level
+constexpr uint32_t kErrTimeout = 1u << 2;  // a bounded wait for a tile load gave up
 
 struct KpOut {
     uint16_t *x, *y, *X, *Y, *response;
@@ -45,17 +48,20 @@ struct KpOut {
 };
 
 struct LevelDesc {
-    const uint8_t *raw;      // raw level (level 0: unused, the input comes from Inputs)
-    uint8_t *raw_w;          // writable raw level (nullptr at level 0)
+    const uint8_t *raw;      // raw level (level 0: aligned copy of the input)
+    uint8_t *raw_w;          // the same buffer, written by the pyramid kernel
     uint8_t *blur;           // blurred level
     const uint32_t *tapx;    // bilinear taps: src index | weight << 16 (levels >= 1)
     const uint32_t *tapy;
     const uint16_t *projx;   // s0 projection of each x / y of the level
     const uint16_t *projy;
-    int32_t W, H, pitch;     // pitch of raw (level 0: see Inputs)
+    int32_t W, H, pitch;     // pitch of raw: width rounded up to 128
     int32_t blur_pitch;
     int32_t c, cells_x, cells_y;
-    int32_t bx, by;          // cells per detection CTA
+    int32_t bx, by;          // cells per detection tile
+    int32_t cinv;            // ceil(2^16 / c): exact division by c for values < 128
+    const CUtensorMap *tmap; // TMA map of the raw level (nullptr: tiles loaded with plain loads)
+    int32_t box_w, box_h;    // detection tile box: bytes per row (multiple of 16) and rows
     int32_t slot_base;       // first candidate slot of the level
     int32_t seg_base;        // first segment (cell row) of the level
     int32_t image, level;
@@ -103,11 +109,14 @@ struct Batch {
     const PairDesc *pairs;
     const int32_t *pyr_tile_base;   // n_levels + 1
     const int32_t *fast_tile_base;  // n_levels + 1
+    const int32_t *fast_tile_level; // level index of each detection tile
     const int32_t *seg_level;       // level index of each segment
     int32_t n_images, n_levels, n_pairs, n_segments;
     int32_t pyr_tiles, fast_tiles;
     int32_t max_capacity;           // largest keypoint capacity of any image
     int32_t fast_smem;              // dynamic shared memory of the detection kernel
+    int32_t fast_max_box, fast_max_px, fast_max_cells;  // its tile layout maxima
+    const uint32_t *corner_lut;     // bit m: P_min <= longest circular run of m <= P_max
     uint32_t *slots;                // candidate keys per slot
     uint32_t *slot_k;               // PFA scores seen by each slot
     int32_t *slot_rank;             // rank within its segment, -1 if suppressed

@@ -3,9 +3,9 @@
 //
 // k_pyramid   one CTA per 128x32 output tile of any (image, level): resamples
 //             the level from level 0 (bilinear, Q8 taps from host tables),
-//             writes it, and writes its 7-tap Gaussian (Sec. III, streamlined
-//             multiscale detection and extraction: "Gaussian filtering ...
-//             essential for robustness").
+//             writes it (level 0: an aligned copy of the input), and writes its
+//             7-tap Gaussian (Sec. III, streamlined multiscale detection and
+//             extraction: Gaussian filtering before ORB).
 // k_fast_cull one CTA per block of culling cells of any (image, level): stages
 //             the raw tile plus a 3-pixel halo in shared memory, evaluates the
 //             16-pixel ring of every pixel (Sec. II-A, Eq. 1 labels, Eq. 3
@@ -13,6 +13,10 @@
 //             the top-k corners of each cell (Sec. II-C-1, Feature Culling)
 //             and adds each survivor to the s0 score map (Sec. II-C-2, PFA
 //             steps 1-2: K_l and K_r accumulate in one packed word).
+#include <algorithm>
+
+#include <cuda.h>
+
 #include "jslam_internal.h"
 
 namespace jslam {
@@ -36,12 +40,38 @@ __device__ __forceinline__ int find_bucket(const int32_t *base, int n, int v)
 }
 
 // ---------------------------------------------------------------- pyramid
+//
+// Per 128x32 output tile: the raw level over the tile plus a halo (3 rows, 4
+// columns) is built in shared memory -- level 0 is copied from the input,
+// deeper levels are resampled from level 0 separably and exactly: every
+// needed source row is interpolated horizontally once ((256-a) p0 + a p1,
+// exact in 16 bits), then pairs of those rows vertically with rounding.
+// The raw interior is written to the level buffer (level 0 included: an
+// aligned copy of the input).  The 7-tap Gaussian runs vertically first on
+// bytes in 16-bit lanes (two pixels per multiply; the symmetric taps need 3
+// adds and 4 multiplies), then horizontally on the 16-bit column sums.
+
+constexpr int kPyrCols = kPyrTW + 8;         // raw tile columns: x in [x0 - 4, x0 + 132)
+constexpr int kPyrRows = kPyrTH + 6;         // raw tile rows: y in [y0 - 3, y0 + 35)
+constexpr int kPyrSrcRows = 2 * kPyrRows;    // level-0 rows interpolated per tile, at most
+
+__device__ __forceinline__ uint32_t blur7_sym(uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t a4,
+                                              uint32_t a5, uint32_t a6)
+{
+    return c_blur_w[0] * (a0 + a6) + c_blur_w[1] * (a1 + a5) + c_blur_w[2] * (a2 + a4) + c_blur_w[3] * a3;
+}
 
 __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
 {
-    constexpr int RW = kPyrTW + 6, RH = kPyrTH + 6;
-    __shared__ uint8_t rs[RH][kPyrTW + 8];
-    __shared__ uint16_t hs[RH][kPyrTW];
+    __shared__ __align__(16) uint8_t raw[kPyrRows][kPyrCols];
+    __shared__ __align__(16) uint16_t V[kPyrTH][kPyrCols];
+    __shared__ __align__(16) uint16_t Hs[kPyrSrcRows][kPyrCols];
+    __shared__ uint32_t tx[kPyrCols];
+    __shared__ int src_row[kPyrSrcRows];
+    __shared__ uint8_t ia[kPyrRows], ib[kPyrRows];
+    __shared__ uint16_t wb[kPyrRows];
+    __shared__ int s_ya[kPyrRows];
+    __shared__ int nsrc;
 
     const int li = find_bucket(b.pyr_tile_base, b.n_levels, blockIdx.x);
     const LevelDesc L = b.levels[li];
@@ -51,55 +81,109 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
     const int x0 = (t % tiles_x) * kPyrTW, y0 = (t / tiles_x) * kPyrTH;
     const uint8_t *L0 = b.in.ptr[L.image];
     const int W0 = I.W0, H0 = I.H0, pitch0 = b.in.pitch[L.image];
+    const int W = L.W, H = L.H;
+    constexpr int WPR = kPyrCols / 4;
 
-    // Raw level values over the tile plus a 3-pixel halo; coordinates outside
-    // the level are clamped (replicated border of the blur).
-    for (int i = threadIdx.x; i < RW * RH; i += kPyrThreads) {
-        const int ry = i / RW, rx = i - ry * RW;
-        const int gy = min(max(y0 - 3 + ry, 0), L.H - 1);
-        const int gx = min(max(x0 - 3 + rx, 0), L.W - 1);
-        uint32_t v;
-        if (L.level == 0) {
-            v = __ldg(L0 + (size_t)gy * pitch0 + gx);
-        } else {
-            const uint32_t tx = __ldg(L.tapx + gx), ty = __ldg(L.tapy + gy);
-            const int xa = tx & 0xFFFF, a = tx >> 16, xb = min(xa + 1, W0 - 1);
-            const int ya = ty & 0xFFFF, wb = ty >> 16, yb = min(ya + 1, H0 - 1);
-            const uint8_t *ra = L0 + (size_t)ya * pitch0, *rb = L0 + (size_t)yb * pitch0;
-            const uint32_t top = (256u - a) * __ldg(ra + xa) + (uint32_t)a * __ldg(ra + xb);
-            const uint32_t bot = (256u - a) * __ldg(rb + xa) + (uint32_t)a * __ldg(rb + xb);
-            v = ((256u - wb) * top + (uint32_t)wb * bot + 32768u) >> 16;
+    if (L.level == 0) {
+        for (int i = threadIdx.x; i < kPyrRows * WPR; i += kPyrThreads) {
+            const int r = i / WPR, w = i - r * WPR;
+            const uint8_t *row = L0 + (size_t)min(max(y0 - 3 + r, 0), H - 1) * pitch0;
+            const int gx = x0 - 4 + 4 * w;
+            uint32_t v;
+            if (gx >= 0 && gx + 3 < W && (reinterpret_cast<uintptr_t>(row + gx) & 3u) == 0) {
+                v = __ldg(reinterpret_cast<const uint32_t *>(row + gx));
+            } else {
+                v = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v |= (uint32_t)__ldg(row + min(max(gx + q, 0), W - 1)) << (8 * q);
+            }
+            *reinterpret_cast<uint32_t *>(&raw[r][4 * w]) = v;
         }
-        rs[ry][rx] = (uint8_t)v;
+    } else {
+        for (int c = threadIdx.x; c < kPyrCols; c += kPyrThreads)
+            tx[c] = __ldg(L.tapx + min(max(x0 - 4 + c, 0), W - 1));
+        if (threadIdx.x < kPyrRows) {
+            const uint32_t ty = __ldg(L.tapy + min(max(y0 - 3 + (int)threadIdx.x, 0), H - 1));
+            s_ya[threadIdx.x] = ty & 0xFFFF;
+            wb[threadIdx.x] = (uint16_t)(ty >> 16);
+        }
+        __syncthreads();
+        // level-0 rows needed by the tile's raw rows: a contiguous range when
+        // it is short enough, else two rows per raw row
+        const int first = s_ya[0], last = min(s_ya[kPyrRows - 1] + 1, H0 - 1);
+        const bool contiguous = last - first + 1 <= kPyrSrcRows;
+        if (threadIdx.x < kPyrRows) {
+            const int r = threadIdx.x, ya = s_ya[r], yb = min(ya + 1, H0 - 1);
+            ia[r] = (uint8_t)(contiguous ? ya - first : 2 * r);
+            ib[r] = (uint8_t)(contiguous ? yb - first : 2 * r + 1);
+        }
+        const int nrows = contiguous ? last - first + 1 : kPyrSrcRows;
+        for (int j = threadIdx.x; j < nrows; j += kPyrThreads)
+            src_row[j] = contiguous ? first + j : ((j & 1) ? min(s_ya[j >> 1] + 1, H0 - 1) : s_ya[j >> 1]);
+        if (threadIdx.x == 0) nsrc = nrows;
+        __syncthreads();
+        const int ns = nsrc;
+        for (int i = threadIdx.x; i < ns * kPyrCols; i += kPyrThreads) {
+            const int j = i / kPyrCols, c = i - j * kPyrCols;
+            const uint8_t *row = L0 + (size_t)src_row[j] * pitch0;
+            const uint32_t tp = tx[c];
+            const int xa = tp & 0xFFFF, a = tp >> 16, xb = min(xa + 1, W0 - 1);
+            Hs[j][c] = (uint16_t)((256u - a) * __ldg(row + xa) + (uint32_t)a * __ldg(row + xb));
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kPyrRows * kPyrCols; i += kPyrThreads) {
+            const int r = i / kPyrCols, c = i - r * kPyrCols;
+            const uint32_t w = wb[r];
+            raw[r][c] = (uint8_t)(((256u - w) * Hs[ia[r]][c] + w * Hs[ib[r]][c] + 32768u) >> 16);
+        }
     }
     __syncthreads();
 
-    if (L.level > 0) {
-        for (int i = threadIdx.x; i < kPyrTW * kPyrTH; i += kPyrThreads) {
-            const int ry = i / kPyrTW, rx = i % kPyrTW;
-            const int gy = y0 + ry, gx = x0 + rx;
-            if (gy < L.H && gx < L.W) L.raw_w[(size_t)gy * L.pitch + gx] = rs[ry + 3][rx + 3];
-        }
+    // raw interior -> level buffer (whole words; the row pitch covers the tile)
+    for (int i = threadIdx.x; i < kPyrTH * (kPyrTW / 4); i += kPyrThreads) {
+        const int r = i / (kPyrTW / 4), w = i - r * (kPyrTW / 4);
+        const int gy = y0 + r, gx = x0 + 4 * w;
+        if (gy < H && gx < W)
+            *reinterpret_cast<uint32_t *>(L.raw_w + (size_t)gy * L.pitch + gx) =
+                *reinterpret_cast<const uint32_t *>(&raw[r + 3][4 * w + 4]);
     }
-    // Horizontal pass over every halo row.
-    for (int i = threadIdx.x; i < kPyrTW * RH; i += kPyrThreads) {
-        const int ry = i / kPyrTW, rx = i % kPyrTW;
-        uint32_t acc = 0;
+    // vertical 7-tap sums of every column, two pixels per 32-bit lane pair
+    for (int i = threadIdx.x; i < kPyrTH * WPR; i += kPyrThreads) {
+        const int r = i / WPR, w = i - r * WPR;
+        uint32_t e[7], o[7];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) acc += (uint32_t)c_blur_w[k] * rs[ry][rx + k];
-        hs[ry][rx] = (uint16_t)acc;
+        for (int j = 0; j < 7; ++j) {
+            const uint32_t x = *reinterpret_cast<const uint32_t *>(&raw[r + j][4 * w]);
+            e[j] = x & 0x00FF00FFu;
+            o[j] = (x >> 8) & 0x00FF00FFu;
+        }
+        const uint32_t se = blur7_sym(e[0], e[1], e[2], e[3], e[4], e[5], e[6]);
+        const uint32_t so = blur7_sym(o[0], o[1], o[2], o[3], o[4], o[5], o[6]);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&V[r][4 * w]);
+        dst[0] = __byte_perm(se, so, 0x5410);
+        dst[1] = __byte_perm(se, so, 0x7632);
     }
     __syncthreads();
-    // Vertical pass and rounding.
-    for (int i = threadIdx.x; i < kPyrTW * kPyrTH; i += kPyrThreads) {
-        const int ry = i / kPyrTW, rx = i % kPyrTW;
-        const int gy = y0 + ry, gx = x0 + rx;
-        if (gy < L.H && gx < L.W) {
-            uint32_t acc = 0;
+    // horizontal 7-tap on the column sums, 4 output pixels per thread
+    for (int i = threadIdx.x; i < kPyrTH * (kPyrTW / 4); i += kPyrThreads) {
+        const int r = i / (kPyrTW / 4), q = i - r * (kPyrTW / 4);
+        const int gy = y0 + r, gx = x0 + 4 * q;
+        if (gy >= H || gx >= W) continue;
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&V[r][4 * q]);
+        uint32_t v[12];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) acc += (uint32_t)c_blur_w[k] * hs[ry + k][rx];
-            L.blur[(size_t)gy * L.blur_pitch + gx] = (uint8_t)((acc + 32768u) >> 16);
+        for (int j = 0; j < 6; ++j) {
+            const uint32_t p = src[j];
+            v[2 * j] = p & 0xFFFFu;
+            v[2 * j + 1] = p >> 16;
         }
+        uint32_t out = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t s = blur7_sym(v[k + 1], v[k + 2], v[k + 3], v[k + 4], v[k + 5], v[k + 6], v[k + 7]);
+            out |= ((s + 32768u) >> 16) << (8 * k);
+        }
+        *reinterpret_cast<uint32_t *>(L.blur + (size_t)gy * L.blur_pitch + gx) = out;
     }
 }
 
@@ -111,166 +195,402 @@ cudaError_t launch_pyramid(const Batch &b, cudaStream_t stream)
 }
 
 // ---------------------------------------------------------------- FAST + FC
+//
+// One persistent CTA loops over detection tiles (a block of whole culling
+// cells of any image and level).  The raw tile plus its halo is fetched by
+// TMA (one 2-D tensor map per level) into one of two shared-memory buffers
+// while the CTA works on the other, with an mbarrier per buffer.  Per tile:
+//   1. primary threshold: every thread classifies 4 horizontally adjacent
+//      pixels at once.  For each of the 16 ring offsets the 4 ring bytes are
+//      compared with the 4 per-pixel thresholds by byte-wise carries (no
+//      carry crosses a byte), and the flags are gathered into per-pixel
+//      16-bit bright / dark masks; the corner test of Eq. 3 is one look-up
+//      per mask in the 64 Ki-entry bit table of Sec. III (built on the host
+//      for P_min, P_max).  Corners go to a compacted list and mark their cell;
+//   2. fallback threshold, only for pixels of cells left without a corner;
+//   3. for each listed corner the SAD response is computed and the cell's
+//      top-k is kept by atomicMax on the key response << 16 | (0xFFFF -
+//      index in cell) (strongest first, then smaller y, then smaller x);
+//   4. slots are written and every survivor is added to the s0 score map
+//      (PFA steps 1-2: K_l << 16 | K_r in one word).
 
 // Ring offsets (dx, dy) of the radius-3 Bresenham circle, index 0 below the
 // centre (image y down), in ring order.
 __constant__ int8_t c_ring_dx[16] = { 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1 };
 __constant__ int8_t c_ring_dy[16] = { 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1, 0, 1, 2, 3 };
 
-// Positions i where bits i .. i+n-1 of d are all set, non-empty iff d holds a
-// run of n ones (n <= 16).  R_{a+b} = R_a & (R_b >> a).
-struct RunTest {
-    int n;
-    __device__ __forceinline__ bool operator()(uint32_t d) const
-    {
-        const uint32_t r1 = d, r2 = r1 & (r1 >> 1), r4 = r2 & (r2 >> 2), r8 = r4 & (r4 >> 4);
-        const uint32_t r16 = r8 & (r8 >> 8);
-        uint32_t acc = 0xFFFFFFFFu;
-        int off = 0;
-        if (n & 16) { acc &= r16 >> off; off += 16; }
-        if (n & 8) { acc &= r8 >> off; off += 8; }
-        if (n & 4) { acc &= r4 >> off; off += 4; }
-        if (n & 2) { acc &= r2 >> off; off += 2; }
-        if (n & 1) { acc &= r1 >> off; }
-        return acc != 0;
-    }
+constexpr uint32_t kH = 0x80808080u, kL7 = 0x7F7F7F7Fu;
+
+// Majority of three words, bitwise: at each byte's MSB, with c the carry into
+// that bit from the low 7 bits, it is the carry out of the byte sum a + b.
+__device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
+
+struct FastLayout {
+    int buf0, buf1, clist, ckey, has_hi, sel, bar, total;
 };
 
-// Eq. 3 on one 16-bit ring mask: P_min <= longest circular run <= P_max.
-// The ring is doubled into 32 bits so that circular runs become linear.
-__device__ __forceinline__ bool bounded_run(uint32_t m, RunTest lo, RunTest hi, bool upper)
+__host__ __device__ inline int fast_align(int v, int a) { return (v + a - 1) / a * a; }
+
+__host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int max_cells, int k)
 {
-    const uint32_t d = m | (m << 16);
-    return lo(d) && !(upper && hi(d));
+    FastLayout l;
+    int o = kLutWords * 4;
+    l.buf0 = o;  o += fast_align(max_box, 128);
+    l.buf1 = o;  o += fast_align(max_box, 128);
+    l.clist = o; o += fast_align(max_px * 2, 16);
+    l.ckey = o;  o += k > 1 ? fast_align(max_px * 4, 16) : 0;
+    l.has_hi = o; o += fast_align(max_cells, 16);
+    l.sel = o;   o += fast_align(max_cells * k * 4, 16);
+    l.bar = o;   o += 16;
+    l.total = o;
+    return l;
 }
 
-struct FastSmem {
-    int rwp, rh, tw, th, cells;
-    __host__ __device__ static int align16(int v) { return (v + 15) & ~15; }
-    __host__ __device__ int raw_bytes() const { return align16(rwp * rh); }
-    __host__ __device__ int code_bytes() const { return align16(tw * th * 2); }
-    __host__ __device__ int hi_bytes() const { return align16(cells); }
-    __host__ __device__ int total(int k) const { return raw_bytes() + code_bytes() + hi_bytes() + cells * k * 4; }
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Position of a detection tile: its cells, pixels and the TMA box origin.
+struct TileGeom {
+    int li, ccx0, ccy0, ncx, ncy, x0, y0, tw, th, xs, ys, delta;
 };
+
+__device__ __forceinline__ TileGeom tile_geom(const Batch &b, int t)
+{
+    TileGeom G;
+    G.li = __ldg(b.fast_tile_level + t);
+    const LevelDesc &L = b.levels[G.li];
+    const int tt = t - __ldg(b.fast_tile_base + G.li);
+    const int ctas_x = (L.cells_x + L.bx - 1) / L.bx;
+    const int ty = tt / ctas_x;
+    G.ccx0 = (tt - ty * ctas_x) * L.bx;
+    G.ccy0 = ty * L.by;
+    G.ncx = min(L.bx, L.cells_x - G.ccx0);
+    G.ncy = min(L.by, L.cells_y - G.ccy0);
+    G.x0 = G.ccx0 * L.c;
+    G.y0 = G.ccy0 * L.c;
+    G.tw = min(G.ncx * L.c, L.W - G.x0);
+    G.th = min(G.ncy * L.c, L.H - G.y0);
+    // box columns start on a 16-byte boundary at or before x0 - 4; the
+    // tile's first column (x0 - 4) sits delta bytes into each box row
+    G.xs = L.tmap ? ((G.x0 - 4) & ~15) : G.x0 - 4;
+    G.ys = G.y0 - 3;
+    G.delta = G.x0 - 4 - G.xs;
+    return G;
+}
+
+// Issue the TMA of tile t into buf; completion arrives on the mbarrier.
+__device__ __forceinline__ void issue_tile(const Batch &b, int t, uint8_t *buf, uint64_t *bar)
+{
+    const TileGeom G = tile_geom(b, t);
+    const LevelDesc &L = b.levels[G.li];
+    if (!L.tmap) return;
+    const uint32_t bytes = (uint32_t)(L.box_w * L.box_h);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(buf)), "l"(reinterpret_cast<uint64_t>(L.tmap)), "r"(G.xs), "r"(G.ys), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Wait for the mbarrier phase `parity`, giving up after about a second.
+__device__ __forceinline__ bool wait_tile(uint64_t *bar, uint32_t parity)
+{
+    const long long start = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+        if (done) return true;
+        if (clock64() - start > (1ll << 31)) return false;
+    }
+}
+
+// Corner bits (bit j: pixel 4g + j) of a group of 4 pixels; `base` points at
+// the word left of the group's centre word in the first of its 7 tile rows.
+__device__ __forceinline__ uint32_t group_corners(const uint32_t *base, int wpr, uint32_t e0, uint32_t e1,
+                                                  const uint32_t *lut, int p_min)
+{
+    constexpr int RDX[16] = { 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1 };
+    constexpr int RDY[16] = { 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1, 0, 1, 2, 3 };
+    uint32_t w[7][3];
+#pragma unroll
+    for (int r = 0; r < 7; ++r) {
+        w[r][0] = base[r * wpr + 0];
+        w[r][1] = base[r * wpr + 1];
+        w[r][2] = base[r * wpr + 2];
+    }
+    const uint32_t C = w[3][1];
+    // per byte: Tb = C + eps and Td = C - eps (wrapped); nb / nd flag the
+    // bytes where no ring pixel can be brighter than C + eps (C + eps >= 255)
+    // or darker than C - eps (C <= eps)
+    const uint32_t sb0 = (C & kL7) + (e0 & kL7);
+    const uint32_t Tb = sb0 ^ ((C ^ e0) & kH);
+    const uint32_t sb1 = (C & kL7) + (e1 & kL7);
+    const uint32_t nb = maj3(C, e1, sb1) & kH;
+    const uint32_t sd0 = (C | kH) - (e0 & kL7);
+    const uint32_t Td = sd0 ^ (~(C ^ e0) & kH);
+    const uint32_t sd1 = (C | kH) - (e1 & kL7);
+    const uint32_t nd = ~((C & ~e1) | (~(C ^ e1) & sd1)) & kH;
+    const uint32_t N = ~Tb, N7 = N & kL7, K = (Td & kL7) + kL7;
+    uint32_t b_lo = 0, b_hi = 0, d_lo = 0, d_hi = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int r = RDY[q] + 3, dx = RDX[q];
+        uint32_t P;
+        if (dx == 0) P = w[r][1];
+        else if (dx > 0) P = __funnelshift_r(w[r][1], w[r][2], 8 * dx);
+        else P = __funnelshift_r(w[r][0], w[r][1], 8 * (4 + dx));
+        const uint32_t Pl = P & kL7;
+        const uint32_t gb = maj3(P, N, Pl + N7);    // MSB: carry of P + ~(C + eps), i.e. P > C + eps
+        const uint32_t gd = maj3(Td, ~P, K - Pl);   // MSB: carry of (C - eps) + ~P, i.e. P < C - eps
+        const int sh = q < 8 ? 7 - q : 15 - q;
+        const uint32_t m = kH >> sh;
+        if (q < 8) { b_lo |= (gb >> sh) & m; d_lo |= (gd >> sh) & m; }
+        else { b_hi |= (gb >> sh) & m; d_hi |= (gd >> sh) & m; }
+    }
+    const uint32_t nbx = (nb >> 7) * 0xFFu, ndx = (nd >> 7) * 0xFFu;
+    b_lo &= ~nbx; b_hi &= ~nbx; d_lo &= ~ndx; d_hi &= ~ndx;
+    uint32_t bits = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t sel = (uint32_t)j | ((uint32_t)(4 + j) << 4);
+        const uint32_t mb = __byte_perm(b_lo, b_hi, sel) & 0xFFFFu;
+        const uint32_t md = __byte_perm(d_lo, d_hi, sel) & 0xFFFFu;
+        // a mask with fewer than P_min set bits has no run of P_min: skip the
+        // look-up (lanes that skip issue no shared-memory request)
+        uint32_t ok = 0;
+        if (__popc(mb) >= p_min) ok = lut[mb >> 5] >> (mb & 31);
+        if (__popc(md) >= p_min) ok |= lut[md >> 5] >> (md & 31);
+        bits |= (ok & 1u) << j;
+    }
+    return bits;
+}
+
+// floor(v / c) for 0 <= v < 128 and 1 <= c <= 128 with cinv = ceil(2^16 / c):
+// exact because v * c < 2^16.
+__device__ __forceinline__ int div_small(int v, uint32_t cinv) { return (int)(((uint32_t)v * cinv) >> 16); }
 
 __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
 {
-    extern __shared__ __align__(16) uint8_t smem[];
-    const int li = find_bucket(b.fast_tile_base, b.n_levels, blockIdx.x);
-    const LevelDesc L = b.levels[li];
-    const ImageDesc &I = b.images[L.image];
-    const int k = b.prm.k, border = b.prm.border;
-    const int t = blockIdx.x - b.fast_tile_base[li];
-    const int ctas_x = (L.cells_x + L.bx - 1) / L.bx;
-    const int ccx0 = (t % ctas_x) * L.bx, ccy0 = (t / ctas_x) * L.by;
-    const int c = L.c;
-    const int ncx = min(L.bx, L.cells_x - ccx0), ncy = min(L.by, L.cells_y - ccy0);
-    const int x0 = ccx0 * c, y0 = ccy0 * c;
-    const int tw = min(ncx * c, L.W - x0), th = min(ncy * c, L.H - y0);
-    const int rw = tw + 6, rh = th + 6;
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ int n_corner, need_lo;
+    const int k = b.prm.k, border = b.prm.border, p_min = b.prm.p_min;
+    const FastLayout lay = fast_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k);
+    uint32_t *lut = reinterpret_cast<uint32_t *>(smem);
+    uint8_t *const buf0 = smem + lay.buf0, *const buf1 = smem + lay.buf1;
+    uint16_t *clist = reinterpret_cast<uint16_t *>(smem + lay.clist);
+    uint32_t *ckey = reinterpret_cast<uint32_t *>(smem + lay.ckey);
+    uint8_t *has_hi = smem + lay.has_hi;
+    uint32_t *sel = reinterpret_cast<uint32_t *>(smem + lay.sel);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    FastSmem lay;
-    lay.rwp = (rw + 3) & ~3; lay.rh = rh; lay.tw = tw; lay.th = th; lay.cells = ncx * ncy;
-    uint8_t *rs = smem;
-    uint16_t *code = reinterpret_cast<uint16_t *>(smem + lay.raw_bytes());
-    uint8_t *has_hi = smem + lay.raw_bytes() + lay.code_bytes();
-    uint32_t *sel = reinterpret_cast<uint32_t *>(smem + lay.raw_bytes() + lay.code_bytes() + lay.hi_bytes());
-    const int rwp = lay.rwp;
-
-    const uint8_t *raw = L.level == 0 ? b.in.ptr[L.image] : L.raw;
-    const int pitch = L.level == 0 ? b.in.pitch[L.image] : L.pitch;
-    for (int i = threadIdx.x; i < rw * rh; i += kFastThreads) {
-        const int ry = i / rw, rx = i - ry * rw;
-        const int gy = min(max(y0 - 3 + ry, 0), L.H - 1);
-        const int gx = min(max(x0 - 3 + rx, 0), L.W - 1);
-        rs[ry * rwp + rx] = __ldg(raw + (size_t)gy * pitch + gx);
+    // TMA destinations must be 128-byte aligned; refuse to run otherwise
+    if ((smem_u32(buf0) | smem_u32(buf1)) & 127u) {
+        if (threadIdx.x == 0) atomicOr(b.err, kErrDecode);
+        return;
     }
-    for (int i = threadIdx.x; i < lay.cells; i += kFastThreads) has_hi[i] = 0;
-    for (int i = threadIdx.x; i < lay.cells * k; i += kFastThreads) sel[i] = 0;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < kLutWords; i += kFastThreads) lut[i] = __ldg(b.corner_lut + i);
     __syncthreads();
+    if (threadIdx.x == 0 && blockIdx.x < b.fast_tiles) issue_tile(b, blockIdx.x, buf0, &bars[0]);
+    uint32_t phase0 = 0u, phase1 = 0u;
 
-    int ring[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) ring[q] = c_ring_dy[q] * rwp + c_ring_dx[q];
-    const int eps = I.eps_hi, eps2 = I.eps_lo;
-    const bool use_lo = eps2 > 0;
-    const RunTest run_lo{b.prm.p_min}, run_hi{b.prm.p_max + 1};
-    const bool upper = b.prm.p_max < 16;
+    int it = 0;
+    for (int t = blockIdx.x; t < b.fast_tiles; t += gridDim.x, ++it) {
+        const int cur = it & 1;
+        const TileGeom G = tile_geom(b, t);
+        const LevelDesc &L = b.levels[G.li];
+        const ImageDesc &I = b.images[L.image];
+        // prefetch the next tile into the other buffer (its readers finished
+        // at the barrier that ended the previous iteration)
+        if (threadIdx.x == 0 && t + (int)gridDim.x < b.fast_tiles)
+            issue_tile(b, t + gridDim.x, cur ? buf0 : buf1, &bars[cur ^ 1]);
+        const int c = L.c, cells_x = L.cells_x, W = L.W, Hh = L.H;
+        const uint32_t cinv = (uint32_t)L.cinv;
+        const int ncx = G.ncx, x0 = G.x0, y0 = G.y0, tw = G.tw, th = G.th;
+        const int rowb = L.box_w, wpr = rowb >> 2;
+        const int cells = ncx * G.ncy;
+        uint8_t *tb = cur ? buf1 : buf0;
 
-    // CRF-matrix of the tile, packed: response | hi << 12 | lo << 13 (0 off-corner).
-    for (int i = threadIdx.x; i < tw * th; i += kFastThreads) {
-        const int py = i / tw, px = i - py * tw;
-        const int gx = x0 + px, gy = y0 + py;
-        uint32_t cd = 0;
-        if (gx >= border && gx < L.W - border && gy >= border && gy < L.H - border) {
-            const uint8_t *p = rs + (py + 3) * rwp + (px + 3);
-            const int ic = p[0];
-            uint32_t bb = 0, bd = 0, bb2 = 0, bd2 = 0;
-            int r = 0;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) {
-                const int d = (int)p[ring[q]] - ic;
-                bb |= (uint32_t)(d > eps) << q;
-                bd |= (uint32_t)(d < -eps) << q;
-                bb2 |= (uint32_t)(d > eps2) << q;
-                bd2 |= (uint32_t)(d < -eps2) << q;
-                r += abs(d);
+        if (L.tmap) {
+            if (!wait_tile(&bars[cur], cur ? phase1 : phase0)) {
+                if (threadIdx.x == 0) atomicOr(b.err, kErrTimeout);
+                return;
             }
-            const bool hi = bounded_run(bb, run_lo, run_hi, upper) || bounded_run(bd, run_lo, run_hi, upper);
-            const bool lo = use_lo && (bounded_run(bb2, run_lo, run_hi, upper) || bounded_run(bd2, run_lo, run_hi, upper));
-            if (hi || lo) cd = (uint32_t)r | ((uint32_t)hi << 12) | ((uint32_t)lo << 13);
-            if (hi) has_hi[(py / c) * ncx + px / c] = 1;
+            if (cur) phase1 ^= 1u; else phase0 ^= 1u;
+        } else {
+            // levels whose tiles cannot start on a word boundary: plain loads,
+            // the same layout (box rows of box_w bytes, delta = 0)
+            uint32_t *tw32 = reinterpret_cast<uint32_t *>(tb);
+            for (int i = threadIdx.x; i < L.box_h * wpr; i += kFastThreads) {
+                const int r = i / wpr, wi = i - r * wpr;
+                const uint8_t *row = L.raw + (size_t)min(max(G.ys + r, 0), Hh - 1) * L.pitch;
+                const int gx = G.xs + 4 * wi;
+                uint32_t v = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v |= (uint32_t)__ldg(row + min(max(gx + q, 0), W - 1)) << (8 * q);
+                tw32[i] = v;
+            }
         }
-        code[i] = (uint16_t)cd;
-    }
-    __syncthreads();
+        for (int i = threadIdx.x; i < cells; i += kFastThreads) has_hi[i] = 0;
+        for (int i = threadIdx.x; i < cells * k; i += kFastThreads) sel[i] = 0;
+        if (threadIdx.x == 0) { n_corner = 0; need_lo = 0; }
+        __syncthreads();
 
-    // Top-k per cell by key = response << 16 | (0xFFFF - index in cell): the
-    // largest key is the strongest corner, ties resolved towards the smaller
-    // y, then the smaller x.  Cells with a primary-threshold corner choose
-    // among those only; the others fall back to the lower threshold.
-    for (int j = 0; j < k; ++j) {
-        for (int i = threadIdx.x; i < tw * th; i += kFastThreads) {
-            const uint32_t cd = code[i];
-            if (!cd) continue;
-            const int py = i / tw, px = i - py * tw;
-            const int cell = (py / c) * ncx + px / c;
-            const bool ok = has_hi[cell] ? (cd & 0x1000u) : (cd & 0x2000u);
-            if (!ok) continue;
-            const uint32_t inidx = (uint32_t)((py % c) * c + (px % c));
-            const uint32_t key = ((cd & 0xFFFu) << 16) | (0xFFFFu - inidx);
-            if (j == 0 || key < sel[cell * k + j - 1]) atomicMax(&sel[cell * k + j], key);
+        // pixels evaluated: tile-local x in [plo, phi), rows whose y is inside the border
+        const int plo = max(border - x0, 0), phi = min(W - border - x0, tw);
+        const int gpr = (tw + 3) >> 2, ngroups = gpr * th;
+        // word of tile column 0 (pixel x0 - 4) within a box row
+        const uint32_t *words = reinterpret_cast<const uint32_t *>(tb) + (G.delta >> 2);
+
+        // 1./2. corner bits of every group, pushed to the compacted list.
+        for (int pass = 0; pass < 2; ++pass) {
+            const int eps = pass == 0 ? I.eps_hi : I.eps_lo;
+            if (pass == 1) {
+                if (eps <= 0) break;
+                __syncthreads();  // has_hi complete
+                for (int i = threadIdx.x; i < cells; i += kFastThreads)
+                    if (!has_hi[i]) need_lo = 1;
+                __syncthreads();
+                if (!need_lo) break;
+            }
+            const uint32_t e0 = (uint32_t)eps * 0x01010101u, e1 = (uint32_t)(eps + 1) * 0x01010101u;
+            const int gstep_y = kFastThreads / gpr, gstep_x = kFastThreads - gstep_y * gpr;
+            int py = threadIdx.x / gpr, g = threadIdx.x - (threadIdx.x / gpr) * gpr;
+            for (int base = warp * 32; base < ngroups; base += kFastThreads) {
+                const int gi = base + lane;
+                uint32_t bits = 0;
+                if (gi < ngroups) {
+                    const int gy = y0 + py;
+                    const int px0 = 4 * g;
+                    if (gy >= border && gy < Hh - border && px0 + 3 >= plo && px0 < phi) {
+                        uint32_t valid = 0;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) valid |= (uint32_t)(px0 + j >= plo && px0 + j < phi) << j;
+                        if (pass == 1) {
+                            const int crow = div_small(py, cinv) * ncx;
+                            uint32_t need = 0;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                need |= (uint32_t)(!has_hi[crow + div_small(px0 + j, cinv)]) << j;
+                            valid &= need;
+                        }
+                        if (valid) bits = group_corners(words + py * wpr + g, wpr, e0, e1, lut, p_min) & valid;
+                    }
+                }
+                const int cpy = py, cg = g;  // this iteration's group
+                g += gstep_x; py += gstep_y;
+                if (g >= gpr) { g -= gpr; ++py; }
+                // warp-aggregated append of this iteration's corners
+                const int cnt = __popc(bits);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                int start = 0;
+                if (lane == 31 && total) start = atomicAdd(&n_corner, total);
+                start = __shfl_sync(0xFFFFFFFFu, start, 31) + incl - cnt;
+                if (bits) {
+                    const int crow = div_small(cpy, cinv) * ncx;
+                    do {
+                        const int j = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        const int px = 4 * cg + j;
+                        clist[start++] = (uint16_t)((cpy << 7) | px);
+                        if (pass == 0) has_hi[crow + div_small(px, cinv)] = 1;
+                    } while (bits);
+                }
+            }
         }
         __syncthreads();
-    }
 
-    // Store the cell slots and scatter survivors into the s0 score map.
-    for (int e = threadIdx.x; e < lay.cells * k; e += kFastThreads) {
-        const int cell = e / k, j = e - cell * k;
-        const int gcx = ccx0 + cell % ncx, gcy = ccy0 + cell / ncx;
-        const uint32_t key = sel[e];
-        b.slots[L.slot_base + (gcy * L.cells_x + gcx) * k + j] = key;
-        if (key) {
-            const int inidx = 0xFFFF - (int)(key & 0xFFFFu);
-            const int x = gcx * c + inidx % c, y = gcy * c + inidx / c;
-            if (x >= L.W || y >= L.H) { atomicOr(b.err, kErrDecode); continue; }
-            const int X = __ldg(L.projx + x), Y = __ldg(L.projy + y);
-            atomicAdd(I.map + (size_t)Y * I.W0 + X, (1u << 16) + (key >> 16));
+        // 3. response of every listed corner and the per-cell top-k.
+        const int nc = n_corner;
+        const uint8_t *tbytes = tb + G.delta;  // pixel (x, y) at (y - y0 + 3) * rowb + (x - x0 + 4)
+        for (int i = threadIdx.x; i < nc; i += kFastThreads) {
+            const int e = clist[i];
+            const int py = e >> 7, px = e & 127;
+            const uint8_t *p = tbytes + (py + 3) * rowb + (px + 4);
+            const int ic = p[0];
+            int r = 0;
+#pragma unroll
+            for (int q = 0; q < 16; ++q) r += abs((int)p[c_ring_dy[q] * rowb + c_ring_dx[q]] - ic);
+            const int cy = div_small(py, cinv), cx = div_small(px, cinv);
+            const uint32_t inidx = (uint32_t)((py - cy * c) * c + (px - cx * c));
+            const uint32_t key = ((uint32_t)r << 16) | (0xFFFFu - inidx);
+            const int cell = cy * ncx + cx;
+            if (k == 1) atomicMax(&sel[cell], key);
+            else ckey[i] = key;
         }
+        if (k > 1) {
+            __syncthreads();
+            for (int j = 0; j < k; ++j) {
+                for (int i = threadIdx.x; i < nc; i += kFastThreads) {
+                    const int e = clist[i];
+                    const int cell = div_small(e >> 7, cinv) * ncx + div_small(e & 127, cinv);
+                    const uint32_t key = ckey[i];
+                    if (j == 0 || key < sel[cell * k + j - 1]) atomicMax(&sel[cell * k + j], key);
+                }
+                __syncthreads();
+            }
+        }
+        __syncthreads();
+
+        // 4. slots and the s0 score map.
+        for (int e = threadIdx.x; e < cells * k; e += kFastThreads) {
+            const int cell = e / k, j = e - cell * k;
+            const int lcy = cell / ncx;
+            const int gcx = G.ccx0 + cell - lcy * ncx, gcy = G.ccy0 + lcy;
+            const uint32_t key = sel[e];
+            b.slots[L.slot_base + (gcy * cells_x + gcx) * k + j] = key;
+            if (key) {
+                const int inidx = 0xFFFF - (int)(key & 0xFFFFu);
+                const int x = gcx * c + inidx % c, y = gcy * c + inidx / c;
+                if (x >= W || y >= Hh) { atomicOr(b.err, kErrDecode); continue; }
+                const int X = __ldg(L.projx + x), Y = __ldg(L.projy + y);
+                atomicAdd(I.map + (size_t)Y * I.W0 + X, (1u << 16) + (key >> 16));
+            }
+        }
+        __syncthreads();  // every reader of this buffer is done before it is refilled
     }
 }
 
-int fast_smem_bytes(int tw, int th, int cells, int k)
+int fast_smem_bytes(int max_box, int max_px, int max_cells, int k)
 {
-    FastSmem lay;
-    lay.rwp = (tw + 6 + 3) & ~3; lay.rh = th + 6; lay.tw = tw; lay.th = th; lay.cells = cells;
-    return lay.total(k);
+    return fast_layout(max_box, max_px, max_cells, k).total;
 }
 
 cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream)
 {
     if (b.fast_tiles == 0) return cudaSuccess;
-    k_fast_cull<<<b.fast_tiles, kFastThreads, b.fast_smem, stream>>>(b);
+    static int cached_smem = -1, cached_blocks = 0, n_sm = 0;
+    cudaError_t e;
+    if (n_sm == 0) {
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    }
+    if (cached_smem != b.fast_smem) {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, k_fast_cull, kFastThreads,
+                                                               b.fast_smem)) != cudaSuccess)
+            return e;
+        cached_smem = b.fast_smem;
+    }
+    const int grid = std::min(b.fast_tiles, std::max(1, cached_blocks) * n_sm);
+    k_fast_cull<<<grid, kFastThreads, b.fast_smem, stream>>>(b);
     return cudaGetLastError();
 }
 

@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
     const KpOut &o = I.out;
     const int lvl = o.level[i], x = o.x[i], y = o.y[i];
     const LevelDesc &L = b.levels[I.level_base + lvl];
-    const uint8_t *raw = lvl == 0 ? b.in.ptr[img] : L.raw;
-    const int pitch = lvl == 0 ? b.in.pitch[img] : L.pitch;
+    const uint8_t *raw = L.raw;
+    const int pitch = L.pitch;
 
     int m10 = 0, m01 = 0;
     if (lane < 2 * kDiskR + 1) {

@@ -17,7 +17,7 @@
 #include <cmath>
 #include <mutex>
 
-#include "../../include/jslam.h"
+#include "jslam.h"
 #include "jslam_internal.h"
 #include "tables.h"
 

@@ -146,4 +146,27 @@ void rotated_pattern(int8_t *out)
     }
 }
 
+// Bit m of the table: the 16-bit ring mask m has its longest circular run of
+// set bits in [p_min, p_max] (Eq. 3 on one mask; Sec. III builds such a table).
+void corner_table(int p_min, int p_max, uint32_t *bits)
+{
+    for (int w = 0; w < 2048; ++w) bits[w] = 0;
+    for (uint32_t m = 0; m < 65536; ++m) {
+        int longest = 0;
+        if (m == 0xFFFFu) {
+            longest = 16;
+        } else {
+            // rotate so that bit 15 is clear, then scan linearly
+            uint32_t r = m;
+            while (r & 0x8000u) r = ((r << 1) | (r >> 15)) & 0xFFFFu;
+            int run = 0;
+            for (int i = 0; i < 16; ++i) {
+                run = (r >> i & 1u) ? run + 1 : 0;
+                longest = run > longest ? run : longest;
+            }
+        }
+        if (longest >= p_min && longest <= p_max) bits[m >> 5] |= 1u << (m & 31);
+    }
+}
+
 }  // namespace jslam

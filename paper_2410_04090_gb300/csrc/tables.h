@@ -21,5 +21,6 @@ void blur_weights(int32_t w[7]);
 void sector_tables(double *cosb, double *sinb);
 void brief_pattern(int8_t *base);
 void rotated_pattern(int8_t *out);
+void corner_table(int p_min, int p_max, uint32_t *bits /* 2048 words */);
 
 }  // namespace jslam

@@ -79,7 +79,7 @@ SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extra
            "jslam_sync", "jslam_get_keypoints", "jslam_get_matches", "jslam_get_level", "jslam_result_bytes",
            "jslam_download", "jslam_result_view", "jslam_destroy", "jslam_status_str", "jslam_pattern_table",
            "jslam_level_geometry", "jslam_project", "jslam_match_band", "jslam_enable_stage_timing",
-           "jslam_stage_times", "jslam_pfa_scores_static")
+           "jslam_stage_times", "jslam_pfa_scores_static", "jslam_corner_table")
 STAGES = ("pyramid", "detect", "pfa_nms", "pfa_final", "orb", "match")
 
 _lib = None
@@ -131,6 +131,8 @@ def lib():
         L.jslam_project.restype = C.c_int32
         L.jslam_match_band.argtypes = [C.c_int32, C.c_float, C.c_int32]
         L.jslam_match_band.restype = C.c_int32
+        L.jslam_corner_table.argtypes = [C.c_int32, C.c_int32, C.c_void_p]
+        L.jslam_corner_table.restype = st
         L.jslam_enable_stage_timing.argtypes = [C.c_void_p, C.c_int32]
         L.jslam_enable_stage_timing.restype = st
         L.jslam_stage_times.argtypes = [C.c_void_p, C.c_void_p]
@@ -169,6 +171,12 @@ def level_geometry(width: int, height: int, levels: int, scale: float, cell: int
 
 def project(v: int, level: int, scale: float, extent: int) -> int:
     return lib().jslam_project(v, level, scale, extent)
+
+
+def corner_table(p_min: int = 9, p_max: int = 13) -> np.ndarray:
+    out = np.zeros(2048, np.uint32)
+    _check(lib().jslam_corner_table(p_min, p_max, out.ctypes.data), "jslam_corner_table")
+    return out
 
 
 def match_band(level: int, scale: float, row_band_px: int) -> int:

@@ -61,3 +61,11 @@ def test_other_scales(jslam, oracle):
         w, h, c = jslam.level_geometry(999, 777, 6, scale, 40)
         ow, oh, oc = oracle.level_geometry(999, 777, 6, scale, 40)
         assert np.array_equal(w, ow) and np.array_equal(h, oh) and np.array_equal(c, oc)
+
+
+@pytest.mark.parametrize("p_min,p_max", [(9, 13), (9, 16), (12, 14), (1, 16), (16, 16)])
+def test_corner_table_matches_oracle(jslam, oracle, p_min, p_max):
+    table = jslam.corner_table(p_min, p_max)
+    bits = np.unpackbits(table.view(np.uint8), bitorder="little").astype(bool)
+    want = np.array([p_min <= oracle.longest_run(m) <= p_max for m in range(1 << 16)])
+    assert np.array_equal(bits, want)
