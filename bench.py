@@ -3,15 +3,18 @@
 
 One step = the whole hot path (pyramid + Gaussian filter, FAST with Bounded
 Rectification, PyCA culling + aggregation, orientation + descriptors, stereo
-row matching) over one batch of synthetic input: the 100-frame KITTI-shaped
-sequence (1241x376 u8, 8 levels, scale 1.2, FAST 20 with fallback 7, 32x32
-cells, 2000 features per image) by default.
+row matching) over one batch of synthetic input: by default the 100-frame
+KITTI-shaped sequence (1241x376 u8, 8 levels, scale 1.2, FAST 20 with
+fallback 7, 32x32 cells, 2000 features per image).
 
-Modes: ``batched`` (all frames of the step in one launch sequence, the
-headline) and ``plain`` (one C-ABI call per stereo pair).  Inputs are resident
-in HBM before the timed region; L2 is flushed (256 MB write) before every
-timed step.  ``e2e`` repeats the batched step through the C ABI with pinned
-host images and downloads every result block, copies inside the timed region.
+Modes, each timed over the same steps:
+  batched  all pairs of the step in one C-ABI call (one launch per stage) -- the headline
+  graph    the batched call captured once as a CUDA graph and replayed
+  plain    one C-ABI call per stereo pair
+Inputs are resident in HBM before the timed region; L2 is flushed (256 MB
+write) before every timed step.  `e2e` repeats the batched step through the
+C ABI with pinned host images and downloads every result block, copies
+inside the timed region.
 
 ``--impl reference`` times the CPU oracle (the plain C implementation written
 from the paper) on the host cores, one stereo pair per step.
@@ -46,6 +49,8 @@ WORKLOAD_DESC = {
     "fhd_1920x1080_L8": "1920x1080 synthetic stereo sequence, 8 levels at scale 1.2, FAST 20 (fallback 7), "
                         "32x32 cells, 3000 features per image",
     "single_640x480_L1": "single 640x480 stereo pair, 1 level, FAST 20, 32x32 cells, 1 feature per cell",
+    "mixed16": "16 concurrent stereo streams: 4x 640x480 (4 levels), 4x 752x480 (5), 4x 1241x376 (6), "
+               "4x 1920x1080 (8), scale 1.2, FAST 20 (fallback 7), 32x32 cells",
 }
 
 # Stage -> kernel name, for the roofline and the ncu summaries.
@@ -53,33 +58,38 @@ KERNELS = {"pyramid": "k_pyramid", "detect": "k_fast_cull", "pfa_nms": "k_pfa_nm
            "pfa_final": "k_pfa_finalize", "orb": "k_orient_desc", "match": "k_match"}
 KERNEL_SOURCES = {"k_pyramid": "k_detect.cu", "k_fast_cull": "k_detect.cu", "k_pfa_nms": "k_pyca.cu",
                   "k_pfa_finalize": "k_pyca.cu", "k_orient_desc": "k_orb_match.cu", "k_match": "k_orb_match.cu"}
+LAUNCHES_PER_CALL = 6  # pyramid, detect, PFA NMS, PFA final, ORB, match
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="kitti_1241x376_L8", choices=sorted(WORKLOAD_DESC))
-    ap.add_argument("--frames", type=int, default=100)
-    ap.add_argument("--mode", choices=["batched", "plain"], default="batched")
+    ap.add_argument("--frames", type=int, default=100, help="pairs per step (sequence workloads)")
+    ap.add_argument("--mode", choices=["batched", "graph", "plain"], default="batched")
     ap.add_argument("--cpu-pairs", type=int, default=12, help="pairs in the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-batched", action="store_true",
-                    help="time the batched mode only (no plain mode, no e2e): the launch sequence ncu captures")
+                    help="time the batched mode only (no other modes, no e2e): the launch sequence ncu captures")
     return ap.parse_args()
 
 
-def workload_params(name):
+def make_workload(name, frames):
+    """(stereo pairs, per-pair parameters, fallback threshold) of one step."""
     from paper_2410_04090_gb300 import scenes
+    if name == "mixed16":
+        pairs, params = [], []
+        for i, sp in enumerate(scenes.MIXED_STREAMS):
+            pairs.append(scenes.stereo_pair(sp["kind"], sp["width"], sp["height"], frame=0, stream=i, config_id=4))
+            params.append(dict(levels=sp["levels"], scale=1.2, fast_thresh=20, cell=32, max_feats=sp["max_feats"]))
+        return pairs, params, 7
     w = scenes.WORKLOADS[name]
-    return dict(levels=w["levels"], scale=1.2, fast_thresh=w["fast_thresh"], cell=32, max_feats=w["max_feats"]), w
-
-
-def make_frames(name, frames):
-    from paper_2410_04090_gb300 import scenes
-    return [scenes.workload_pair(name, f) for f in range(frames)]
+    pairs = [scenes.workload_pair(name, f % w["frames"]) for f in range(frames)]
+    p = dict(levels=w["levels"], scale=1.2, fast_thresh=w["fast_thresh"], cell=32, max_feats=w["max_feats"])
+    return pairs, [p] * len(pairs), w["fast_thresh_lo"]
 
 
 # ------------------------------------------------------------------ helpers
@@ -90,21 +100,24 @@ def level_pixels(W0, H0, levels, scale):
     return [int(a) * int(b) for a, b in zip(w, h)]
 
 
-def algorithmic_bytes(stage, W0, H0, jp, n_pairs, kp_counts):
-    """Bytes a stage must move per launch (the batch's n_pairs pairs)."""
-    px = level_pixels(W0, H0, jp["levels"], jp["scale"])
-    A = sum(px)
-    imgs = 2 * n_pairs
+def algorithmic_bytes(stage, pairs, params, kp_counts):
+    """Bytes a stage must move per launch over the whole batch (None: not defined)."""
+    if stage not in ("pyramid", "detect", "orb", "match"):
+        return None
     kps = sum(kp_counts)
-    if stage == "pyramid":   # read L0, write raw levels >= 1, write every blurred level
-        return imgs * (px[0] + (A - px[0]) + A)
-    if stage == "detect":    # read every raw level once
-        return imgs * A
-    if stage == "orb":       # per keypoint: 32-byte descriptor + angle + sector out
+    if stage == "orb":     # per keypoint: 32-byte descriptor + angle + sector out
         return kps * (32 + 4 + 1)
-    if stage == "match":     # per left keypoint: its descriptor and the result
+    if stage == "match":   # per left keypoint: its descriptor and the result
         return (kps // 2) * (32 + 8)
-    return None
+    total = 0
+    for pr, p in zip(pairs, params):
+        px = level_pixels(pr.left.shape[1], pr.left.shape[0], p["levels"], p["scale"])
+        A = sum(px)
+        if stage == "pyramid":   # read L0, write raw levels >= 1, write every blurred level
+            total += 2 * (px[0] + (A - px[0]) + A)
+        else:                    # detect: read every raw level once
+            total += 2 * A
+    return total
 
 
 class ClockSampler:
@@ -196,25 +209,26 @@ def profiled_traffic(kernel, workload):
         return None
 
 
+def oracle_params(O, p, lo):
+    return O.FrontendParams(levels=p["levels"], scale=p["scale"], max_feats=p["max_feats"],
+                            fast_thresh=p["fast_thresh"], cell=p["cell"], fast_thresh_lo=lo)
+
+
 # ------------------------------------------------------------------ reference arm
 
 def run_reference(args, rank):
     if rank != 0:
         return
-    import numpy as np
     from oracle import oracle as O
-    jp, w = workload_params(args.workload)
-    p = O.FrontendParams(levels=jp["levels"], max_feats=jp["max_feats"], fast_thresh=jp["fast_thresh"],
-                         fast_thresh_lo=w["fast_thresh_lo"])
-    frames = make_frames(args.workload, min(args.steps + args.warmup, args.frames))
+    pairs, params, lo = make_workload(args.workload, min(args.frames, args.steps + args.warmup))
     for i in range(args.warmup):
-        fr = frames[i % len(frames)]
-        O.extract_pair(fr.left, fr.right, p)
+        k = i % len(pairs)
+        O.extract_pair(pairs[k].left, pairs[k].right, oracle_params(O, params[k], lo))
     times = []
     for i in range(args.steps):
-        fr = frames[(args.warmup + i) % len(frames)]
+        k = (args.warmup + i) % len(pairs)
         t0 = time.perf_counter()
-        O.extract_pair(fr.left, fr.right, p)
+        O.extract_pair(pairs[k].left, pairs[k].right, oracle_params(O, params[k], lo))
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = args.steps / total
@@ -223,27 +237,25 @@ def run_reference(args, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
-                       "step": "one stereo pair through the CPU oracle (bounded sample of the sequence)"},
+                       "step": "one stereo pair through the CPU oracle (bounded sample of the workload)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} stereo pairs of the sequence, one per step"},
+                             "sample": f"{args.steps} stereo pairs of the workload, one per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------ our arm
 
-def cpu_baseline(args, frames, jp, w):
+def cpu_baseline(args, pairs, params, lo):
     from oracle import oracle as O
-    p = O.FrontendParams(levels=jp["levels"], max_feats=jp["max_feats"], fast_thresh=jp["fast_thresh"],
-                         fast_thresh_lo=w["fast_thresh_lo"])
-    n = min(args.cpu_pairs, len(frames))
-    O.extract_pair(frames[0].left, frames[0].right, p)  # warm the library
+    n = min(args.cpu_pairs, len(pairs))
+    O.extract_pair(pairs[0].left, pairs[0].right, oracle_params(O, params[0], lo))  # warm the library
     t0 = time.perf_counter()
     for i in range(n):
-        O.extract_pair(frames[i].left, frames[i].right, p)
+        O.extract_pair(pairs[i].left, pairs[i].right, oracle_params(O, params[i], lo))
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n} stereo pairs of the sequence, single-threaded C oracle"}
+            "sample": f"first {n} stereo pairs of the workload, single-threaded C oracle"}
 
 
 def main():
@@ -255,7 +267,6 @@ def main():
         run_reference(args, rank)
         return
 
-    import numpy as np
     import torch
     from paper_2410_04090_gb300 import build as B
 
@@ -272,17 +283,18 @@ def main():
         B.build()
     from paper_2410_04090_gb300 import jslam
 
-    jp, w = workload_params(args.workload)
-    frames = make_frames(args.workload, args.frames)
-    W0, H0 = frames[0].left.shape[1], frames[0].left.shape[0]
+    pairs, params, lo = make_workload(args.workload, args.frames)
+    n = len(pairs)
     dev = torch.device("cuda", torch.cuda.current_device())
-    lefts = [torch.from_numpy(f.left).to(dev) for f in frames]
-    rights = [torch.from_numpy(f.right).to(dev) for f in frames]
+    lefts = [torch.from_numpy(f.left).to(dev) for f in pairs]
+    rights = [torch.from_numpy(f.right).to(dev) for f in pairs]
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)  # torch work (flush, events) and the library share this stream
-    fe = jslam.Frontend(device=dev.index, stream=stream, max_width=W0, max_height=H0, max_levels=8,
-                        max_feats=jp["max_feats"], max_pairs=args.frames, fast_thresh_lo=w["fast_thresh_lo"])
-    jobs = [jslam.Job(l, r, **jp) for l, r in zip(lefts, rights)]
+    dims = dict(max_width=max(p.left.shape[1] for p in pairs), max_height=max(p.left.shape[0] for p in pairs),
+                max_levels=8, max_feats=max(p["max_feats"] for p in params), max_pairs=n, fast_thresh_lo=lo)
+    fe = jslam.Frontend(device=dev.index, stream=stream, **dims)
+    jobs = fe.prepare_batch([jslam.Job(l, r, **p) for l, r, p in zip(lefts, rights, params)])
+    tuning = fe.autotune(jobs)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
 
     def step_batched():
@@ -290,9 +302,14 @@ def main():
         fe.match()
 
     def step_plain():
-        for l, r in zip(lefts, rights):
-            fe.extract(l, r, **jp)
+        for l, r, p in zip(lefts, rights, params):
+            fe.extract(l, r, **p)
             fe.match()
+
+    graph_fe = None
+
+    def step_graph():
+        graph_fe.graph_launch()
 
     def timed(step, k, on_step=None):
         total = 0.0
@@ -309,11 +326,15 @@ def main():
                 on_step()
         return total  # ms
 
-    modes = {"batched": step_batched, "plain": step_plain}
-    if args.only_batched:
+    modes = {"batched": step_batched}
+    if not args.only_batched:
+        graph_fe = jslam.Frontend(device=dev.index, stream=stream, **dims)
+        graph_fe.set_tuning(*tuning)
+        graph_fe.graph_capture(jobs)
+        modes["graph"] = step_graph
+        modes["plain"] = step_plain
+    if args.mode not in modes:
         args.mode = "batched"
-        modes = {"batched": step_batched}
-    main_step = modes[args.mode]
     for _ in range(args.warmup):
         for s in modes.values():
             s()
@@ -331,51 +352,55 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(dev.index) as clocks:
-        total_ms = timed(main_step, args.steps, grab)
-    fe.enable_stage_timing(False)
-    other = "plain" if args.mode == "batched" else "batched"
-    other_ms = timed(modes[other], args.steps) if other in modes else float("nan")
+    with ClockSampler(dev.index) as clocks:  # samples every timed region (all modes)
+        time.sleep(0.3)  # let the sampler start before the first timed step
+        total_ms = timed(modes[args.mode], args.steps, grab)
+        fe.enable_stage_timing(False)
+        other_ms = {m: timed(s, args.steps) for m, s in modes.items() if m != args.mode}
 
-    t = torch.tensor([total_ms, other_ms], dtype=torch.float64, device=dev)
+    t = torch.tensor([total_ms] + list(other_ms.values()), dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, other_ms = t.tolist()
-    pairs = args.frames * args.steps * world
-    value = pairs / (total_ms / 1e3)
+    vals = t.tolist()
+    total_ms = vals[0]
+    pairs_done = n * args.steps * world
+    value = pairs_done / (total_ms / 1e3)
     mode_values = {args.mode: value}
-    if other in modes:
-        mode_values[other] = pairs / (other_ms / 1e3)
+    for m, ms in zip(other_ms, vals[1:]):
+        mode_values[m] = pairs_done / (ms / 1e3)
 
     # keypoint counts of the last batch (for algorithmic bytes)
     fe.extract_batch(jobs); fe.match(); fe.sync()
-    counts = [fe.keypoints(p, s)["count"] for p in range(args.frames) for s in (0, 1)]
+    counts = [fe.keypoints(p, s)["count"] for p in range(n) for s in (0, 1)]
 
-    # end to end: pinned host images through the C ABI, result blocks back
-    e2e_value, h2d, d2h = None, 0, 0
+    e2e = None
     if not args.only_batched:
-        e2e_value, h2d, d2h = run_e2e(args, fe, frames, jp, jslam, torch, dist, dev, pairs)
+        e2e = run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done)
     if rank == 0:
-        emit(args, world, value, total_ms, mode_values, stage_acc, counts, W0, H0, jp, frames, w, e2e_value,
-             h2d, d2h, clocks)
+        emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks,
+             tuning)
     fe.close()
+    if graph_fe:
+        graph_fe.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
 
 
-def run_e2e(args, fe, frames, jp, jslam, torch, dist, dev, pairs):
-    host_l = [torch.from_numpy(f.left).pin_memory() for f in frames]
-    host_r = [torch.from_numpy(f.right).pin_memory() for f in frames]
-    hjobs = [jslam.Job(l.numpy(), r.numpy(), **jp) for l, r in zip(host_l, host_r)]
+def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done):
+    """Pinned host images in, result blocks out, through the C ABI."""
+    n = len(pairs)
+    host_l = [torch.from_numpy(f.left).pin_memory() for f in pairs]
+    host_r = [torch.from_numpy(f.right).pin_memory() for f in pairs]
+    hjobs = fe.prepare_batch([jslam.Job(l.numpy(), r.numpy(), **p) for l, r, p in zip(host_l, host_r, params)])
     fe.extract_batch(hjobs); fe.match(); fe.sync()
-    rb = [fe.result_bytes(p) for p in range(args.frames)]
-    outs = [torch.empty(n, dtype=torch.uint8).pin_memory() for n in rb]
+    rb = [fe.result_bytes(p) for p in range(n)]
+    outs = [torch.empty(b, dtype=torch.uint8).pin_memory() for b in rb]
 
     def step_e2e():
         fe.extract_batch(hjobs)
         fe.match()
-        for p in range(args.frames):
+        for p in range(n):
             fe.download(p, outs[p])
         fe.sync()
 
@@ -390,42 +415,37 @@ def run_e2e(args, fe, frames, jp, jslam, torch, dist, dev, pairs):
     te = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
     if dist:
         dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = pairs / te.item()
-    h2d = sum(f.left.nbytes + f.right.nbytes for f in frames)
-    d2h = sum(rb)
-    return e2e_value, h2d, d2h
+    return {"value": pairs_done / te.item(), "unit": UNIT,
+            "h2d_bytes_per_step": sum(f.left.nbytes + f.right.nbytes for f in pairs),
+            "d2h_bytes_per_step": sum(rb)}
 
 
-def emit(args, world, value, total_ms, mode_values, stage_acc, counts, W0, H0, jp, frames, w, e2e_value, h2d,
-     d2h, clocks):
+def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks, tuning):
     import numpy as np
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
     roof = None
     if args.mode == "batched" and any(stage_ms.values()):
-        dom = max((k for k in stage_ms if algorithmic_bytes(k, W0, H0, jp, 1, [1]) is not None),
+        dom = max((k for k in stage_ms if algorithmic_bytes(k, pairs[:1], params[:1], [1]) is not None),
                   key=lambda k: stage_ms[k])
-        alg = algorithmic_bytes(dom, W0, H0, jp, args.frames, counts)
+        alg = algorithmic_bytes(dom, pairs, params, counts)
         ach = alg / (stage_ms[dom] / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": KERNELS[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth",
                 "algorithmic_bytes_per_launch": alg,
                 "traffic": profiled_traffic(KERNELS[dom], args.workload),
                 "stage_ms_per_launch": stage_ms}
-    cpu = None if args.no_cpu_baseline else cpu_baseline(args, frames, jp, w)
-    launches_per_call = 6
-    gpu_launches = launches_per_call * args.steps * (1 if args.mode == "batched" else args.frames)
+    cpu = None if args.no_cpu_baseline else cpu_baseline(args, pairs, params, lo)
+    launches = {"batched": LAUNCHES_PER_CALL, "graph": LAUNCHES_PER_CALL, "plain": LAUNCHES_PER_CALL * n}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
-                       "frames_per_step": args.frames, "mode": args.mode,
+                       "pairs_per_step": n, "mode": args.mode, "detect_tile_px": list(tuning),
                        "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
             "modes": mode_values,
-            "roofline": roof, "cpu_baseline": cpu,
-            "e2e": None if e2e_value is None else
-                   {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "clocks": clocks.summary(), "gpu_launches": gpu_launches,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "clocks": clocks.summary(), "gpu_launches": launches[args.mode] * args.steps,
             "keypoints_per_image_mean": float(np.mean(counts))}
     print(json.dumps(line), flush=True)
 

@@ -214,6 +214,36 @@ jslam_status jslam_enable_stage_timing(jslam_ctx *ctx, int32_t enable);
  * Valid after jslam_sync(); JSLAM_ERR_STATE if timing was off. */
 jslam_status jslam_stage_times(jslam_ctx *ctx, float *ms /* JSLAM_NUM_STAGES entries */);
 
+/* Launch-shape tuning: the target detection tile in pixels (whole culling
+ * cells, so results never depend on it).  Defaults 128 x 64. */
+typedef struct {
+    int32_t tile_w_px;   /* 32..128, multiple of 4 */
+    int32_t tile_h_px;   /* 8..128 */
+} jslam_tuning;
+
+/* Use `t` for the following extractions (plans are rebuilt on change).
+ * JSLAM_ERR_ARG for values outside the ranges above. */
+jslam_status jslam_set_tuning(jslam_ctx *ctx, const jslam_tuning *t);
+
+/* Time the detection stage of the batch `jobs` (n pairs, as for
+ * jslam_extract_batch) under a set of candidate tile shapes with the stage
+ * events, keep the fastest for the context and return it in *out (may be
+ * NULL).  Runs the batch several times; results are unaffected. */
+jslam_status jslam_autotune(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n, jslam_tuning *out);
+
+/* Capture extraction + matching of the batch `jobs` into a CUDA graph owned
+ * by the context (the batch runs once uncaptured first, so that the plan
+ * and buffers exist).  Replays read the same input buffers: device images
+ * in place, host images (which must then be pinned) copied again.  The
+ * context stream must not be the legacy default stream.  Replaces any
+ * earlier graph. */
+jslam_status jslam_graph_capture(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n);
+
+/* Enqueue one replay of the captured graph on the context stream; results
+ * are read as after jslam_extract_batch + jslam_match.  JSLAM_ERR_STATE if
+ * nothing was captured. */
+jslam_status jslam_graph_launch(jslam_ctx *ctx);
+
 /* PFA scores of one image's culled corners, computed without allocating
  * device memory.  No counterpart in the paper: it exists for callers that
  * cannot call cudaMalloc -- a real-time loop that forbids allocation after

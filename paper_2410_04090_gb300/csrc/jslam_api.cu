@@ -188,6 +188,13 @@ struct jslam_ctx {
     bool timing = false;
     cudaEvent_t events[JSLAM_NUM_STAGES + 1] = {};
     bool stage_done[JSLAM_NUM_STAGES] = {};
+
+    // launch-shape tuning and the captured graph
+    jslam_tuning tune{128, 64};
+    jslam_tuning plan_tune{0, 0};  // tuning the current plan was built with
+    cudaGraphExec_t graph = nullptr;
+    int graph_pairs = 0;
+    bool graph_timed = false;  // the graph records the stage events
 };
 
 namespace {
@@ -229,15 +236,15 @@ jslam_status check_job(const jslam_ctx *ctx, const jslam_stereo_job &j)
     return JSLAM_OK;
 }
 
-// Cells per detection tile: about 128 x 64 pixels, capped in cells x k; the
-// tile width is kept a multiple of 4 pixels where possible so that tiles
-// start on word boundaries.
-void fast_block(int c, int k, int *bx, int *by)
+// Cells per detection tile: about tile_w x tile_h pixels (128 x 64 by
+// default), capped in cells x k; the tile width is kept a multiple of 4
+// pixels where possible so that tiles start on word boundaries.
+void fast_block(int c, int k, int tile_w, int tile_h, int *bx, int *by)
 {
-    int x = 128 / c > 1 ? 128 / c : 1;
+    int x = tile_w / c > 1 ? tile_w / c : 1;
     for (int cand = x; cand >= 1; --cand)
         if ((cand * c) % 4 == 0) { x = cand; break; }
-    int y = 64 / c > 1 ? 64 / c : 1;
+    int y = tile_h / c > 1 ? tile_h / c : 1;
     while (x * y * k > kFastMaxCellsPerCta) {
         if (y > 1) --y; else --x;
     }
@@ -259,7 +266,9 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
         const jslam_image *im[2] = { &jobs[p].left, &jobs[p].right };
         for (int s = 0; s < 2; ++s) k.mem[s] = im[s]->memory;
     }
-    if (keys == ctx->keys) return JSLAM_OK;
+    if (keys == ctx->keys && ctx->plan_tune.tile_w_px == ctx->tune.tile_w_px &&
+        ctx->plan_tune.tile_h_px == ctx->tune.tile_h_px)
+        return JSLAM_OK;
 
     const int n_img = 2 * n;
     const int k = cfg.k_per_cell;
@@ -286,7 +295,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 n_slots += cx * cy * k;
                 n_segs += cy;
                 int bx, by;
-                fast_block(g.c[l], k, &bx, &by);
+                fast_block(g.c[l], k, ctx->tune.tile_w_px, ctx->tune.tile_h_px, &bx, &by);
                 const int tw = std::min(bx * g.c[l], g.W[l]), th = std::min(by * g.c[l], g.H[l]);
                 int bw, bh;
                 detect_box(tw, th, &bw, &bh);
@@ -328,7 +337,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     for (int p = 0; p < n; ++p)
         for (int l = 0; l < geo[p].levels; ++l) {
             int bx, by;
-            fast_block(geo[p].c[l], k, &bx, &by);
+            fast_block(geo[p].c[l], k, ctx->tune.tile_w_px, ctx->tune.tile_h_px, &bx, &by);
             const int cx = (geo[p].W[l] + geo[p].c[l] - 1) / geo[p].c[l], cy = (geo[p].H[l] + geo[p].c[l] - 1) / geo[p].c[l];
             n_fast_tiles += 2 * (size_t)(((cx + bx - 1) / bx) * ((cy + by - 1) / by));
         }
@@ -393,7 +402,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 L.W = g.W[l]; L.H = g.H[l]; L.c = g.c[l];
                 L.cells_x = (L.W + L.c - 1) / L.c;
                 L.cells_y = (L.H + L.c - 1) / L.c;
-                fast_block(L.c, k, &L.bx, &L.by);
+                fast_block(L.c, k, ctx->tune.tile_w_px, ctx->tune.tile_h_px, &L.bx, &L.by);
                 L.cinv = (65536 + L.c - 1) / L.c;
                 detect_box(std::min(L.bx * L.c, L.W), std::min(L.by * L.c, L.H), &L.box_w, &L.box_h);
                 L.image = img; L.level = l;
@@ -494,6 +503,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.prm = ctx->prm;
 
     ctx->keys = keys;
+    ctx->plan_tune = ctx->tune;
     ctx->layouts = layouts;
     ctx->result_off = result_off;
     ctx->h_images.assign(images, images + n_img);
@@ -840,6 +850,86 @@ jslam_status jslam_stage_times(jslam_ctx *ctx, float *ms)
     return JSLAM_OK;
 }
 
+jslam_status jslam_set_tuning(jslam_ctx *ctx, const jslam_tuning *t)
+{
+    if (!ctx || !t) return JSLAM_ERR_ARG;
+    if (t->tile_w_px < 32 || t->tile_w_px > kFastMaxTile || t->tile_w_px % 4 != 0) return JSLAM_ERR_ARG;
+    if (t->tile_h_px < 8 || t->tile_h_px > kFastMaxTile) return JSLAM_ERR_ARG;
+    ctx->tune = *t;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_autotune(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n, jslam_tuning *out)
+{
+    if (!ctx || !jobs) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    static const jslam_tuning candidates[] = { { 128, 64 }, { 128, 32 }, { 128, 128 }, { 64, 64 }, { 64, 128 } };
+    const bool was_timing = ctx->timing;
+    jslam_status st = jslam_enable_stage_timing(ctx, 1);
+    if (st != JSLAM_OK) return st;
+    jslam_tuning best = ctx->tune;
+    float best_ms = -1.0f;
+    for (const jslam_tuning &cand : candidates) {
+        ctx->tune = cand;
+        float fastest = -1.0f;
+        for (int rep = 0; rep < 4; ++rep) {  // the first run builds the plan
+            if ((st = jslam_extract_batch(ctx, jobs, n)) != JSLAM_OK) break;
+            if ((st = jslam_sync(ctx)) != JSLAM_OK) break;
+            float ms[JSLAM_NUM_STAGES];
+            if ((st = jslam_stage_times(ctx, ms)) != JSLAM_OK) break;
+            if (rep > 0 && (fastest < 0 || ms[JSLAM_STAGE_DETECT] < fastest)) fastest = ms[JSLAM_STAGE_DETECT];
+        }
+        if (st != JSLAM_OK) break;
+        if (best_ms < 0 || fastest < best_ms) { best_ms = fastest; best = cand; }
+    }
+    ctx->tune = best;
+    if (st == JSLAM_OK) st = jslam_enable_stage_timing(ctx, was_timing ? 1 : 0);
+    if (st == JSLAM_OK && out) *out = best;
+    return st;
+}
+
+jslam_status jslam_graph_capture(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n)
+{
+    if (!ctx || !jobs) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (ctx->stream == nullptr || ctx->stream == cudaStreamLegacy) return JSLAM_ERR_STATE;
+    jslam_status st = jslam_extract_batch(ctx, jobs, n);  // plan, buffers, tables
+    if (st == JSLAM_OK) st = jslam_match(ctx);
+    if (st == JSLAM_OK) st = jslam_sync(ctx);
+    if (st != JSLAM_OK) return st;
+    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+    cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(ctx, e);
+    jslam_status cap = jslam_extract_batch(ctx, jobs, n);
+    if (cap == JSLAM_OK) cap = jslam_match(ctx);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(ctx->stream, &graph);
+    if (cap != JSLAM_OK) { if (graph) cudaGraphDestroy(graph); return cap; }
+    if (e != cudaSuccess) return fail(ctx, e);
+    e = cudaGraphInstantiate(&ctx->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { ctx->graph = nullptr; return fail(ctx, e); }
+    ctx->graph_pairs = n;
+    ctx->graph_timed = ctx->timing;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_graph_launch(jslam_ctx *ctx)
+{
+    if (!ctx) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (!ctx->graph) return JSLAM_ERR_STATE;
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, e);
+    ctx->have_extract = true;
+    ctx->have_match = true;
+    ctx->synced = false;
+    for (int i = 0; i < JSLAM_NUM_STAGES; ++i) ctx->stage_done[i] = ctx->graph_timed && ctx->timing;
+    return JSLAM_OK;
+}
+
 void jslam_destroy(jslam_ctx *ctx)
 {
     if (!ctx) return;
@@ -857,6 +947,7 @@ void jslam_destroy(jslam_ctx *ctx)
     if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
     for (cudaEvent_t ev : ctx->events)
         if (ev) cudaEventDestroy(ev);
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
     delete ctx;

@@ -90,8 +90,13 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
             const uint8_t *row = L0 + (size_t)min(max(y0 - 3 + r, 0), H - 1) * pitch0;
             const int gx = x0 - 4 + 4 * w;
             uint32_t v;
-            if (gx >= 0 && gx + 3 < W && (reinterpret_cast<uintptr_t>(row + gx) & 3u) == 0) {
-                v = __ldg(reinterpret_cast<const uint32_t *>(row + gx));
+            if (gx >= 0 && gx + 3 < W) {
+                // the two aligned words holding bytes gx .. gx + 3 (each holds
+                // at least one byte of the row, so neither leaves the buffer)
+                const uintptr_t a = reinterpret_cast<uintptr_t>(row + gx);
+                const uint32_t *p = reinterpret_cast<const uint32_t *>(a & ~static_cast<uintptr_t>(3));
+                const uint32_t sh = (uint32_t)(a & 3u) * 8u;
+                v = sh ? __funnelshift_r(__ldg(p), __ldg(p + 1), sh) : __ldg(p);
             } else {
                 v = 0;
 #pragma unroll
@@ -131,10 +136,17 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
             Hs[j][c] = (uint16_t)((256u - a) * __ldg(row + xa) + (uint32_t)a * __ldg(row + xb));
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < kPyrRows * kPyrCols; i += kPyrThreads) {
-            const int r = i / kPyrCols, c = i - r * kPyrCols;
-            const uint32_t w = wb[r];
-            raw[r][c] = (uint8_t)(((256u - w) * Hs[ia[r]][c] + w * Hs[ib[r]][c] + 32768u) >> 16);
+        // vertical interpolation, 4 columns per thread (16-bit taps read as words)
+        for (int i = threadIdx.x; i < kPyrRows * (kPyrCols / 4); i += kPyrThreads) {
+            const int r = i / (kPyrCols / 4), q = i - r * (kPyrCols / 4);
+            const uint32_t w = wb[r], w0 = 256u - w;
+            const uint2 ha = *reinterpret_cast<const uint2 *>(&Hs[ia[r]][4 * q]);
+            const uint2 hb = *reinterpret_cast<const uint2 *>(&Hs[ib[r]][4 * q]);
+            const uint32_t v0 = (w0 * (ha.x & 0xFFFFu) + w * (hb.x & 0xFFFFu) + 32768u) >> 16;
+            const uint32_t v1 = (w0 * (ha.x >> 16) + w * (hb.x >> 16) + 32768u) >> 16;
+            const uint32_t v2 = (w0 * (ha.y & 0xFFFFu) + w * (hb.y & 0xFFFFu) + 32768u) >> 16;
+            const uint32_t v3 = (w0 * (ha.y >> 16) + w * (hb.y >> 16) + 32768u) >> 16;
+            *reinterpret_cast<uint32_t *>(&raw[r][4 * q]) = v0 | (v1 << 8) | (v2 << 16) | (v3 << 24);
         }
     }
     __syncthreads();

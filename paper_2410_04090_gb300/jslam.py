@@ -49,6 +49,10 @@ class StereoJob(C.Structure):
                 ("fast_thresh", C.c_int32), ("cell", C.c_int32), ("max_feats", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("tile_w_px", C.c_int32), ("tile_h_px", C.c_int32)]
+
+
 class Keypoints(C.Structure):
     _fields_ = [("count", C.c_int32), ("capacity", C.c_int32),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("X", C.c_void_p), ("Y", C.c_void_p),
@@ -79,7 +83,8 @@ SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extra
            "jslam_sync", "jslam_get_keypoints", "jslam_get_matches", "jslam_get_level", "jslam_result_bytes",
            "jslam_download", "jslam_result_view", "jslam_destroy", "jslam_status_str", "jslam_pattern_table",
            "jslam_level_geometry", "jslam_project", "jslam_match_band", "jslam_enable_stage_timing",
-           "jslam_stage_times", "jslam_pfa_scores_static", "jslam_corner_table")
+           "jslam_stage_times", "jslam_pfa_scores_static", "jslam_corner_table", "jslam_set_tuning",
+           "jslam_autotune", "jslam_graph_capture", "jslam_graph_launch")
 STAGES = ("pyramid", "detect", "pfa_nms", "pfa_final", "orb", "match")
 
 _lib = None
@@ -131,6 +136,14 @@ def lib():
         L.jslam_project.restype = C.c_int32
         L.jslam_match_band.argtypes = [C.c_int32, C.c_float, C.c_int32]
         L.jslam_match_band.restype = C.c_int32
+        L.jslam_set_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
+        L.jslam_set_tuning.restype = st
+        L.jslam_autotune.argtypes = [C.c_void_p, C.POINTER(StereoJob), C.c_int32, C.POINTER(Tuning)]
+        L.jslam_autotune.restype = st
+        L.jslam_graph_capture.argtypes = [C.c_void_p, C.POINTER(StereoJob), C.c_int32]
+        L.jslam_graph_capture.restype = st
+        L.jslam_graph_launch.argtypes = [C.c_void_p]
+        L.jslam_graph_launch.restype = st
         L.jslam_corner_table.argtypes = [C.c_int32, C.c_int32, C.c_void_p]
         L.jslam_corner_table.restype = st
         L.jslam_enable_stage_timing.argtypes = [C.c_void_p, C.c_int32]
@@ -249,6 +262,18 @@ class Job:
     max_feats: int = 2000
 
 
+class PreparedBatch:
+    """A marshalled jslam_stereo_job array (keeps its images alive)."""
+
+    def __init__(self, jobs):
+        self.jobs = tuple(jobs)
+        self.n = len(self.jobs)
+        self.array = (StereoJob * self.n)()
+        for i, j in enumerate(self.jobs):
+            self.array[i] = StereoJob(_image(j.left), _image(j.right), j.levels, j.scale, j.fast_thresh, j.cell,
+                                      j.max_feats)
+
+
 class Frontend:
     """One libjslam context (one device, one stream)."""
 
@@ -295,15 +320,37 @@ class Frontend:
         self._keep = (left, right)
         _check(lib().jslam_extract(self._h, li, ri, levels, scale, fast_thresh, cell, max_feats), "jslam_extract")
 
+    def prepare_batch(self, jobs) -> "PreparedBatch":
+        """Marshal a list of Job once, for repeated extract_batch calls on the
+        same buffers (the tensors must stay alive and in place)."""
+        return PreparedBatch(jobs)
+
     def extract_batch(self, jobs):
-        arr = (StereoJob * len(jobs))()
-        for i, j in enumerate(jobs):
-            arr[i] = StereoJob(_image(j.left), _image(j.right), j.levels, j.scale, j.fast_thresh, j.cell, j.max_feats)
-        self._keep = tuple(jobs)
-        _check(lib().jslam_extract_batch(self._h, arr, len(jobs)), "jslam_extract_batch")
+        pb = jobs if isinstance(jobs, PreparedBatch) else PreparedBatch(jobs)
+        self._keep = pb
+        _check(lib().jslam_extract_batch(self._h, pb.array, pb.n), "jslam_extract_batch")
 
     def match(self):
         _check(lib().jslam_match(self._h), "jslam_match")
+
+    def set_tuning(self, tile_w_px: int, tile_h_px: int):
+        t = Tuning(tile_w_px, tile_h_px)
+        _check(lib().jslam_set_tuning(self._h, C.byref(t)), "jslam_set_tuning")
+
+    def autotune(self, jobs) -> tuple:
+        pb = jobs if isinstance(jobs, PreparedBatch) else PreparedBatch(jobs)
+        self._keep = pb
+        t = Tuning()
+        _check(lib().jslam_autotune(self._h, pb.array, pb.n, C.byref(t)), "jslam_autotune")
+        return t.tile_w_px, t.tile_h_px
+
+    def graph_capture(self, jobs):
+        pb = jobs if isinstance(jobs, PreparedBatch) else PreparedBatch(jobs)
+        self._graph_keep = pb
+        _check(lib().jslam_graph_capture(self._h, pb.array, pb.n), "jslam_graph_capture")
+
+    def graph_launch(self):
+        _check(lib().jslam_graph_launch(self._h), "jslam_graph_launch")
 
     def sync(self):
         _check(lib().jslam_sync(self._h), "jslam_sync")

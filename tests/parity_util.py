@@ -14,8 +14,8 @@ def params_from(oracle, **kw):
     return p
 
 
-def frontend_for(J, p, max_width=1920, max_height=1080, max_pairs=16, max_feats=None):
-    return J.Frontend(device=0, max_width=max_width, max_height=max_height, max_levels=8,
+def frontend_for(J, p, max_width=1920, max_height=1080, max_pairs=16, max_feats=None, stream=None):
+    return J.Frontend(device=0, stream=stream, max_width=max_width, max_height=max_height, max_levels=8,
                       max_feats=max_feats or max(p.max_feats, 4000), max_pairs=max_pairs,
                       fast_thresh_lo=p.fast_thresh_lo, p_min=p.p_min, p_max=p.p_max,
                       k_per_cell=p.k_per_cell, nms_q=p.nms_q, border=p.border, max_disp=p.max_disp,

@@ -285,3 +285,66 @@ def test_shared_torch_streams(J, oracle):
         compare_keypoints(jslam.to_numpy(fe.keypoints(0, 0)), ol, "left")
         compare_matches(jslam.to_numpy(fe.matches(0)), om)
         fe.close()
+
+
+@pytest.mark.parametrize("tune", [(32, 8), (64, 128), (128, 128), (128, 32)])
+def test_tuning_does_not_change_results(J, oracle, tune):
+    pair = scenes.planes_pair(501, 333, 0, 55, 56)
+    p = params_from(oracle, levels=6, max_feats=900, fast_thresh_lo=7)
+    fe = frontend_for(J, p)
+    fe.set_tuning(*tune)
+    _check_pair(J, oracle, pair.left, pair.right, p, fe=fe)
+    fe.close()
+
+
+def _mixed_streams(J, specs, frame):
+    import torch
+    pairs, jobs = [], []
+    for i, sp in enumerate(specs):
+        pr = scenes.stereo_pair(sp["kind"], sp["width"], sp["height"], frame=frame, stream=i, config_id=4)
+        pairs.append(pr)
+        jobs.append(J.Job(torch.from_numpy(pr.left).cuda(), torch.from_numpy(pr.right).cuda(), sp["levels"], 1.2, 20,
+                          32, sp["max_feats"]))
+    return pairs, jobs
+
+
+def _check_batch(J, oracle, fe, pairs, specs):
+    for i, (pr, sp) in enumerate(zip(pairs, specs)):
+        p = params_from(oracle, levels=sp["levels"], max_feats=sp["max_feats"], fast_thresh_lo=7)
+        ol, orr, om = oracle.extract_pair(pr.left, pr.right, p)
+        compare_keypoints(J.to_numpy(fe.keypoints(i, 0)), ol, f"pair {i} left")
+        compare_keypoints(J.to_numpy(fe.keypoints(i, 1)), orr, f"pair {i} right")
+        compare_matches(J.to_numpy(fe.matches(i)), om, f"pair {i}")
+
+
+def test_mixed_sixteen_streams(J, oracle):
+    """The mixed multi-stream batch: 4 streams each of 640x480 (4 levels),
+    752x480 (5), 1241x376 (6) and 1920x1080 (8), autotuned, in one launch set."""
+    specs = scenes.MIXED_STREAMS
+    fe = frontend_for(J, params_from(oracle, fast_thresh_lo=7), max_pairs=16)
+    pairs, jobs = _mixed_streams(J, specs, 0)
+    tile = fe.autotune(jobs)
+    assert tile[0] in (64, 128) and tile[1] in (32, 64, 128)
+    fe.extract_batch(jobs)
+    fe.match()
+    fe.sync()
+    _check_batch(J, oracle, fe, pairs, specs)
+    fe.close()
+
+
+def test_graph_replay_follows_new_frames(J, oracle):
+    import torch
+    specs = scenes.MIXED_STREAMS[::4]  # one stream of each size
+    fe = frontend_for(J, params_from(oracle, fast_thresh_lo=7), max_pairs=4, stream=torch.cuda.Stream())
+    pairs, jobs = _mixed_streams(J, specs, 0)
+    fe.graph_capture(jobs)
+    for frame in (1, 2):
+        nxt, _ = _mixed_streams(J, specs, frame)
+        for j, pr in zip(jobs, nxt):  # new frames into the captured buffers
+            j.left.copy_(torch.from_numpy(pr.left))
+            j.right.copy_(torch.from_numpy(pr.right))
+        torch.cuda.synchronize()
+        fe.graph_launch()
+        fe.sync()
+        _check_batch(J, oracle, fe, nxt, specs)
+    fe.close()
