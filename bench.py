@@ -58,7 +58,8 @@ KERNELS = {"pyramid": "k_pyramid", "detect": "k_fast_cull", "pfa_nms": "k_pfa_nm
            "pfa_final": "k_pfa_finalize", "orb": "k_orient_desc", "match": "k_match"}
 KERNEL_SOURCES = {"k_pyramid": "k_detect.cu", "k_fast_cull": "k_detect.cu", "k_pfa_nms": "k_pyca.cu",
                   "k_pfa_finalize": "k_pyca.cu", "k_orient_desc": "k_orb_match.cu", "k_match": "k_orb_match.cu"}
-LAUNCHES_PER_CALL = 6  # pyramid, detect, PFA NMS, PFA final, ORB, match
+LAUNCHES_PER_CALL = 6  # pyramid, detect, PFA NMS, PFA final, ORB, match (exact path)
+SKIP_MODEL = os.path.join(ROOT, "paper_2410_04090_gb300", "skipnet_v1.bin")
 
 
 def parse_args():
@@ -326,7 +327,19 @@ def main():
                 on_step()
         return total  # ms
 
+    skip_fe = None
+
+    def step_skip():
+        skip_fe.extract_batch(jobs)
+        skip_fe.match()
+
     modes = {"batched": step_batched}
+    if not args.only_batched and os.path.exists(SKIP_MODEL):
+        skip_fe = jslam.Frontend(device=dev.index, stream=stream, **dims)
+        skip_fe.set_tuning(*tuning)
+        skip_fe.set_skip_model(open(SKIP_MODEL, "rb").read(),
+                               json.load(open(os.path.splitext(SKIP_MODEL)[0] + ".json"))["thresh"])
+        modes["learned_skip"] = step_skip
     if not args.only_batched:
         graph_fe = jslam.Frontend(device=dev.index, stream=stream, **dims)
         graph_fe.set_tuning(*tuning)
@@ -372,16 +385,31 @@ def main():
     # keypoint counts of the last batch (for algorithmic bytes)
     fe.extract_batch(jobs); fe.match(); fe.sync()
     counts = [fe.keypoints(p, s)["count"] for p in range(n) for s in (0, 1)]
+    skip_quality = None
+    if skip_fe:
+        skip_fe.extract_batch(jobs); skip_fe.sync()
+        inter = total = kept = 0
+        skipped = []
+        for p in range(n):
+            skipped.append(float(skip_fe.skip_view(p, 0)["skip"].float().mean()))
+            for s in (0, 1):
+                a = jslam.to_numpy(fe.keypoints(p, s)); b = jslam.to_numpy(skip_fe.keypoints(p, s))
+                ka = set(zip(a["level"].tolist(), a["y"].tolist(), a["x"].tolist()))
+                kb = set(zip(b["level"].tolist(), b["y"].tolist(), b["x"].tolist()))
+                inter += len(ka & kb); total += len(ka); kept += len(kb)
+        skip_quality = {"recall": inter / max(total, 1), "precision": inter / max(kept, 1),
+                        "cells_skipped": sum(skipped) / len(skipped), "model": os.path.basename(SKIP_MODEL)}
 
     e2e = None
     if not args.only_batched:
         e2e = run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done)
     if rank == 0:
         emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks,
-             tuning)
+             tuning, skip_quality)
     fe.close()
-    if graph_fe:
-        graph_fe.close()
+    for extra in (graph_fe, skip_fe):
+        if extra:
+            extra.close()
     if dist:
         dist.barrier()
         dist.destroy_process_group()
@@ -420,7 +448,8 @@ def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done):
             "d2h_bytes_per_step": sum(rb)}
 
 
-def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks, tuning):
+def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks, tuning,
+         skip_quality):
     import numpy as np
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
@@ -436,14 +465,15 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
                 "traffic": profiled_traffic(KERNELS[dom], args.workload),
                 "stage_ms_per_launch": stage_ms}
     cpu = None if args.no_cpu_baseline else cpu_baseline(args, pairs, params, lo)
-    launches = {"batched": LAUNCHES_PER_CALL, "graph": LAUNCHES_PER_CALL, "plain": LAUNCHES_PER_CALL * n}
+    launches = {"batched": LAUNCHES_PER_CALL, "graph": LAUNCHES_PER_CALL, "plain": LAUNCHES_PER_CALL * n,
+                "learned_skip": LAUNCHES_PER_CALL + 2}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
                        "pairs_per_step": n, "mode": args.mode, "detect_tile_px": list(tuning),
                        "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
-            "modes": mode_values,
+            "modes": mode_values, "learned_skip": skip_quality,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks.summary(), "gpu_launches": launches[args.mode] * args.steps,
             "keypoints_per_image_mean": float(np.mean(counts))}

@@ -196,12 +196,13 @@ jslam_status jslam_result_view(jslam_ctx *ctx, int32_t pair, const void *block, 
 /* Stages of the launch sequence, in launch order. */
 enum {
     JSLAM_STAGE_PYRAMID = 0,      /* pyramid + Gaussian filter */
-    JSLAM_STAGE_DETECT = 1,       /* FAST + Bounded Rectification + cell culling + PFA scatter */
-    JSLAM_STAGE_PFA_NMS = 2,      /* PFA sparse NMS and per-row ranking */
-    JSLAM_STAGE_PFA_FINAL = 3,    /* PFA aggregation, cap, canonical compaction */
-    JSLAM_STAGE_ORB = 4,          /* orientation + descriptors */
-    JSLAM_STAGE_MATCH = 5,        /* stereo row matching */
-    JSLAM_NUM_STAGES = 6
+    JSLAM_STAGE_SKIP = 1,         /* learned cell-skip proposal (0 ms in exact mode) */
+    JSLAM_STAGE_DETECT = 2,       /* FAST + Bounded Rectification + cell culling + PFA scatter */
+    JSLAM_STAGE_PFA_NMS = 3,      /* PFA sparse NMS and per-row ranking */
+    JSLAM_STAGE_PFA_FINAL = 4,    /* PFA aggregation, cap, canonical compaction */
+    JSLAM_STAGE_ORB = 5,          /* orientation + descriptors */
+    JSLAM_STAGE_MATCH = 6,        /* stereo row matching */
+    JSLAM_NUM_STAGES = 7
 };
 
 /* Turn per-stage timing on or off.  When on, every extraction and match
@@ -276,6 +277,28 @@ jslam_status jslam_pfa_scores_static(const uint8_t *level, const uint16_t *x, co
                                      int32_t levels, float scale, int32_t nms_q, int32_t pfa_rule,
                                      uint16_t *X, uint16_t *Y, uint8_t *k_levels, uint32_t *k_resp,
                                      uint8_t *alive, int32_t device, void *cuda_stream);
+
+/* Learned cell-skip proposal (opt-in, approximate; no counterpart in the
+ * paper).  `blob` holds a versioned model: the 16-byte header
+ * {"JSKP", version 1, channels 16, downsample 8} (little-endian uint32
+ * fields after the 4 magic bytes), then FP32 biases b1[16], b2[16], b3[1],
+ * then BF16 weights w1[16][1][3][3], w2[16][16][3][3], w3[1][16][3][3] of
+ * three 3x3 convolutions (zero padding, ReLU after the first two) applied to
+ * the 8x8 box mean of level 0 scaled to [-0.5, 0.5].  An s0 culling cell
+ * whose largest logit is below `thresh` is skipped: detection ignores every
+ * cell of every level whose centre projects into it.  blob == NULL returns
+ * to the exact path.  JSLAM_ERR_ARG for a malformed blob. */
+jslam_status jslam_set_skip_model(jslam_ctx *ctx, const void *blob, size_t bytes, float thresh);
+
+/* Device views of the skip proposal of `side` of pair `pair` (after an
+ * extraction in skip mode): the 1/8-scale logits (h8 x w8 floats) and the
+ * per-cell skip flags (cells_y x cells_x bytes, 1 = skipped). */
+typedef struct {
+    int32_t w8, h8, cells_x, cells_y;
+    const float *logits;
+    const uint8_t *skip;
+} jslam_skip_view;
+jslam_status jslam_get_skip_view(jslam_ctx *ctx, int32_t pair, int32_t side, jslam_skip_view *out);
 
 /* Release the context and everything it owns.  NULL is ignored. */
 void jslam_destroy(jslam_ctx *ctx);

@@ -12,7 +12,7 @@
 #include "tables.h"
 
 namespace jslam {
-int fast_smem_bytes(int max_box, int max_px, int max_cells, int k);
+int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, bool skip);
 }
 
 using namespace jslam;
@@ -189,6 +189,13 @@ struct jslam_ctx {
     cudaEvent_t events[JSLAM_NUM_STAGES + 1] = {};
     bool stage_done[JSLAM_NUM_STAGES] = {};
 
+    // learned cell-skip model
+    GrowBuf skipw, skipbuf;
+    SkipModelDev skip_model{};
+    bool skip_on = false;
+    float skip_thresh = 0.0f;
+    bool plan_skip = false;  // the current plan has skip buffers
+
     // launch-shape tuning and the captured graph
     jslam_tuning tune{128, 64};
     jslam_tuning plan_tune{0, 0};  // tuning the current plan was built with
@@ -267,7 +274,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
         for (int s = 0; s < 2; ++s) k.mem[s] = im[s]->memory;
     }
     if (keys == ctx->keys && ctx->plan_tune.tile_w_px == ctx->tune.tile_w_px &&
-        ctx->plan_tune.tile_h_px == ctx->tune.tile_h_px)
+        ctx->plan_tune.tile_h_px == ctx->tune.tile_h_px && ctx->plan_skip == ctx->skip_on)
         return JSLAM_OK;
 
     const int n_img = 2 * n;
@@ -319,6 +326,20 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     for (int p = 0; p < n; ++p)
         any_host |= jobs[p].left.memory == JSLAM_MEM_HOST || jobs[p].right.memory == JSLAM_MEM_HOST;
     if (any_host && (e = ctx->staging.ensure(staging_bytes + 256, false, nullptr)) != cudaSuccess) return fail(ctx, e);
+    // learned cell-skip buffers: logits at 1/8 scale and per-s0-cell flags
+    size_t skip_bytes = 0;
+    int skip_max_tiles = 0, skip_max_cells = 0;
+    if (ctx->skip_on) {
+        for (int p = 0; p < n; ++p) {
+            const int w8 = (geo[p].W[0] + 7) / 8, h8 = (geo[p].H[0] + 7) / 8;
+            const int cx = (geo[p].W[0] + jobs[p].cell - 1) / jobs[p].cell, cy = (geo[p].H[0] + jobs[p].cell - 1) / jobs[p].cell;
+            skip_bytes += 2 * (align_up((size_t)w8 * h8 * 4, 256) + align_up((size_t)cx * cy, 256));
+            skip_max_tiles = std::max(skip_max_tiles, ((w8 + kSkipTile - 1) / kSkipTile) * ((h8 + kSkipTile - 1) / kSkipTile));
+            skip_max_cells = std::max(skip_max_cells, cx * cy);
+        }
+        if ((e = ctx->skipbuf.ensure(skip_bytes + 256, false, nullptr)) != cudaSuccess) return fail(ctx, e);
+    }
+    size_t skip_off = 0;
     const size_t slot_words = (size_t)n_slots + 64;
     const size_t seg_words = (size_t)n_segs + 64;
     const size_t scratch_bytes = slot_words * 4 * 4 + seg_words * 4 * 2;
@@ -381,6 +402,19 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
             I.map = ctx->maps.as<uint32_t>(map_off);
             map_off += align_up((size_t)g.W[0] * g.H[0] * 4, 256);
             I.count = dcounts + img;
+            I.skip = nullptr;
+            I.skip_logits = nullptr;
+            I.skip_w8 = (g.W[0] + 7) / 8;
+            I.skip_h8 = (g.H[0] + 7) / 8;
+            I.skip_c0 = jobs[p].cell;
+            I.skip_cells_x = (g.W[0] + jobs[p].cell - 1) / jobs[p].cell;
+            I.skip_cells_y = (g.H[0] + jobs[p].cell - 1) / jobs[p].cell;
+            if (ctx->skip_on) {
+                I.skip_logits = ctx->skipbuf.as<float>(skip_off);
+                skip_off += align_up((size_t)I.skip_w8 * I.skip_h8 * 4, 256);
+                I.skip = ctx->skipbuf.as<uint8_t>(skip_off);
+                skip_off += align_up((size_t)I.skip_cells_x * I.skip_cells_y, 256);
+            }
             I.level_start = reinterpret_cast<int32_t *>(dplan + o_lstart) + img * (kMaxLevels + 1);
             const SideLayout &sl = pl.side[s];
             I.out.capacity = pl.capacity;
@@ -487,8 +521,10 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.n_images = n_img; b.n_levels = n_levels; b.n_pairs = n; b.n_segments = n_segs;
     b.pyr_tiles = pyr; b.fast_tiles = fast; b.max_capacity = max_cap;
     b.fast_max_box = max_box; b.fast_max_px = max_px; b.fast_max_cells = max_cells;
-    b.fast_smem = fast_smem_bytes(max_box, max_px, max_cells, k);
+    b.fast_smem = fast_smem_bytes(max_box, max_px, max_cells, k, skip_max_tiles > 0);
     b.corner_lut = ctx->d_lut;
+    b.skip_max_tiles = skip_max_tiles;
+    b.skip_max_cells = skip_max_cells;
     uint32_t *sw = ctx->scratch.as<uint32_t>();
     b.slots = sw;
     b.slot_k = sw + slot_words;
@@ -504,6 +540,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
 
     ctx->keys = keys;
     ctx->plan_tune = ctx->tune;
+    ctx->plan_skip = ctx->skip_on;
     ctx->layouts = layouts;
     ctx->result_off = result_off;
     ctx->h_images.assign(images, images + n_img);
@@ -590,6 +627,7 @@ jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
         }
     }
     if (e == cudaSuccess) e = configure_kernels();
+    if (e == cudaSuccess) e = configure_skipnet();
     int32_t w[7];
     blur_weights(w);
     if (e == cudaSuccess) e = set_blur_weights(w);
@@ -662,12 +700,20 @@ jslam_status jslam_extract_batch(jslam_ctx *ctx, const jslam_stereo_job *jobs, i
         }
     }
     cudaError_t e;
-    cudaError_t (*const stages[])(const Batch &, cudaStream_t) = {
-        launch_pyramid, launch_fast_cull, launch_pfa_nms, launch_pfa_finalize, launch_orient_desc };
     for (bool &d : ctx->stage_done) d = false;
     if (ctx->timing && (e = cudaEventRecord(ctx->events[0], ctx->stream)) != cudaSuccess) return fail(ctx, e);
     for (int i = 0; i < JSLAM_STAGE_MATCH; ++i) {
-        if ((e = stages[i](b, ctx->stream)) != cudaSuccess) return fail(ctx, e);
+        switch (i) {
+        case JSLAM_STAGE_PYRAMID: e = launch_pyramid(b, ctx->stream); break;
+        case JSLAM_STAGE_SKIP:
+            e = ctx->skip_on ? launch_skipnet(b, ctx->skip_model, ctx->skip_thresh, ctx->stream) : cudaSuccess;
+            break;
+        case JSLAM_STAGE_DETECT: e = launch_fast_cull(b, ctx->stream); break;
+        case JSLAM_STAGE_PFA_NMS: e = launch_pfa_nms(b, ctx->stream); break;
+        case JSLAM_STAGE_PFA_FINAL: e = launch_pfa_finalize(b, ctx->stream); break;
+        default: e = launch_orient_desc(b, ctx->stream); break;
+        }
+        if (e != cudaSuccess) return fail(ctx, e);
         if (ctx->timing) {
             if ((e = cudaEventRecord(ctx->events[i + 1], ctx->stream)) != cudaSuccess) return fail(ctx, e);
             ctx->stage_done[i] = true;
@@ -850,6 +896,56 @@ jslam_status jslam_stage_times(jslam_ctx *ctx, float *ms)
     return JSLAM_OK;
 }
 
+jslam_status jslam_set_skip_model(jslam_ctx *ctx, const void *blob, size_t bytes, float thresh)
+{
+    if (!ctx) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (!blob) {
+        ctx->skip_on = false;
+        return JSLAM_OK;
+    }
+    constexpr size_t kHeader = 16, kBias = (2 * kSkipC + 1) * sizeof(float);
+    constexpr size_t kW1 = kSkipC * 9, kW2 = kSkipC * kSkipC * 9, kW3 = kSkipC * 9;
+    constexpr size_t kBytes = kHeader + kBias + 2 * (kW1 + kW2 + kW3);
+    const uint8_t *p = static_cast<const uint8_t *>(blob);
+    uint32_t hdr[3];
+    if (bytes != kBytes || std::memcmp(p, "JSKP", 4) != 0) return JSLAM_ERR_ARG;
+    std::memcpy(hdr, p + 4, sizeof(hdr));
+    if (hdr[0] != 1 || hdr[1] != (uint32_t)kSkipC || hdr[2] != 8) return JSLAM_ERR_ARG;
+    if (!(thresh == thresh)) return JSLAM_ERR_ARG;  // NaN
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    cudaError_t e = ctx->skipw.ensure(kBytes + 256, false, nullptr);
+    if (e != cudaSuccess) return fail(ctx, e);
+    // device layout: biases (FP32) first, then the BF16 weights
+    e = cudaMemcpy(ctx->skipw.ptr, p + kHeader, kBytes - kHeader, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(ctx, e);
+    float b3 = 0.0f;
+    std::memcpy(&b3, p + kHeader + 2 * kSkipC * sizeof(float), sizeof(float));
+    SkipModelDev &m = ctx->skip_model;
+    m.b1 = ctx->skipw.as<float>(0);
+    m.b2 = ctx->skipw.as<float>(kSkipC * sizeof(float));
+    m.b3 = b3;
+    m.w1 = ctx->skipw.as<uint16_t>(kBias);
+    m.w2 = m.w1 + kW1;
+    m.w3 = m.w2 + kW2;
+    ctx->skip_thresh = thresh;
+    ctx->skip_on = true;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_get_skip_view(jslam_ctx *ctx, int32_t pair, int32_t side, jslam_skip_view *out)
+{
+    if (!ctx || !out) return JSLAM_ERR_ARG;
+    if (!ctx->have_extract || !ctx->plan_skip) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size() || side < 0 || side > 1) return JSLAM_ERR_ARG;
+    const ImageDesc &I = ctx->h_images[2 * pair + side];
+    out->w8 = I.skip_w8; out->h8 = I.skip_h8;
+    out->cells_x = I.skip_cells_x; out->cells_y = I.skip_cells_y;
+    out->logits = I.skip_logits; out->skip = I.skip;
+    return JSLAM_OK;
+}
+
 jslam_status jslam_set_tuning(jslam_ctx *ctx, const jslam_tuning *t)
 {
     if (!ctx || !t) return JSLAM_ERR_ARG;
@@ -944,6 +1040,8 @@ void jslam_destroy(jslam_ctx *ctx)
     ctx->results.release();
     ctx->staging.release();
     ctx->counts.release();
+    ctx->skipw.release();
+    ctx->skipbuf.release();
     if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
     for (cudaEvent_t ev : ctx->events)
         if (ev) cudaEventDestroy(ev);

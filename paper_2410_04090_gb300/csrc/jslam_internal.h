@@ -30,6 +30,8 @@ constexpr int kPyrTW = 128, kPyrTH = 32, kPyrThreads = 256;
 constexpr int kFastMaxTile = 128, kFastThreads = 256;
 constexpr int kFastMaxCellsPerCta = 2048;  // cells x k per CTA
 constexpr int kLutWords = 2048;            // 2^16-entry corner bit table
+constexpr int kSkipC = 16;                 // channels of the learned cell-skip net
+constexpr int kSkipTile = 14;              // its logits per CTA side
 constexpr int kNmsThreads = 128;
 constexpr int kFinThreads = 1024;
 
@@ -79,6 +81,17 @@ struct ImageDesc {
     int32_t *count;          // keypoint count written by finalisation
     int32_t *level_start;    // kMaxLevels + 1 entries
     KpOut out;
+    // learned cell-skip (skip == nullptr: exact mode)
+    float *skip_logits;      // skip_h8 x skip_w8 logits at 1/8 scale
+    uint8_t *skip;           // per s0 culling cell: 1 = skipped
+    int32_t skip_w8, skip_h8, skip_cells_x, skip_cells_y, skip_c0;
+};
+
+// Device copy of the skip net: BF16 weights, FP32 biases.
+struct SkipModelDev {
+    const uint16_t *w1, *w2, *w3;  // [16][9], [16][16][9], [16][9]
+    const float *b1, *b2;          // [16], [16]
+    float b3;
 };
 
 struct PairDesc {
@@ -127,6 +140,7 @@ struct Batch {
     const double *bin_cos, *bin_sin;
     uint32_t *err;
     Params prm;
+    int32_t skip_max_tiles, skip_max_cells;  // learned cell-skip launch shape
     Inputs in;
 };
 
@@ -137,7 +151,10 @@ cudaError_t launch_pfa_nms(const Batch &b, cudaStream_t stream);
 cudaError_t launch_pfa_finalize(const Batch &b, cudaStream_t stream);
 cudaError_t launch_orient_desc(const Batch &b, cudaStream_t stream);
 cudaError_t launch_match(const Batch &b, cudaStream_t stream);
+cudaError_t launch_skipnet(const Batch &b, const SkipModelDev &m, float thresh, cudaStream_t stream);
 cudaError_t set_blur_weights(const int32_t w[7]);
 cudaError_t configure_kernels();
+cudaError_t configure_skipnet();
+int skipnet_smem_bytes();
 
 }  // namespace jslam

@@ -238,12 +238,15 @@ constexpr uint32_t kH = 0x80808080u, kL7 = 0x7F7F7F7Fu;
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
 
 struct FastLayout {
-    int buf0, buf1, clist, ckey, has_hi, sel, bar, total;
+    int buf0, buf1, clist, ckey, glist, has_hi, sel, bar, total;
 };
 
 __host__ __device__ inline int fast_align(int v, int a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int max_cells, int k)
+// `skip`: the learned cell-skip proposal is on, which adds the list of
+// pixel groups that touch a cell it keeps (a group is 4 pixels of a row;
+// a tile row of at most kFastMaxTile pixels has at most kFastMaxTile / 4).
+__host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int max_cells, int k, bool skip)
 {
     FastLayout l;
     int o = kLutWords * 4;
@@ -251,6 +254,7 @@ __host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int m
     l.buf1 = o;  o += fast_align(max_box, 128);
     l.clist = o; o += fast_align(max_px * 2, 16);
     l.ckey = o;  o += k > 1 ? fast_align(max_px * 4, 16) : 0;
+    l.glist = o; o += skip ? fast_align((max_px / 4 + kFastMaxTile) * 2, 16) : 0;
     l.has_hi = o; o += fast_align(max_cells, 16);
     l.sel = o;   o += fast_align(max_cells * k * 4, 16);
     l.bar = o;   o += 16;
@@ -390,13 +394,14 @@ __device__ __forceinline__ int div_small(int v, uint32_t cinv) { return (int)(((
 __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ int n_corner, need_lo;
+    __shared__ int n_corner, need_lo, n_skipped, n_glist;
     const int k = b.prm.k, border = b.prm.border, p_min = b.prm.p_min;
-    const FastLayout lay = fast_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k);
+    const FastLayout lay = fast_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k, b.skip_max_tiles > 0);
     uint32_t *lut = reinterpret_cast<uint32_t *>(smem);
     uint8_t *const buf0 = smem + lay.buf0, *const buf1 = smem + lay.buf1;
     uint16_t *clist = reinterpret_cast<uint16_t *>(smem + lay.clist);
     uint32_t *ckey = reinterpret_cast<uint32_t *>(smem + lay.ckey);
+    uint16_t *glist = reinterpret_cast<uint16_t *>(smem + lay.glist);
     uint8_t *has_hi = smem + lay.has_hi;
     uint32_t *sel = reinterpret_cast<uint32_t *>(smem + lay.sel);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
@@ -454,10 +459,27 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
                 tw32[i] = v;
             }
         }
-        for (int i = threadIdx.x; i < cells; i += kFastThreads) has_hi[i] = 0;
+        // cell state: 0 no corner yet, 1 primary-threshold corner, 2 skipped by
+        // the learned proposal (its centre projects into a skipped s0 cell)
+        int my_skipped = 0;
+        for (int i = threadIdx.x; i < cells; i += kFastThreads) {
+            uint8_t st = 0;
+            if (I.skip) {
+                const int lcy = i / ncx, lcx = i - lcy * ncx;
+                const int px = min((G.ccx0 + lcx) * c + c / 2, W - 1), py = min((G.ccy0 + lcy) * c + c / 2, Hh - 1);
+                const int X = __ldg(L.projx + px), Y = __ldg(L.projy + py);
+                st = I.skip[(Y / I.skip_c0) * I.skip_cells_x + X / I.skip_c0] ? 2 : 0;
+                my_skipped += st == 2;
+            }
+            has_hi[i] = st;
+        }
         for (int i = threadIdx.x; i < cells * k; i += kFastThreads) sel[i] = 0;
-        if (threadIdx.x == 0) { n_corner = 0; need_lo = 0; }
+        if (threadIdx.x == 0) { n_corner = 0; need_lo = 0; n_skipped = 0; n_glist = 0; }
         __syncthreads();
+        if (my_skipped) atomicAdd(&n_skipped, my_skipped);
+        __syncthreads();
+        const bool all_skipped = n_skipped == cells;
+        const bool some_skipped = n_skipped > 0;  // tiles without skipped cells run as in exact mode
 
         // pixels evaluated: tile-local x in [plo, phi), rows whose y is inside the border
         const int plo = max(border - x0, 0), phi = min(W - border - x0, tw);
@@ -465,8 +487,38 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
         // word of tile column 0 (pixel x0 - 4) within a box row
         const uint32_t *words = reinterpret_cast<const uint32_t *>(tb) + (G.delta >> 2);
 
+        // skip mode, tiles with at least half their cells skipped: compact the
+        // groups that touch a kept cell, so that the warps below only visit
+        // those (entry: row << 5 | group in the row).  Below half, building
+        // the list costs more than the masked groups it would save.
+        const bool use_list = some_skipped && !all_skipped && 2 * n_skipped >= cells;
+        if (use_list) {
+            for (int base = warp * 32; base < ngroups; base += kFastThreads) {
+                const int gi = base + lane;
+                bool act = false;
+                int py = 0, g = 0;
+                if (gi < ngroups) {
+                    py = gi / gpr;
+                    g = gi - py * gpr;
+                    const int gy = y0 + py, px0 = 4 * g;
+                    if (gy >= border && gy < Hh - border && px0 + 3 >= plo && px0 < phi) {
+                        const int crow = div_small(py, cinv) * ncx;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) act |= has_hi[crow + div_small(min(px0 + j, tw - 1), cinv)] != 2;
+                    }
+                }
+                const uint32_t m = __ballot_sync(0xFFFFFFFFu, act);
+                int start = 0;
+                if (lane == 0 && m) start = atomicAdd(&n_glist, __popc(m));
+                start = __shfl_sync(0xFFFFFFFFu, start, 0);
+                if (act) glist[start + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((py << 5) | g);
+            }
+            __syncthreads();
+        }
+        const int nitems = use_list ? n_glist : ngroups;
+
         // 1./2. corner bits of every group, pushed to the compacted list.
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int pass = 0; pass < 2 && !all_skipped; ++pass) {
             const int eps = pass == 0 ? I.eps_hi : I.eps_lo;
             if (pass == 1) {
                 if (eps <= 0) break;
@@ -479,30 +531,38 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
             const uint32_t e0 = (uint32_t)eps * 0x01010101u, e1 = (uint32_t)(eps + 1) * 0x01010101u;
             const int gstep_y = kFastThreads / gpr, gstep_x = kFastThreads - gstep_y * gpr;
             int py = threadIdx.x / gpr, g = threadIdx.x - (threadIdx.x / gpr) * gpr;
-            for (int base = warp * 32; base < ngroups; base += kFastThreads) {
+            for (int base = warp * 32; base < nitems; base += kFastThreads) {
                 const int gi = base + lane;
+                if (use_list) {
+                    const int e = gi < nitems ? glist[gi] : 0;
+                    py = e >> 5;
+                    g = e & 31;
+                }
                 uint32_t bits = 0;
-                if (gi < ngroups) {
+                if (gi < nitems) {
                     const int gy = y0 + py;
                     const int px0 = 4 * g;
                     if (gy >= border && gy < Hh - border && px0 + 3 >= plo && px0 < phi) {
                         uint32_t valid = 0;
 #pragma unroll
                         for (int j = 0; j < 4; ++j) valid |= (uint32_t)(px0 + j >= plo && px0 + j < phi) << j;
-                        if (pass == 1) {
+                        if (pass == 1 || some_skipped) {
+                            // fallback pass: cells without a corner; skip mode: cells not skipped
                             const int crow = div_small(py, cinv) * ncx;
-                            uint32_t need = 0;
+                            uint32_t keep = 0;
 #pragma unroll
-                            for (int j = 0; j < 4; ++j)
-                                need |= (uint32_t)(!has_hi[crow + div_small(px0 + j, cinv)]) << j;
-                            valid &= need;
+                            for (int j = 0; j < 4; ++j) {
+                                const uint8_t st = has_hi[crow + div_small(min(px0 + j, tw - 1), cinv)];
+                                keep |= (uint32_t)(pass == 1 ? st == 0 : st != 2) << j;
+                            }
+                            valid &= keep;
                         }
                         if (valid) bits = group_corners(words + py * wpr + g, wpr, e0, e1, lut, p_min) & valid;
                     }
                 }
                 const int cpy = py, cg = g;  // this iteration's group
                 g += gstep_x; py += gstep_y;
-                if (g >= gpr) { g -= gpr; ++py; }
+                if (g >= gpr) { g -= gpr; ++py; }  // unused in list mode (reloaded above)
                 // warp-aggregated append of this iteration's corners
                 const int cnt = __popc(bits);
                 int incl = cnt;
@@ -580,9 +640,9 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
     }
 }
 
-int fast_smem_bytes(int max_box, int max_px, int max_cells, int k)
+int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, bool skip)
 {
-    return fast_layout(max_box, max_px, max_cells, k).total;
+    return fast_layout(max_box, max_px, max_cells, k, skip).total;
 }
 
 cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream)

@@ -53,6 +53,11 @@ class Tuning(C.Structure):
     _fields_ = [("tile_w_px", C.c_int32), ("tile_h_px", C.c_int32)]
 
 
+class SkipView(C.Structure):
+    _fields_ = [("w8", C.c_int32), ("h8", C.c_int32), ("cells_x", C.c_int32), ("cells_y", C.c_int32),
+                ("logits", C.c_void_p), ("skip", C.c_void_p)]
+
+
 class Keypoints(C.Structure):
     _fields_ = [("count", C.c_int32), ("capacity", C.c_int32),
                 ("x", C.c_void_p), ("y", C.c_void_p), ("X", C.c_void_p), ("Y", C.c_void_p),
@@ -84,8 +89,9 @@ SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extra
            "jslam_download", "jslam_result_view", "jslam_destroy", "jslam_status_str", "jslam_pattern_table",
            "jslam_level_geometry", "jslam_project", "jslam_match_band", "jslam_enable_stage_timing",
            "jslam_stage_times", "jslam_pfa_scores_static", "jslam_corner_table", "jslam_set_tuning",
-           "jslam_autotune", "jslam_graph_capture", "jslam_graph_launch")
-STAGES = ("pyramid", "detect", "pfa_nms", "pfa_final", "orb", "match")
+           "jslam_autotune", "jslam_graph_capture", "jslam_graph_launch", "jslam_set_skip_model",
+           "jslam_get_skip_view")
+STAGES = ("pyramid", "skip", "detect", "pfa_nms", "pfa_final", "orb", "match")
 
 _lib = None
 
@@ -136,6 +142,10 @@ def lib():
         L.jslam_project.restype = C.c_int32
         L.jslam_match_band.argtypes = [C.c_int32, C.c_float, C.c_int32]
         L.jslam_match_band.restype = C.c_int32
+        L.jslam_set_skip_model.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_float]
+        L.jslam_set_skip_model.restype = st
+        L.jslam_get_skip_view.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(SkipView)]
+        L.jslam_get_skip_view.restype = st
         L.jslam_set_tuning.argtypes = [C.c_void_p, C.POINTER(Tuning)]
         L.jslam_set_tuning.restype = st
         L.jslam_autotune.argtypes = [C.c_void_p, C.POINTER(StereoJob), C.c_int32, C.POINTER(Tuning)]
@@ -332,6 +342,21 @@ class Frontend:
 
     def match(self):
         _check(lib().jslam_match(self._h), "jslam_match")
+
+    def set_skip_model(self, blob, thresh: float = 0.0):
+        """Enable the learned cell-skip proposal (blob: bytes of a model) or
+        return to the exact path (blob None)."""
+        if blob is None:
+            _check(lib().jslam_set_skip_model(self._h, None, 0, 0.0), "jslam_set_skip_model")
+            return
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        _check(lib().jslam_set_skip_model(self._h, buf, len(blob), thresh), "jslam_set_skip_model")
+
+    def skip_view(self, pair: int = 0, side: int = 0) -> dict:
+        v = SkipView()
+        _check(lib().jslam_get_skip_view(self._h, pair, side, C.byref(v)), "jslam_get_skip_view")
+        return {"logits": _device_view(v.logits, (v.h8, v.w8), np.float32, self.device),
+                "skip": _device_view(v.skip, (v.cells_y, v.cells_x), np.uint8, self.device)}
 
     def set_tuning(self, tile_w_px: int, tile_h_px: int):
         t = Tuning(tile_w_px, tile_h_px)
