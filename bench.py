@@ -73,6 +73,8 @@ def parse_args():
     ap.add_argument("--mode", choices=["batched", "graph", "plain"], default="batched")
     ap.add_argument("--cpu-pairs", type=int, default=12, help="pairs in the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, nargs=2, metavar=("W", "H"),
+                    help="detection tile in pixels instead of the autotuner's pick (no autotune launches)")
     ap.add_argument("--only-batched", action="store_true",
                     help="time the batched mode only (no other modes, no e2e): the launch sequence ncu captures")
     return ap.parse_args()
@@ -295,7 +297,11 @@ def main():
                 max_levels=8, max_feats=max(p["max_feats"] for p in params), max_pairs=n, fast_thresh_lo=lo)
     fe = jslam.Frontend(device=dev.index, stream=stream, **dims)
     jobs = fe.prepare_batch([jslam.Job(l, r, **p) for l, r, p in zip(lefts, rights, params)])
-    tuning = fe.autotune(jobs)
+    if args.tile:
+        fe.set_tuning(*args.tile)
+        tuning = tuple(args.tile)
+    else:
+        tuning = fe.autotune(jobs)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
 
     def step_batched():

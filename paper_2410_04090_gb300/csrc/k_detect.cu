@@ -238,14 +238,16 @@ constexpr uint32_t kH = 0x80808080u, kL7 = 0x7F7F7F7Fu;
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
 
 struct FastLayout {
-    int buf0, buf1, clist, ckey, glist, has_hi, sel, bar, total;
+    int buf0, buf1, clist, ckey, cand, glist, has_hi, sel, bar, total;
 };
 
 __host__ __device__ inline int fast_align(int v, int a) { return (v + a - 1) / a * a; }
 
-// `skip`: the learned cell-skip proposal is on, which adds the list of
-// pixel groups that touch a cell it keeps (a group is 4 pixels of a row;
-// a tile row of at most kFastMaxTile pixels has at most kFastMaxTile / 4).
+// A group is 4 pixels of a row; a tile of max_px pixels whose rows hold at
+// most kFastMaxTile pixels has at most max_px / 4 + kFastMaxTile groups.
+// `cand` lists the groups that pass the cardinal pre-test; `skip` (the
+// learned cell-skip proposal is on) adds the list of groups that touch a
+// cell it keeps.
 __host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int max_cells, int k, bool skip)
 {
     FastLayout l;
@@ -254,6 +256,7 @@ __host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int m
     l.buf1 = o;  o += fast_align(max_box, 128);
     l.clist = o; o += fast_align(max_px * 2, 16);
     l.ckey = o;  o += k > 1 ? fast_align(max_px * 4, 16) : 0;
+    l.cand = o;  o += fast_align((max_px / 4 + kFastMaxTile) * 2, 16);
     l.glist = o; o += skip ? fast_align((max_px / 4 + kFastMaxTile) * 2, 16) : 0;
     l.has_hi = o; o += fast_align(max_cells, 16);
     l.sel = o;   o += fast_align(max_cells * k * 4, 16);
@@ -389,12 +392,46 @@ __device__ __forceinline__ uint32_t group_corners(const uint32_t *base, int wpr,
 
 // floor(v / c) for 0 <= v < 128 and 1 <= c <= 128 with cinv = ceil(2^16 / c):
 // exact because v * c < 2^16.
+// Cardinal pre-test of a group (bit j: pixel 4g + j may be a corner).  An
+// arc of 8 or more contiguous ring pixels holds two neighbouring cardinal
+// points (ring positions 0, 4, 8, 12), so a pixel whose cardinal flags
+// satisfy neither (F0 | F8) & (F4 | F12) for brighter nor for darker is no
+// corner at any P_min >= 8 (8 contiguous positions hold two neighbouring
+// cardinal points; 7 may hold only one).  The flags use the same byte compares as the
+// full test (without its never-masks, which only clear flags), so every
+// corner passes.  `base` as for group_corners.
+__device__ __forceinline__ uint32_t group_pretest(const uint32_t *base, int wpr, uint32_t e0)
+{
+    const uint32_t C = base[3 * wpr + 1];
+    const uint32_t P0 = base[6 * wpr + 1];                          // ( 0, +3)
+    const uint32_t P4 = __funnelshift_r(C, base[3 * wpr + 2], 24);  // (+3,  0)
+    const uint32_t P8 = base[1];                                    // ( 0, -3)
+    const uint32_t P12 = __funnelshift_r(base[3 * wpr], C, 8);      // (-3,  0)
+    const uint32_t sb0 = (C & kL7) + (e0 & kL7);
+    const uint32_t Tb = sb0 ^ ((C ^ e0) & kH);
+    const uint32_t sd0 = (C | kH) - (e0 & kL7);
+    const uint32_t Td = sd0 ^ (~(C ^ e0) & kH);
+    const uint32_t N = ~Tb, N7 = N & kL7, K = (Td & kL7) + kL7;
+    uint32_t gb[4], gd[4];
+    const uint32_t P[4] = { P0, P4, P8, P12 };
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t Pl = P[i] & kL7;
+        gb[i] = maj3(P[i], N, Pl + N7);
+        gd[i] = maj3(Td, ~P[i], K - Pl);
+    }
+    const uint32_t x = (((gb[0] | gb[2]) & (gb[1] | gb[3])) | ((gd[0] | gd[2]) & (gd[1] | gd[3]))) & kH;
+    // byte MSBs (bits 7, 15, 23, 31) to bits 0..3: after >> 7 they sit at
+    // 0, 8, 16, 24; the multiply moves them to 21..24 without carries
+    return (((x >> 7) * 0x00204081u) >> 21) & 0xFu;
+}
+
 __device__ __forceinline__ int div_small(int v, uint32_t cinv) { return (int)(((uint32_t)v * cinv) >> 16); }
 
 __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ int n_corner, need_lo, n_skipped, n_glist;
+    __shared__ int n_corner, need_lo, n_skipped, n_glist, n_cand[2];
     const int k = b.prm.k, border = b.prm.border, p_min = b.prm.p_min;
     const FastLayout lay = fast_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k, b.skip_max_tiles > 0);
     uint32_t *lut = reinterpret_cast<uint32_t *>(smem);
@@ -402,6 +439,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
     uint16_t *clist = reinterpret_cast<uint16_t *>(smem + lay.clist);
     uint32_t *ckey = reinterpret_cast<uint32_t *>(smem + lay.ckey);
     uint16_t *glist = reinterpret_cast<uint16_t *>(smem + lay.glist);
+    uint16_t *cand = reinterpret_cast<uint16_t *>(smem + lay.cand);
     uint8_t *has_hi = smem + lay.has_hi;
     uint32_t *sel = reinterpret_cast<uint32_t *>(smem + lay.sel);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
@@ -474,7 +512,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
             has_hi[i] = st;
         }
         for (int i = threadIdx.x; i < cells * k; i += kFastThreads) sel[i] = 0;
-        if (threadIdx.x == 0) { n_corner = 0; need_lo = 0; n_skipped = 0; n_glist = 0; }
+        if (threadIdx.x == 0) { n_corner = 0; need_lo = 0; n_skipped = 0; n_glist = 0; n_cand[0] = n_cand[1] = 0; }
         __syncthreads();
         if (my_skipped) atomicAdd(&n_skipped, my_skipped);
         __syncthreads();
@@ -517,12 +555,15 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
         }
         const int nitems = use_list ? n_glist : ngroups;
 
-        // 1./2. corner bits of every group, pushed to the compacted list.
+        // 1./2. per threshold pass: (a) cardinal pre-test of every group, the
+        // survivors compacted with their pixel masks (entry: row << 9 | group
+        // << 4 | mask); (b) full ring test of the survivors, corners pushed to
+        // the compacted corner list.
         for (int pass = 0; pass < 2 && !all_skipped; ++pass) {
             const int eps = pass == 0 ? I.eps_hi : I.eps_lo;
             if (pass == 1) {
                 if (eps <= 0) break;
-                __syncthreads();  // has_hi complete
+                __syncthreads();  // has_hi complete, pass-0 readers of cand done
                 for (int i = threadIdx.x; i < cells; i += kFastThreads)
                     if (!has_hi[i]) need_lo = 1;
                 __syncthreads();
@@ -538,7 +579,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
                     py = e >> 5;
                     g = e & 31;
                 }
-                uint32_t bits = 0;
+                uint32_t pre = 0;
                 if (gi < nitems) {
                     const int gy = y0 + py;
                     const int px0 = 4 * g;
@@ -557,12 +598,30 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
                             }
                             valid &= keep;
                         }
-                        if (valid) bits = group_corners(words + py * wpr + g, wpr, e0, e1, lut, p_min) & valid;
+                        // the pre-test holds for arcs of 8 or more (P_min >= 8)
+                        if (valid) pre = p_min >= 8 ? group_pretest(words + py * wpr + g, wpr, e0) & valid : valid;
                     }
                 }
-                const int cpy = py, cg = g;  // this iteration's group
+                const uint32_t m = __ballot_sync(0xFFFFFFFFu, pre != 0);
+                int start = 0;
+                if (lane == 0 && m) start = atomicAdd(&n_cand[pass], __popc(m));
+                start = __shfl_sync(0xFFFFFFFFu, start, 0);
+                if (pre) cand[start + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((py << 9) | (g << 4) | pre);
                 g += gstep_x; py += gstep_y;
                 if (g >= gpr) { g -= gpr; ++py; }  // unused in list mode (reloaded above)
+            }
+            __syncthreads();
+            const int ncand = n_cand[pass];
+            for (int base = warp * 32; base < ncand; base += kFastThreads) {
+                const int gi = base + lane;
+                uint32_t bits = 0;
+                int cpy = 0, cg = 0;
+                if (gi < ncand) {
+                    const uint32_t e = cand[gi];
+                    cpy = (int)(e >> 9);
+                    cg = (int)(e >> 4) & 31;
+                    bits = group_corners(words + cpy * wpr + cg, wpr, e0, e1, lut, p_min) & e & 0xFu;
+                }
                 // warp-aggregated append of this iteration's corners
                 const int cnt = __popc(bits);
                 int incl = cnt;

@@ -69,3 +69,16 @@ def test_corner_table_matches_oracle(jslam, oracle, p_min, p_max):
     bits = np.unpackbits(table.view(np.uint8), bitorder="little").astype(bool)
     want = np.array([p_min <= oracle.longest_run(m) <= p_max for m in range(1 << 16)])
     assert np.array_equal(bits, want)
+
+
+def test_cardinal_pretest_is_necessary(oracle):
+    """The detection kernel rejects a pixel early when, for both polarities,
+    (F0 | F8) & (F4 | F12) fails on its ring flags.  That is only sound if
+    every mask whose longest circular run is 8 or more passes it, and the
+    kernel uses it only for P_min >= 8; 7 is too short."""
+    runs = np.array([oracle.longest_run(m) for m in range(1 << 16)])
+    m = np.arange(1 << 16)
+    f = lambda q: (m >> q) & 1
+    passes = ((f(0) | f(8)) & (f(4) | f(12))).astype(bool)
+    assert passes[runs >= 8].all()
+    assert not passes[runs == 7].all()

@@ -110,6 +110,8 @@ def test_strided_device_input(J, oracle):
     dict(pfa_rule=1),
     dict(p_max=16),            # classic FAST (Eq. 2) as the unbounded special case
     dict(p_min=12, p_max=14),
+    dict(p_min=8, p_max=13),   # shortest arc the cardinal pre-test covers
+    dict(p_min=6, p_max=10),   # below it: the pre-test is off
     dict(cell=7),
     dict(cell=100),
     dict(max_feats=5),         # cap binds hard; ties resolved in canonical order
