@@ -128,12 +128,28 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
         if (threadIdx.x == 0) nsrc = nrows;
         __syncthreads();
         const int ns = nsrc;
-        for (int i = threadIdx.x; i < ns * kPyrCols; i += kPyrThreads) {
-            const int j = i / kPyrCols, c = i - j * kPyrCols;
-            const uint8_t *row = L0 + (size_t)src_row[j] * pitch0;
-            const uint32_t tp = tx[c];
-            const int xa = tp & 0xFFFF, a = tp >> 16, xb = min(xa + 1, W0 - 1);
-            Hs[j][c] = (uint16_t)((256u - a) * __ldg(row + xa) + (uint32_t)a * __ldg(row + xb));
+        // horizontal interpolation: a thread owns 4 adjacent columns, keeps
+        // their taps in registers and walks the source rows
+        constexpr int kQuads = kPyrCols / 4, kRowSlots = kPyrThreads / kQuads;
+        const int q = threadIdx.x % kQuads, slot = threadIdx.x / kQuads;
+        if (slot < kRowSlots) {
+            int xa[4], xb[4];
+            uint32_t wa[4], wbx[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t tp = tx[4 * q + k];
+                xa[k] = tp & 0xFFFF;
+                xb[k] = min(xa[k] + 1, W0 - 1);
+                wbx[k] = tp >> 16;
+                wa[k] = 256u - wbx[k];
+            }
+            for (int j = slot; j < ns; j += kRowSlots) {
+                const uint8_t *row = L0 + (size_t)src_row[j] * pitch0;
+                uint32_t h[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) h[k] = wa[k] * __ldg(row + xa[k]) + wbx[k] * __ldg(row + xb[k]);
+                *reinterpret_cast<uint2 *>(&Hs[j][4 * q]) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
+            }
         }
         __syncthreads();
         // vertical interpolation, 4 columns per thread (16-bit taps read as words)
@@ -159,43 +175,73 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
             *reinterpret_cast<uint32_t *>(L.raw_w + (size_t)gy * L.pitch + gx) =
                 *reinterpret_cast<const uint32_t *>(&raw[r + 3][4 * w + 4]);
     }
-    // vertical 7-tap sums of every column, two pixels per 32-bit lane pair
-    for (int i = threadIdx.x; i < kPyrTH * WPR; i += kPyrThreads) {
-        const int r = i / WPR, w = i - r * WPR;
-        uint32_t e[7], o[7];
+    // vertical 7-tap sums, two pixels per 32-bit lane pair: a thread owns one
+    // word column and slides a 7-row window down a run of rows
+    {
+        constexpr int kSegs = kPyrThreads / WPR, kRun = (kPyrTH + kSegs - 1) / kSegs;
+        const int w = threadIdx.x % WPR, seg = threadIdx.x / WPR;
+        if (seg < kSegs) {
+            const int r0 = seg * kRun;
+            uint32_t e[7], o[7];
 #pragma unroll
-        for (int j = 0; j < 7; ++j) {
-            const uint32_t x = *reinterpret_cast<const uint32_t *>(&raw[r + j][4 * w]);
-            e[j] = x & 0x00FF00FFu;
-            o[j] = (x >> 8) & 0x00FF00FFu;
+            for (int j = 0; j < 6; ++j) {
+                const uint32_t x = *reinterpret_cast<const uint32_t *>(&raw[min(r0 + j, kPyrRows - 1)][4 * w]);
+                e[j] = x & 0x00FF00FFu;
+                o[j] = (x >> 8) & 0x00FF00FFu;
+            }
+#pragma unroll
+            for (int k = 0; k < kRun; ++k) {
+                const int r = r0 + k;
+                if (r < kPyrTH) {
+                    const uint32_t x = *reinterpret_cast<const uint32_t *>(&raw[r + 6][4 * w]);
+                    e[6] = x & 0x00FF00FFu;
+                    o[6] = (x >> 8) & 0x00FF00FFu;
+                    const uint32_t se = blur7_sym(e[0], e[1], e[2], e[3], e[4], e[5], e[6]);
+                    const uint32_t so = blur7_sym(o[0], o[1], o[2], o[3], o[4], o[5], o[6]);
+                    *reinterpret_cast<uint2 *>(&V[r][4 * w]) =
+                        make_uint2(__byte_perm(se, so, 0x5410), __byte_perm(se, so, 0x7632));
+                }
+#pragma unroll
+                for (int j = 0; j < 6; ++j) { e[j] = e[j + 1]; o[j] = o[j + 1]; }
+            }
         }
-        const uint32_t se = blur7_sym(e[0], e[1], e[2], e[3], e[4], e[5], e[6]);
-        const uint32_t so = blur7_sym(o[0], o[1], o[2], o[3], o[4], o[5], o[6]);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(&V[r][4 * w]);
-        dst[0] = __byte_perm(se, so, 0x5410);
-        dst[1] = __byte_perm(se, so, 0x7632);
     }
     __syncthreads();
-    // horizontal 7-tap on the column sums, 4 output pixels per thread
-    for (int i = threadIdx.x; i < kPyrTH * (kPyrTW / 4); i += kPyrThreads) {
-        const int r = i / (kPyrTW / 4), q = i - r * (kPyrTW / 4);
-        const int gy = y0 + r, gx = x0 + 4 * q;
-        if (gy >= H || gx >= W) continue;
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(&V[r][4 * q]);
+    // horizontal 7-tap on the column sums: a thread owns a row and a run of
+    // 4 quads (16 output pixels) and slides along it
+    {
+        constexpr int kQuadRun = 4, kRunsPerRow = (kPyrTW / 4) / kQuadRun;
+        static_assert(kPyrTH * kRunsPerRow == kPyrThreads, "one run per thread");
+        const int r = threadIdx.x / kRunsPerRow, q0 = (threadIdx.x % kRunsPerRow) * kQuadRun;
+        const int gy = y0 + r;
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&V[r][4 * q0]);
         uint32_t v[12];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
+        for (int j = 0; j < 4; ++j) {
             const uint32_t p = src[j];
             v[2 * j] = p & 0xFFFFu;
             v[2 * j + 1] = p >> 16;
         }
-        uint32_t out = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t s = blur7_sym(v[k + 1], v[k + 2], v[k + 3], v[k + 4], v[k + 5], v[k + 6], v[k + 7]);
-            out |= ((s + 32768u) >> 16) << (8 * k);
+        for (int k = 0; k < kQuadRun; ++k) {
+            // v[0..7] hold columns 4 (q0 + k) .. + 7; fetch the next 4
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const uint32_t p = src[2 * k + 4 + j];
+                v[8 + 2 * j] = p & 0xFFFFu;
+                v[9 + 2 * j] = p >> 16;
+            }
+            uint32_t out = 0;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const uint32_t sm = blur7_sym(v[m + 1], v[m + 2], v[m + 3], v[m + 4], v[m + 5], v[m + 6], v[m + 7]);
+                out |= ((sm + 32768u) >> 16) << (8 * m);
+            }
+            const int gx = x0 + 4 * (q0 + k);
+            if (gy < H && gx < W) *reinterpret_cast<uint32_t *>(L.blur + (size_t)gy * L.blur_pitch + gx) = out;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = v[j + 4];
         }
-        *reinterpret_cast<uint32_t *>(L.blur + (size_t)gy * L.blur_pitch + gx) = out;
     }
 }
 
