@@ -427,10 +427,18 @@ __device__ __forceinline__ uint32_t group_corners(const uint32_t *base, int wpr,
         const uint32_t mb = __byte_perm(b_lo, b_hi, sel) & 0xFFFFu;
         const uint32_t md = __byte_perm(d_lo, d_hi, sel) & 0xFFFFu;
         // a mask with fewer than P_min set bits has no run of P_min: skip the
-        // look-up (lanes that skip issue no shared-memory request)
+        // look-up (lanes that skip issue no shared-memory request).  Brighter
+        // and darker flags are disjoint, so for P_min >= 9 at most one of the
+        // two masks can reach P_min and one look-up suffices.
+        const int pb = __popc(mb), pd = __popc(md);
         uint32_t ok = 0;
-        if (__popc(mb) >= p_min) ok = lut[mb >> 5] >> (mb & 31);
-        if (__popc(md) >= p_min) ok |= lut[md >> 5] >> (md & 31);
+        if (p_min >= 9) {
+            const uint32_t m = pb >= p_min ? mb : md;
+            if (max(pb, pd) >= p_min) ok = lut[m >> 5] >> (m & 31);
+        } else {
+            if (pb >= p_min) ok = lut[mb >> 5] >> (mb & 31);
+            if (pd >= p_min) ok |= lut[md >> 5] >> (md & 31);
+        }
         bits |= (ok & 1u) << j;
     }
     return bits;
