@@ -12,7 +12,7 @@
 #include "tables.h"
 
 namespace jslam {
-int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, bool skip);
+int fast_smem_bytes(int max_box, int max_px, int max_cells, int k);
 }
 
 using namespace jslam;
@@ -334,7 +334,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
             const int w8 = (geo[p].W[0] + 7) / 8, h8 = (geo[p].H[0] + 7) / 8;
             const int cx = (geo[p].W[0] + jobs[p].cell - 1) / jobs[p].cell, cy = (geo[p].H[0] + jobs[p].cell - 1) / jobs[p].cell;
             skip_bytes += 2 * (align_up((size_t)w8 * h8 * 4, 256) + align_up((size_t)cx * cy, 256));
-            skip_max_tiles = std::max(skip_max_tiles, ((w8 + kSkipTile - 1) / kSkipTile) * ((h8 + kSkipTile - 1) / kSkipTile));
+            skip_max_tiles = std::max(skip_max_tiles, ((w8 + kSkipTileW - 1) / kSkipTileW) * ((h8 + kSkipTileH - 1) / kSkipTileH));
             skip_max_cells = std::max(skip_max_cells, cx * cy);
         }
         if ((e = ctx->skipbuf.ensure(skip_bytes + 256, false, nullptr)) != cudaSuccess) return fail(ctx, e);
@@ -521,7 +521,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.n_images = n_img; b.n_levels = n_levels; b.n_pairs = n; b.n_segments = n_segs;
     b.pyr_tiles = pyr; b.fast_tiles = fast; b.max_capacity = max_cap;
     b.fast_max_box = max_box; b.fast_max_px = max_px; b.fast_max_cells = max_cells;
-    b.fast_smem = fast_smem_bytes(max_box, max_px, max_cells, k, skip_max_tiles > 0);
+    b.fast_smem = fast_smem_bytes(max_box, max_px, max_cells, k);
     b.corner_lut = ctx->d_lut;
     b.skip_max_tiles = skip_max_tiles;
     b.skip_max_cells = skip_max_cells;

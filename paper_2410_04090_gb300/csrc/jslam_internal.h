@@ -31,7 +31,7 @@ constexpr int kFastMaxTile = 128, kFastThreads = 256;
 constexpr int kFastMaxCellsPerCta = 2048;  // cells x k per CTA
 constexpr int kLutWords = 2048;            // 2^16-entry corner bit table
 constexpr int kSkipC = 16;                 // channels of the learned cell-skip net
-constexpr int kSkipTile = 14;              // its logits per CTA side
+constexpr int kSkipTileW = 26, kSkipTileH = 12;  // its logits per CTA (grid pitch 26 + 6 = 32)
 constexpr int kNmsThreads = 128;
 constexpr int kFinThreads = 1024;
 

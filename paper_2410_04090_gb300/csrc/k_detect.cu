@@ -284,17 +284,15 @@ constexpr uint32_t kH = 0x80808080u, kL7 = 0x7F7F7F7Fu;
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
 
 struct FastLayout {
-    int buf0, buf1, clist, ckey, cand, glist, has_hi, sel, bar, total;
+    int buf0, buf1, clist, ckey, cand, has_hi, sel, bar, total;
 };
 
 __host__ __device__ inline int fast_align(int v, int a) { return (v + a - 1) / a * a; }
 
 // A group is 4 pixels of a row; a tile of max_px pixels whose rows hold at
 // most kFastMaxTile pixels has at most max_px / 4 + kFastMaxTile groups.
-// `cand` lists the groups that pass the cardinal pre-test; `skip` (the
-// learned cell-skip proposal is on) adds the list of groups that touch a
-// cell it keeps.
-__host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int max_cells, int k, bool skip)
+// `cand` lists the groups that pass the cardinal pre-test.
+__host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int max_cells, int k)
 {
     FastLayout l;
     int o = kLutWords * 4;
@@ -303,7 +301,6 @@ __host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int m
     l.clist = o; o += fast_align(max_px * 2, 16);
     l.ckey = o;  o += k > 1 ? fast_align(max_px * 4, 16) : 0;
     l.cand = o;  o += fast_align((max_px / 4 + kFastMaxTile) * 2, 16);
-    l.glist = o; o += skip ? fast_align((max_px / 4 + kFastMaxTile) * 2, 16) : 0;
     l.has_hi = o; o += fast_align(max_cells, 16);
     l.sel = o;   o += fast_align(max_cells * k * 4, 16);
     l.bar = o;   o += 16;
@@ -485,14 +482,13 @@ __device__ __forceinline__ int div_small(int v, uint32_t cinv) { return (int)(((
 __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
 {
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ int n_corner, need_lo, n_skipped, n_glist, n_cand[2];
+    __shared__ int n_corner, need_lo, n_skipped, n_cand[2];
     const int k = b.prm.k, border = b.prm.border, p_min = b.prm.p_min;
-    const FastLayout lay = fast_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k, b.skip_max_tiles > 0);
+    const FastLayout lay = fast_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k);
     uint32_t *lut = reinterpret_cast<uint32_t *>(smem);
     uint8_t *const buf0 = smem + lay.buf0, *const buf1 = smem + lay.buf1;
     uint16_t *clist = reinterpret_cast<uint16_t *>(smem + lay.clist);
     uint32_t *ckey = reinterpret_cast<uint32_t *>(smem + lay.ckey);
-    uint16_t *glist = reinterpret_cast<uint16_t *>(smem + lay.glist);
     uint16_t *cand = reinterpret_cast<uint16_t *>(smem + lay.cand);
     uint8_t *has_hi = smem + lay.has_hi;
     uint32_t *sel = reinterpret_cast<uint32_t *>(smem + lay.sel);
@@ -566,7 +562,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
             has_hi[i] = st;
         }
         for (int i = threadIdx.x; i < cells * k; i += kFastThreads) sel[i] = 0;
-        if (threadIdx.x == 0) { n_corner = 0; need_lo = 0; n_skipped = 0; n_glist = 0; n_cand[0] = n_cand[1] = 0; }
+        if (threadIdx.x == 0) { n_corner = 0; need_lo = 0; n_skipped = 0; n_cand[0] = n_cand[1] = 0; }
         __syncthreads();
         if (my_skipped) atomicAdd(&n_skipped, my_skipped);
         __syncthreads();
@@ -579,35 +575,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
         // word of tile column 0 (pixel x0 - 4) within a box row
         const uint32_t *words = reinterpret_cast<const uint32_t *>(tb) + (G.delta >> 2);
 
-        // skip mode, tiles with at least half their cells skipped: compact the
-        // groups that touch a kept cell, so that the warps below only visit
-        // those (entry: row << 5 | group in the row).  Below half, building
-        // the list costs more than the masked groups it would save.
-        const bool use_list = some_skipped && !all_skipped && 2 * n_skipped >= cells;
-        if (use_list) {
-            for (int base = warp * 32; base < ngroups; base += kFastThreads) {
-                const int gi = base + lane;
-                bool act = false;
-                int py = 0, g = 0;
-                if (gi < ngroups) {
-                    py = gi / gpr;
-                    g = gi - py * gpr;
-                    const int gy = y0 + py, px0 = 4 * g;
-                    if (gy >= border && gy < Hh - border && px0 + 3 >= plo && px0 < phi) {
-                        const int crow = div_small(py, cinv) * ncx;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) act |= has_hi[crow + div_small(min(px0 + j, tw - 1), cinv)] != 2;
-                    }
-                }
-                const uint32_t m = __ballot_sync(0xFFFFFFFFu, act);
-                int start = 0;
-                if (lane == 0 && m) start = atomicAdd(&n_glist, __popc(m));
-                start = __shfl_sync(0xFFFFFFFFu, start, 0);
-                if (act) glist[start + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((py << 5) | g);
-            }
-            __syncthreads();
-        }
-        const int nitems = use_list ? n_glist : ngroups;
+        const int nitems = ngroups;
 
         // 1./2. per threshold pass: (a) cardinal pre-test of every group, the
         // survivors compacted with their pixel masks (entry: row << 9 | group
@@ -628,11 +596,6 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
             int py = threadIdx.x / gpr, g = threadIdx.x - (threadIdx.x / gpr) * gpr;
             for (int base = warp * 32; base < nitems; base += kFastThreads) {
                 const int gi = base + lane;
-                if (use_list) {
-                    const int e = gi < nitems ? glist[gi] : 0;
-                    py = e >> 5;
-                    g = e & 31;
-                }
                 uint32_t pre = 0;
                 if (gi < nitems) {
                     const int gy = y0 + py;
@@ -641,19 +604,26 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
                         uint32_t valid = 0;
 #pragma unroll
                         for (int j = 0; j < 4; ++j) valid |= (uint32_t)(px0 + j >= plo && px0 + j < phi) << j;
-                        if (pass == 1 || some_skipped) {
-                            // fallback pass: cells without a corner; skip mode: cells not skipped
-                            const int crow = div_small(py, cinv) * ncx;
+                        const int crow = div_small(py, cinv) * ncx;
+                        if (pass == 1) {
+                            // fallback pass: only cells without a corner (and not skipped)
                             uint32_t keep = 0;
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) {
-                                const uint8_t st = has_hi[crow + div_small(min(px0 + j, tw - 1), cinv)];
-                                keep |= (uint32_t)(pass == 1 ? st == 0 : st != 2) << j;
-                            }
+                            for (int j = 0; j < 4; ++j)
+                                keep |= (uint32_t)(has_hi[crow + div_small(min(px0 + j, tw - 1), cinv)] == 0) << j;
                             valid &= keep;
                         }
                         // the pre-test holds for arcs of 8 or more (P_min >= 8)
                         if (valid) pre = p_min >= 8 ? group_pretest(words + py * wpr + g, wpr, e0) & valid : valid;
+                        if (pre && pass == 0 && some_skipped) {
+                            // skip mode: drop pixels of skipped cells (after the cheap pre-test,
+                            // which already rejects the flat regions skipped cells tend to be)
+                            uint32_t keep = 0;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                keep |= (uint32_t)(has_hi[crow + div_small(min(px0 + j, tw - 1), cinv)] != 2) << j;
+                            pre &= keep;
+                        }
                     }
                 }
                 const uint32_t m = __ballot_sync(0xFFFFFFFFu, pre != 0);
@@ -662,7 +632,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
                 start = __shfl_sync(0xFFFFFFFFu, start, 0);
                 if (pre) cand[start + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((py << 9) | (g << 4) | pre);
                 g += gstep_x; py += gstep_y;
-                if (g >= gpr) { g -= gpr; ++py; }  // unused in list mode (reloaded above)
+                if (g >= gpr) { g -= gpr; ++py; }
             }
             __syncthreads();
             const int ncand = n_cand[pass];
@@ -753,9 +723,9 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
     }
 }
 
-int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, bool skip)
+int fast_smem_bytes(int max_box, int max_px, int max_cells, int k)
 {
-    return fast_layout(max_box, max_px, max_cells, k, skip).total;
+    return fast_layout(max_box, max_px, max_cells, k).total;
 }
 
 cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream)

@@ -84,10 +84,25 @@ def build_model(torch):
                          nn.Conv2d(CHANNELS, 1, 3, padding=1))
 
 
-def cell_logits(torch, model, x, cell: int):
+def forward_bf16(torch, model, x):
+    """The net with the inference kernel's rounding points: the input and both
+    activations rounded to BF16 (weights are BF16 already), wide accumulation."""
+    def rnd(t):
+        return t.to(torch.bfloat16).to(t.dtype)
+    convs = [m for m in model if isinstance(m, torch.nn.Conv2d)]
+    h = rnd(x)
+    for i, c in enumerate(convs):
+        h = torch.nn.functional.conv2d(h, c.weight.to(h.dtype), c.bias.to(h.dtype), padding=1)
+        if i < len(convs) - 1:
+            h = rnd(torch.relu(h))
+    return h
+
+
+def cell_logits(torch, model, x, cell: int, kernel_numerics: bool = False):
     """Largest 1/8-scale logit over each s0 cell (partial edge cells included)."""
     k = cell // DOWN
-    return torch.nn.functional.max_pool2d(model(x), k, stride=k, ceil_mode=True)
+    y = forward_bf16(torch, model, x) if kernel_numerics else model(x)
+    return torch.nn.functional.max_pool2d(y, k, stride=k, ceil_mode=True)
 
 
 def export_blob(torch, model) -> bytes:
@@ -186,7 +201,7 @@ def main():
         for k, _, _ in kinds:
             Xv = torch.from_numpy(np.stack(val[k][0]))[:, None].to(dev)
             Yv = torch.from_numpy(np.stack(val[k][1]))[:, None].to(dev)
-            lv = cell_logits(torch, model, Xv, args.cell)
+            lv = cell_logits(torch, model, Xv, args.cell, kernel_numerics=True)
             logits[k] = (lv, Yv)
             occ.append(lv[Yv > 0.5].float().cpu().numpy())
     occ = np.concatenate(occ)
