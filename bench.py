@@ -8,16 +8,26 @@ KITTI-shaped sequence (1241x376 u8, 8 levels, scale 1.2, FAST 20 with
 fallback 7, 32x32 cells, 2000 features per image).
 
 Modes, each timed over the same steps:
-  batched  all pairs of the step in one C-ABI call (one launch per stage) -- the headline
-  graph    the batched call captured once as a CUDA graph and replayed
-  plain    one C-ABI call per stereo pair
+  batched       all pairs of the step in one C-ABI call (one launch per stage) -- the headline
+  graph         the batched call captured once as a CUDA graph and replayed
+  plain         one C-ABI call per stereo pair
+  learned_skip  batched, with the learned cell-skip proposal (approximate;
+                its feature recall against the exact path is reported)
 Inputs are resident in HBM before the timed region; L2 is flushed (256 MB
 write) before every timed step.  `e2e` repeats the batched step through the
 C ABI with pinned host images and downloads every result block, copies
 inside the timed region.
 
+`roofline` is the dominant kernel's algorithmic bytes per launch over its
+CUDA-event time against the measured HBM copy bandwidth; its `alu` entry
+puts the same launch's executed instructions (from the committed ncu
+summary of that kernel, when its source is unchanged) against the integer
+issue rate of the SMs.  `cpu_baseline` is the CPU oracle on the host cores,
+frame-parallel (one spawned process per core), with the single-threaded
+figure beside it.
+
 ``--impl reference`` times the CPU oracle (the plain C implementation written
-from the paper) on the host cores, one stereo pair per step.
+from the paper) frame-parallel on the host cores, one pair per core per step.
 
 Multi-GPU (torchrun): replicas only -- every rank processes its own copy of
 the sequence with no data-path collective; value = pairs of all ranks / the
@@ -189,9 +199,9 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(kernel, workload):
-    """DRAM bytes per launch from the committed ncu summary of this kernel,
-    or None if there is none or the kernel's source changed since."""
+def profile_summary(kernel, workload):
+    """Key/value lines of the committed ncu summary of this kernel on this
+    workload, or None if there is none or the kernel's source changed since."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
     try:
         text = open(path).read()
@@ -204,12 +214,28 @@ def profiled_traffic(kernel, workload):
             vals[k.strip()] = v.strip()
     src = os.path.join(ROOT, "paper_2410_04090_gb300", "csrc", KERNEL_SOURCES[kernel])
     cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if vals.get("source_sha256_16") != cur:
-        return None
+    return vals if vals.get("source_sha256_16") == cur else None
+
+
+def profile_number(vals, key):
     try:
-        return float(vals["dram_bytes_per_launch_full_workload"])
-    except (KeyError, ValueError):
+        return float(vals[key].split()[0])
+    except (TypeError, KeyError, ValueError, IndexError):
         return None
+
+
+def alu_peak(dev_index):
+    """Integer issue rate in lane-ops/s: SMs x 4 schedulers x 32 lanes x the
+    maximum SM clock (measured file, else the GB300 maximum 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev_index).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    return sms * 128 * mhz * 1e6, sms, mhz
 
 
 def oracle_params(O, p, lo):
@@ -219,30 +245,67 @@ def oracle_params(O, p, lo):
 
 # ------------------------------------------------------------------ reference arm
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_pair(job):
+    """One stereo pair through the CPU oracle (pool worker)."""
+    left, right, p, lo = job
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    O.extract_pair(left, right, oracle_params(O, p, lo))
+    return 0
+
+
+class OraclePool:
+    """Frame-parallel oracle: one independent stereo pair per worker process
+    (spawned, so that it is safe after CUDA initialisation)."""
+
+    def __init__(self, cores):
+        import multiprocessing as mp
+        self.cores = cores
+        self.pool = mp.get_context("spawn").Pool(cores)
+
+    def run(self, pairs, params, lo):
+        jobs = [(pr.left, pr.right, p, lo) for pr, p in zip(pairs, params)]
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_pair, jobs, chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def run_reference(args, rank):
+    """The oracle as it stands, frame-parallel on the host cores: each step
+    is one bounded sample of the workload (one pair per core)."""
     if rank != 0:
         return
-    from oracle import oracle as O
-    pairs, params, lo = make_workload(args.workload, min(args.frames, args.steps + args.warmup))
-    for i in range(args.warmup):
-        k = i % len(pairs)
-        O.extract_pair(pairs[k].left, pairs[k].right, oracle_params(O, params[k], lo))
-    times = []
-    for i in range(args.steps):
-        k = (args.warmup + i) % len(pairs)
-        t0 = time.perf_counter()
-        O.extract_pair(pairs[k].left, pairs[k].right, oracle_params(O, params[k], lo))
-        times.append(time.perf_counter() - t0)
-    total = sum(times)
-    value = args.steps / total
+    cores = host_cores()
+    pairs, params, lo = make_workload(args.workload, min(args.frames, cores))
+    sample = [(pairs[i % len(pairs)], params[i % len(pairs)]) for i in range(cores)]
+    pool = OraclePool(cores)
+    for _ in range(args.warmup):
+        pool.run([a for a, _ in sample], [b for _, b in sample], lo)
+    total = 0.0
+    for _ in range(args.steps):
+        total += pool.run([a for a, _ in sample], [b for _, b in sample], lo)
+    pool.close()
+    value = args.steps * cores / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
-                       "step": "one stereo pair through the CPU oracle (bounded sample of the workload)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} stereo pairs of the workload, one per step"},
+                       "step": f"{cores} stereo pairs of the workload through the CPU oracle, one per core"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} stereo pairs per step (the first {min(len(pairs), cores)} "
+                                       f"pairs of the workload), one spawned process per core"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -250,15 +313,25 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------ our arm
 
 def cpu_baseline(args, pairs, params, lo):
+    """The oracle on the host cores: frame-parallel over all cores (the
+    reported value) and single-threaded (kept beside it)."""
     from oracle import oracle as O
     n = min(args.cpu_pairs, len(pairs))
     O.extract_pair(pairs[0].left, pairs[0].right, oracle_params(O, params[0], lo))  # warm the library
     t0 = time.perf_counter()
     for i in range(n):
         O.extract_pair(pairs[i].left, pairs[i].right, oracle_params(O, params[i], lo))
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {n} stereo pairs of the workload, single-threaded C oracle"}
+    single = n / (time.perf_counter() - t0)
+    cores = host_cores()
+    m = min(len(pairs), 2 * cores)
+    pool = OraclePool(cores)
+    pool.run(pairs[:cores], params[:cores], lo)  # workers up and warm
+    dt = pool.run(pairs[:m], params[:m], lo)
+    pool.close()
+    return {"value": m / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {m} stereo pairs of the workload, one spawned process per core",
+            "single_core": {"value": single, "unit": UNIT, "cores": 1,
+                            "sample": f"first {n} stereo pairs of the workload, one thread"}}
 
 
 def main():
@@ -405,13 +478,35 @@ def main():
                 inter += len(ka & kb); total += len(ka); kept += len(kb)
         skip_quality = {"recall": inter / max(total, 1), "precision": inter / max(kept, 1),
                         "cells_skipped": sum(skipped) / len(skipped), "model": os.path.basename(SKIP_MODEL)}
+        # the skip net's tensor-core work: 3x3 convs 1->16->16->1 per 1/8-scale position
+        skip_fe.enable_stage_timing(True)
+        skip_ms = []
+        for _ in range(3):
+            skip_fe.extract_batch(jobs); skip_fe.sync()
+            skip_ms.append(skip_fe.stage_times()["skip"])
+        skip_fe.enable_stage_timing(False)
+        flop = sum(2 * ((pr.left.shape[0] + 7) // 8) * ((pr.left.shape[1] + 7) // 8) * 2 * (9 * 16 + 144 * 16 + 144)
+                   for pr in pairs)
+        ms = statistics.median(skip_ms)
+        bf16_peak = None
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16_peak = json.load(f).get("bf16_tflops")
+        except (OSError, ValueError):
+            pass
+        tflops = flop / (ms / 1e3) / 1e12 if ms > 0 else None
+        skip_quality["skipnet"] = {"kernel": "k_skipnet (tcgen05.mma kind::f16, BF16 in, FP32 accumulate)",
+                                   "stage_ms": ms, "flop_per_launch": flop, "achieved_tflops": tflops,
+                                   "peak_tflops": bf16_peak,
+                                   "frac": (tflops / bf16_peak) if (tflops and bf16_peak) else None,
+                                   "peak_kind": "measured cuBLAS bf16 burst"}
 
     e2e = None
     if not args.only_batched:
         e2e = run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done)
     if rank == 0:
         emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks,
-             tuning, skip_quality)
+             tuning, skip_quality, dev.index)
     fe.close()
     for extra in (graph_fe, skip_fe):
         if extra:
@@ -455,7 +550,7 @@ def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done):
 
 
 def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks, tuning,
-         skip_quality):
+         skip_quality, dev_index):
     import numpy as np
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
@@ -465,12 +560,23 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
                   key=lambda k: stage_ms[k])
         alg = algorithmic_bytes(dom, pairs, params, counts)
         ach = alg / (stage_ms[dom] / 1e3) / 1e9
+        prof = profile_summary(KERNELS[dom], args.workload)
         roof = {"bound": "hbm", "kernel": KERNELS[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth",
                 "algorithmic_bytes_per_launch": alg,
-                "traffic": profiled_traffic(KERNELS[dom], args.workload),
+                "traffic": profile_number(prof, "dram_bytes_per_launch_full_workload"),
                 "stage_ms_per_launch": stage_ms}
-    cpu = None if args.no_cpu_baseline else cpu_baseline(args, pairs, params, lo)
+        # the same launch against the integer issue rate (instructions from ncu)
+        warp_inst = profile_number(prof, "inst_executed_warp_per_launch")
+        if warp_inst:
+            apeak, sms, mhz = alu_peak(dev_index)
+            lane_ops = warp_inst * 32
+            pixels = algorithmic_bytes("detect", pairs, params, counts)  # level pixels tested (1 byte each)
+            roof["alu"] = {"achieved": lane_ops / (stage_ms[dom] / 1e3), "peak": apeak, "unit": "lane-op/s",
+                           "frac": lane_ops / (stage_ms[dom] / 1e3) / apeak,
+                           "peak_kind": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz",
+                           "inst_per_launch": lane_ops, "ops_per_pixel": lane_ops / pixels}
+    cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args, pairs, params, lo)
     launches = {"batched": LAUNCHES_PER_CALL, "graph": LAUNCHES_PER_CALL, "plain": LAUNCHES_PER_CALL * n,
                 "learned_skip": LAUNCHES_PER_CALL + 2}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
