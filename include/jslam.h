@@ -61,7 +61,11 @@ enum { JSLAM_MEM_DEVICE = 0, JSLAM_MEM_HOST = 1 };
  *   device and is read in place.
  * memory == JSLAM_MEM_HOST: `data` is host memory (pinned memory makes the
  *   copy asynchronous); the library copies it into its own device staging
- *   buffer on the context stream. */
+ *   buffer on the context stream.  Host images of one call that lie back to
+ *   back in host memory (image k + 1 starting at data_k + pitch_k x
+ *   height_k, in the order left 0, right 0, left 1, ...) with pitch <= width
+ *   rounded up to 128 are copied with a single transfer; keeping a step's
+ *   frames in one pinned buffer therefore makes the upload one copy. */
 typedef struct {
     int32_t width, height, pitch;
     int32_t memory;
@@ -186,6 +190,19 @@ jslam_status jslam_result_bytes(jslam_ctx *ctx, int32_t pair, size_t *bytes);
  * asynchronous).  After jslam_sync the block can be read with
  * jslam_result_view. */
 jslam_status jslam_download(jslam_ctx *ctx, int32_t pair, void *dst, size_t bytes);
+
+/* The result blocks of pairs [first, first + count) lie back to back in
+ * device memory: their total size in *bytes and, if `offsets` is not NULL,
+ * pair first + i's block at offsets[i] (count entries) from the first.
+ * JSLAM_ERR_ARG for an empty or out-of-range span, JSLAM_ERR_STATE before
+ * the first extraction. */
+jslam_status jslam_result_range(jslam_ctx *ctx, int32_t first, int32_t count, size_t *bytes, size_t *offsets);
+
+/* Enqueue ONE asynchronous copy of the result blocks of pairs [first,
+ * first + count) into host memory `dst` of at least the jslam_result_range
+ * bytes; pair first + i's block is then at dst + offsets[i], readable with
+ * jslam_result_view after jslam_sync. */
+jslam_status jslam_download_range(jslam_ctx *ctx, int32_t first, int32_t count, void *dst, size_t bytes);
 
 /* Interpret a downloaded result block: fill host views of `side` (0 or 1)
  * into *kp and, for side 0, the matches into *m (may be NULL).  Pure host

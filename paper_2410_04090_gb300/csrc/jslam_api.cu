@@ -679,25 +679,53 @@ jslam_status jslam_extract_batch(jslam_ctx *ctx, const jslam_stereo_job *jobs, i
     if (st != JSLAM_OK) return st;
 
     // Level-0 inputs of this call; host images are copied into the staging
-    // buffers on the context stream first.
+    // buffers on the context stream first.  Host images that lie back to
+    // back in host memory (each starting where the previous one's pitch x
+    // height ends) and whose pitch fits the staging slot go up in ONE copy
+    // that keeps their pitch (a copy costs ~6 us of setup, and strided 2-D
+    // copies run far below the link rate); other host images use one 2-D
+    // copy each into a 128-aligned pitch.
     Batch &b = ctx->batch;
-    for (int p = 0; p < n; ++p) {
-        const jslam_image *im[2] = { &jobs[p].left, &jobs[p].right };
-        for (int s = 0; s < 2; ++s) {
-            const int img = 2 * p + s;
-            if (im[s]->memory == JSLAM_MEM_HOST) {
-                uint8_t *dst = ctx->staging.as<uint8_t>(ctx->staging_off[img]);
-                const int dpitch = (int)align_up((size_t)im[s]->width, 128);
-                cudaError_t e = cudaMemcpy2DAsync(dst, dpitch, im[s]->data, im[s]->pitch, im[s]->width,
-                                                  im[s]->height, cudaMemcpyHostToDevice, ctx->stream);
-                if (e != cudaSuccess) return fail(ctx, e);
-                b.in.ptr[img] = dst;
-                b.in.pitch[img] = dpitch;
-            } else {
-                b.in.ptr[img] = im[s]->data;
-                b.in.pitch[img] = im[s]->pitch;
-            }
+    const int n_img = 2 * n;
+    auto image_of = [&](int img) -> const jslam_image & { return img & 1 ? jobs[img >> 1].right : jobs[img >> 1].left; };
+    auto fits_slot = [](const jslam_image &im) { return (size_t)im.pitch <= align_up((size_t)im.width, 128); };
+    for (int img = 0; img < n_img;) {
+        const jslam_image &im = image_of(img);
+        if (im.memory != JSLAM_MEM_HOST) {
+            b.in.ptr[img] = im.data;
+            b.in.pitch[img] = im.pitch;
+            ++img;
+            continue;
         }
+        uint8_t *dst = ctx->staging.as<uint8_t>(ctx->staging_off[img]);
+        if (!fits_slot(im)) {
+            const int dpitch = (int)align_up((size_t)im.width, 128);
+            cudaError_t e = cudaMemcpy2DAsync(dst, dpitch, im.data, im.pitch, im.width, im.height,
+                                              cudaMemcpyHostToDevice, ctx->stream);
+            if (e != cudaSuccess) return fail(ctx, e);
+            b.in.ptr[img] = dst;
+            b.in.pitch[img] = dpitch;
+            ++img;
+            continue;
+        }
+        int last = img;  // extend the run while the next image continues it in host memory
+        while (last + 1 < n_img) {
+            const jslam_image &cur = image_of(last), &nxt = image_of(last + 1);
+            if (nxt.memory != JSLAM_MEM_HOST || !fits_slot(nxt) ||
+                nxt.data != cur.data + (size_t)cur.pitch * (size_t)cur.height)
+                break;
+            ++last;
+        }
+        const jslam_image &lim = image_of(last);
+        const size_t span = (size_t)(lim.data - im.data) + (size_t)lim.pitch * (size_t)(lim.height - 1) + lim.width;
+        cudaError_t e = cudaMemcpyAsync(dst, im.data, span, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return fail(ctx, e);
+        for (int k = img; k <= last; ++k) {
+            const jslam_image &ik = image_of(k);
+            b.in.ptr[k] = dst + (ik.data - im.data);
+            b.in.pitch[k] = ik.pitch;
+        }
+        img = last + 1;
     }
     cudaError_t e;
     for (bool &d : ctx->stage_done) d = false;
@@ -831,6 +859,33 @@ jslam_status jslam_download(jslam_ctx *ctx, int32_t pair, void *dst, size_t byte
     if (st != JSLAM_OK) return st;
     return fail(ctx, cudaMemcpyAsync(dst, ctx->results.as<char>(ctx->result_off[pair]), ctx->layouts[pair].bytes,
                                      cudaMemcpyDeviceToHost, ctx->stream));
+}
+
+jslam_status jslam_result_range(jslam_ctx *ctx, int32_t first, int32_t count, size_t *bytes, size_t *offsets)
+{
+    if (!ctx || !bytes) return JSLAM_ERR_ARG;
+    if (!ctx->have_extract) return JSLAM_ERR_STATE;
+    if (first < 0 || count < 1 || first + count > (int)ctx->layouts.size()) return JSLAM_ERR_ARG;
+    const size_t base = ctx->result_off[first];
+    const int end = first + count - 1;
+    *bytes = ctx->result_off[end] + ctx->layouts[end].bytes - base;
+    if (offsets)
+        for (int i = 0; i < count; ++i) offsets[i] = ctx->result_off[first + i] - base;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_download_range(jslam_ctx *ctx, int32_t first, int32_t count, void *dst, size_t bytes)
+{
+    if (!ctx || !dst) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    size_t need = 0;
+    jslam_status st = jslam_result_range(ctx, first, count, &need, nullptr);
+    if (st != JSLAM_OK) return st;
+    if (bytes < need) return JSLAM_ERR_ARG;
+    st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    return fail(ctx, cudaMemcpyAsync(dst, ctx->results.as<char>(ctx->result_off[first]), need, cudaMemcpyDeviceToHost,
+                                     ctx->stream));
 }
 
 jslam_status jslam_result_view(jslam_ctx *ctx, int32_t pair, const void *block, int32_t side, jslam_keypoints *kp,

@@ -571,11 +571,13 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
 
         // pixels evaluated: tile-local x in [plo, phi), rows whose y is inside the border
         const int plo = max(border - x0, 0), phi = min(W - border - x0, tw);
-        const int gpr = (tw + 3) >> 2, ngroups = gpr * th;
+        // groups that hold evaluated pixels: rows [r0, r1) and group columns
+        // [g0, g1) of the tile (only the first and last column can be partial)
+        const int r0 = max(border - y0, 0), r1 = min(Hh - border - y0, th);
+        const int g0 = plo >> 2, g1 = (phi + 3) >> 2;
+        const int gw = max(g1 - g0, 0), nitems = max(r1 - r0, 0) * gw;
         // word of tile column 0 (pixel x0 - 4) within a box row
         const uint32_t *words = reinterpret_cast<const uint32_t *>(tb) + (G.delta >> 2);
-
-        const int nitems = ngroups;
 
         // 1./2. per threshold pass: (a) cardinal pre-test of every group, the
         // survivors compacted with their pixel masks (entry: row << 9 | group
@@ -592,18 +594,18 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
                 if (!need_lo) break;
             }
             const uint32_t e0 = (uint32_t)eps * 0x01010101u, e1 = (uint32_t)(eps + 1) * 0x01010101u;
-            const int gstep_y = kFastThreads / gpr, gstep_x = kFastThreads - gstep_y * gpr;
-            int py = threadIdx.x / gpr, g = threadIdx.x - (threadIdx.x / gpr) * gpr;
+            const int gstep_y = gw > 0 ? kFastThreads / gw : 0, gstep_x = kFastThreads - gstep_y * gw;
+            int py = gw > 0 ? r0 + (int)threadIdx.x / gw : 0;
+            int g = gw > 0 ? g0 + (int)threadIdx.x % gw : 0;
             for (int base = warp * 32; base < nitems; base += kFastThreads) {
                 const int gi = base + lane;
                 uint32_t pre = 0;
                 if (gi < nitems) {
-                    const int gy = y0 + py;
                     const int px0 = 4 * g;
-                    if (gy >= border && gy < Hh - border && px0 + 3 >= plo && px0 < phi) {
-                        uint32_t valid = 0;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) valid |= (uint32_t)(px0 + j >= plo && px0 + j < phi) << j;
+                    {
+                        // pixels px0 + j with plo <= px0 + j < phi
+                        const int lo = min(max(plo - px0, 0), 4), hi = min(max(phi - px0, 0), 4);
+                        uint32_t valid = (0xFu >> (4 - hi)) & (0xFu << lo) & 0xFu;
                         const int crow = div_small(py, cinv) * ncx;
                         if (pass == 1) {
                             // fallback pass: only cells without a corner (and not skipped)
@@ -632,7 +634,7 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
                 start = __shfl_sync(0xFFFFFFFFu, start, 0);
                 if (pre) cand[start + __popc(m & ((1u << lane) - 1u))] = (uint16_t)((py << 9) | (g << 4) | pre);
                 g += gstep_x; py += gstep_y;
-                if (g >= gpr) { g -= gpr; ++py; }
+                if (g >= g1) { g -= gw; ++py; }
             }
             __syncthreads();
             const int ncand = n_cand[pass];

@@ -32,17 +32,25 @@ __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
     const uint8_t *raw = L.raw;
     const int pitch = L.pitch;
 
+    // The keypoint is at least `border` (>= 16) from every edge, so the whole
+    // (2R+1)^2 square around it is inside the level: all 31 rows are loaded
+    // at once (no dependent chain) and the disk is applied as a mask.
     int m10 = 0, m01 = 0;
     if (lane < 2 * kDiskR + 1) {
         const int dx = lane - kDiskR;
         const uint8_t *col = raw + (size_t)(y - kDiskR) * pitch + (x + dx);
-        for (int dy = -kDiskR; dy <= kDiskR; ++dy, col += pitch) {
-            if (dx * dx + dy * dy <= kDiskR * kDiskR) {
-                const int v = __ldg(col);
-                m10 += dx * v;
-                m01 += dy * v;
-            }
+        int v[2 * kDiskR + 1];
+#pragma unroll
+        for (int r = 0; r <= 2 * kDiskR; ++r) v[r] = __ldg(col + (size_t)r * pitch);
+        int s = 0;
+#pragma unroll
+        for (int r = 0; r <= 2 * kDiskR; ++r) {
+            const int dy = r - kDiskR;
+            const int w = dx * dx + dy * dy <= kDiskR * kDiskR ? v[r] : 0;
+            s += w;
+            m01 += dy * w;
         }
+        m10 = dx * s;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -91,14 +99,25 @@ cudaError_t launch_orient_desc(const Batch &b, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-// First index in [lo, hi) whose Y is >= v (Y non-decreasing on the range).
-__device__ __forceinline__ int lower_bound_Y(const uint16_t *Y, int lo, int hi, int v)
+// First index in [lo, hi) whose Y is >= v (Y non-decreasing on the range),
+// found by the whole warp: each round the 32 lanes probe 32 evenly spaced
+// positions and the ballot narrows the range 32-fold (a few dependent loads
+// instead of one per halving).  Every lane returns the same index.
+__device__ __forceinline__ int warp_lower_bound_Y(const uint16_t *Y, int lo, int hi, int v, int lane)
 {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if ((int)Y[mid] < v) lo = mid + 1; else hi = mid;
+    while (hi - lo > 32) {
+        const int n = hi - lo;
+        // probe k marks the end of slice k: position lo + (n * (k + 1)) / 32 - 1
+        const int pos = lo + (int)(((long long)n * (lane + 1)) >> 5) - 1;
+        const uint32_t below = __ballot_sync(0xFFFFFFFFu, (int)__ldg(Y + pos) < v);
+        const int c = __popc(below);  // slices 0..c-1 lie entirely below v
+        const int nlo = c == 0 ? lo : lo + (int)(((long long)n * c) >> 5);
+        const int nhi = c == 32 ? hi : lo + (int)(((long long)n * (c + 1)) >> 5);
+        lo = nlo;
+        hi = nhi;
     }
-    return lo;
+    const bool below = lo + lane < hi && (int)__ldg(Y + lo + lane) < v;
+    return lo + __popc(__ballot_sync(0xFFFFFFFFu, below));
 }
 
 __global__ void __launch_bounds__(256) k_match(Batch b)
@@ -122,8 +141,8 @@ __global__ void __launch_bounds__(256) k_match(Batch b)
     const int m_lo = max(0, n - 1), m_hi = min(Ir.levels - 1, n + 1);
     for (int m = m_lo; m <= m_hi; ++m) {
         const int s = Ir.level_start[m], e = Ir.level_start[m + 1];
-        const int a = lower_bound_Y(orr.Y, s, e, Y - band);
-        const int z = lower_bound_Y(orr.Y, a, e, Y + band + 1);
+        const int a = warp_lower_bound_Y(orr.Y, s, e, Y - band, lane);
+        const int z = warp_lower_bound_Y(orr.Y, a, e, Y + band + 1, lane);
         for (int j = a + lane; j < z; j += 32) {
             const int disp = X - (int)orr.X[j];
             if (disp < 0 || disp > b.prm.max_disp) continue;

@@ -90,7 +90,7 @@ SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extra
            "jslam_level_geometry", "jslam_project", "jslam_match_band", "jslam_enable_stage_timing",
            "jslam_stage_times", "jslam_pfa_scores_static", "jslam_corner_table", "jslam_set_tuning",
            "jslam_autotune", "jslam_graph_capture", "jslam_graph_launch", "jslam_set_skip_model",
-           "jslam_get_skip_view")
+           "jslam_get_skip_view", "jslam_result_range", "jslam_download_range")
 STAGES = ("pyramid", "skip", "detect", "pfa_nms", "pfa_final", "orb", "match")
 
 _lib = None
@@ -126,6 +126,11 @@ def lib():
         L.jslam_result_bytes.restype = st
         L.jslam_download.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t]
         L.jslam_download.restype = st
+        L.jslam_result_range.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_size_t),
+                                         C.POINTER(C.c_size_t)]
+        L.jslam_result_range.restype = st
+        L.jslam_download_range.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t]
+        L.jslam_download_range.restype = st
         L.jslam_result_view.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.POINTER(Keypoints),
                                         C.POINTER(Matches)]
         L.jslam_result_view.restype = st
@@ -430,6 +435,23 @@ class Frontend:
         else:
             ptr, size = dst.data_ptr(), dst.numel() * dst.element_size()
         _check(lib().jslam_download(self._h, pair, ptr, size), "jslam_download")
+
+    def result_range(self, first: int, count: int):
+        """(total bytes, per-pair offsets) of the result blocks of pairs
+        [first, first + count), which lie back to back."""
+        n = C.c_size_t()
+        offs = (C.c_size_t * count)()
+        _check(lib().jslam_result_range(self._h, first, count, C.byref(n), offs), "jslam_result_range")
+        return n.value, list(offs)
+
+    def download_range(self, first: int, count: int, dst) -> None:
+        """Enqueue one copy of the result blocks of pairs [first, first +
+        count) into `dst` (pinned CPU tensor or numpy array)."""
+        if isinstance(dst, np.ndarray):
+            ptr, size = dst.ctypes.data, dst.nbytes
+        else:
+            ptr, size = dst.data_ptr(), dst.numel() * dst.element_size()
+        _check(lib().jslam_download_range(self._h, first, count, ptr, size), "jslam_download_range")
 
     def result_view(self, pair: int, block, side: int) -> dict:
         """Host arrays (copies) of one side of a downloaded result block."""

@@ -207,6 +207,54 @@ def test_download_result_block(J, oracle):
     fe.close()
 
 
+def test_host_frames_back_to_back_and_ranged_download(J, oracle):
+    """Host frames of two pairs in one buffer (one upload copy), a strided
+    host frame (one 2-D copy), and one ranged download of all result
+    blocks, each block byte-identical to its single-pair download."""
+    import torch
+    p = params_from(oracle, levels=5, max_feats=700, fast_thresh_lo=7)
+    prs = [scenes.planes_pair(420, 300, k, 90, 91) for k in range(2)] + [scenes.planes_pair(300, 200, 0, 92, 93)]
+    flat = np.zeros(4 * 420 * 300, np.uint8)
+    views = []
+    for k in range(2):
+        for j, img in enumerate((prs[k].left, prs[k].right)):
+            v = flat[(2 * k + j) * 420 * 300:(2 * k + j + 1) * 420 * 300].reshape(300, 420)
+            v[...] = img
+            views.append(v)
+    wide = np.zeros((200, 512), np.uint8)          # pitch 512 > 384 = 300 rounded up to 128
+    wide[:, :300] = prs[2].left
+    strided = wide[:, :300]
+    fe = frontend_for(J, p, max_pairs=4)
+    jobs = [J.Job(views[0], views[1], p.levels, p.scale, p.fast_thresh, p.cell, p.max_feats),
+            J.Job(views[2], views[3], p.levels, p.scale, p.fast_thresh, p.cell, p.max_feats),
+            J.Job(strided, np.ascontiguousarray(prs[2].right), p.levels, p.scale, p.fast_thresh, p.cell,
+                  p.max_feats)]
+    fe.extract_batch(jobs)
+    fe.match()
+    total, offs = fe.result_range(0, 3)
+    big = torch.empty(total, dtype=torch.uint8).pin_memory()
+    fe.download_range(0, 3, big)
+    singles = []
+    for k in range(3):
+        t = torch.empty(fe.result_bytes(k), dtype=torch.uint8).pin_memory()
+        fe.download(k, t)
+        singles.append(t)
+    fe.sync()
+    for k, pr in enumerate(prs):
+        ol, orr, om = oracle.extract_pair(pr.left, pr.right, p)
+        compare_keypoints(J.to_numpy(fe.keypoints(k, 0)), ol, f"pair {k} left")
+        compare_keypoints(J.to_numpy(fe.keypoints(k, 1)), orr, f"pair {k} right")
+        compare_matches(J.to_numpy(fe.matches(k)), om, f"pair {k}")
+        block = big[offs[k]: offs[k] + singles[k].numel()]
+        assert torch.equal(block, singles[k]), k
+        compare_keypoints(fe.result_view(k, block.clone(), 0), ol, f"pair {k} ranged view")
+    with pytest.raises(J.JslamError):
+        fe.download_range(0, 3, torch.empty(total - 1, dtype=torch.uint8).pin_memory())
+    with pytest.raises(J.JslamError):
+        fe.result_range(2, 2)
+    fe.close()
+
+
 def test_argument_errors(J):
     import torch
     fe = J.Frontend(device=0, max_width=640, max_height=480, max_levels=4, max_feats=500, max_pairs=2)
