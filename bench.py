@@ -8,11 +8,15 @@ KITTI-shaped sequence (1241x376 u8, 8 levels, scale 1.2, FAST 20 with
 fallback 7, 32x32 cells, 2000 features per image).
 
 Modes, each timed over the same steps:
-  batched       all pairs of the step in one C-ABI call (one launch per stage) -- the headline
-  graph         the batched call captured once as a CUDA graph and replayed
-  plain         one C-ABI call per stereo pair
-  learned_skip  batched, with the learned cell-skip proposal (approximate;
-                its feature recall against the exact path is reported)
+  graph_streams2  the step's pairs split over two contexts on two streams, each
+                  half captured once as a CUDA graph and replayed (fork/join by
+                  events) -- the headline
+  streams2        the same two halves as plain batched calls
+  batched         all pairs of the step in one C-ABI call (one launch per stage)
+  graph           the batched call captured once as a CUDA graph and replayed
+  plain           one C-ABI call per stereo pair
+  learned_skip    batched, with the learned cell-skip proposal (approximate;
+                  its feature recall against the exact path is reported)
 Inputs are resident in HBM before the timed region; L2 is flushed (256 MB
 write) before every timed step.  `e2e` repeats the batched step through the
 C ABI with pinned host images and downloads every result block, copies
@@ -80,7 +84,8 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="kitti_1241x376_L8", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--frames", type=int, default=100, help="pairs per step (sequence workloads)")
-    ap.add_argument("--mode", choices=["batched", "graph", "plain"], default="batched")
+    ap.add_argument("--mode", choices=["batched", "graph", "plain", "streams2", "graph_streams2"],
+                    default="graph_streams2", help="the headline mode (the others are timed beside it)")
     ap.add_argument("--cpu-pairs", type=int, default=12, help="pairs in the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, nargs=2, metavar=("W", "H"),
@@ -413,6 +418,7 @@ def main():
         skip_fe.match()
 
     modes = {"batched": step_batched}
+    extra_fes = []
     if not args.only_batched and os.path.exists(SKIP_MODEL):
         skip_fe = jslam.Frontend(device=dev.index, stream=stream, **dims)
         skip_fe.set_tuning(*tuning)
@@ -425,6 +431,48 @@ def main():
         graph_fe.graph_capture(jobs)
         modes["graph"] = step_graph
         modes["plain"] = step_plain
+    if not args.only_batched and n >= 2:
+        # the step's pairs split over two contexts on two streams (fork and
+        # join on the timing stream): one half's kernels fill the other's
+        # launch gaps and kernel tails
+        half = (n + 1) // 2
+        dims2 = dict(dims, max_pairs=half)
+        s2 = torch.cuda.Stream(device=dev)
+        fa = jslam.Frontend(device=dev.index, stream=stream, **dims2)
+        fb = jslam.Frontend(device=dev.index, stream=s2, **dims2)
+        part = [fa.prepare_batch([jslam.Job(l, r, **p) for l, r, p in zip(lefts[:half], rights[:half], params[:half])]),
+                fb.prepare_batch([jslam.Job(l, r, **p) for l, r, p in zip(lefts[half:], rights[half:], params[half:])])]
+        ga = jslam.Frontend(device=dev.index, stream=stream, **dims2)
+        gb = jslam.Frontend(device=dev.index, stream=s2, **dims2)
+        for c in (fa, fb, ga, gb):
+            c.set_tuning(*tuning)
+        ga.graph_capture(part[0])
+        gb.graph_capture(part[1])
+        extra_fes += [fa, fb, ga, gb]
+
+        def fork_join(body):
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            s2.wait_event(ev)
+            body()
+            ev2 = torch.cuda.Event()
+            ev2.record(s2)
+            stream.wait_event(ev2)
+
+        def step_streams2():
+            def body():
+                fa.extract_batch(part[0]); fa.match()
+                fb.extract_batch(part[1]); fb.match()
+            fork_join(body)
+
+        def step_graph_streams2():
+            def body():
+                ga.graph_launch()
+                gb.graph_launch()
+            fork_join(body)
+
+        modes["streams2"] = step_streams2
+        modes["graph_streams2"] = step_graph_streams2
     if args.mode not in modes:
         args.mode = "batched"
     for _ in range(args.warmup):
@@ -432,23 +480,28 @@ def main():
             s()
     torch.cuda.synchronize()
 
-    # timed region: the headline mode, with per-stage events in batched mode
-    fe.enable_stage_timing(args.mode == "batched")
+    # timed regions: the headline mode first, then every other mode; the
+    # batched mode's steps carry per-stage events (the per-kernel durations
+    # of the roofline)
     stage_acc = {k: 0.0 for k in jslam.STAGES}
 
     def grab():
-        if args.mode == "batched":
-            for k, v in fe.stage_times().items():
-                stage_acc[k] += v
+        for k, v in fe.stage_times().items():
+            stage_acc[k] += v
+
+    def timed_mode(m):
+        fe.enable_stage_timing(m == "batched")
+        ms = timed(modes[m], args.steps, grab if m == "batched" else None)
+        fe.enable_stage_timing(False)
+        return ms
 
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clocks:  # samples every timed region (all modes)
         time.sleep(0.3)  # let the sampler start before the first timed step
-        total_ms = timed(modes[args.mode], args.steps, grab)
-        fe.enable_stage_timing(False)
-        other_ms = {m: timed(s, args.steps) for m, s in modes.items() if m != args.mode}
+        total_ms = timed_mode(args.mode)
+        other_ms = {m: timed_mode(m) for m in modes if m != args.mode}
 
     t = torch.tensor([total_ms] + list(other_ms.values()), dtype=torch.float64, device=dev)
     if dist:
@@ -508,7 +561,7 @@ def main():
         emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks,
              tuning, skip_quality, dev.index)
     fe.close()
-    for extra in (graph_fe, skip_fe):
+    for extra in [graph_fe, skip_fe] + extra_fes:
         if extra:
             extra.close()
     if dist:
@@ -587,7 +640,7 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
     roof = None
-    if args.mode == "batched" and any(stage_ms.values()):
+    if any(stage_ms.values()):
         dom = max((k for k in stage_ms if algorithmic_bytes(k, pairs[:1], params[:1], [1]) is not None),
                   key=lambda k: stage_ms[k])
         alg = algorithmic_bytes(dom, pairs, params, counts)
@@ -597,7 +650,8 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
                 "frac": ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth",
                 "algorithmic_bytes_per_launch": alg,
                 "traffic": profile_number(prof, "dram_bytes_per_launch_full_workload"),
-                "stage_ms_per_launch": stage_ms}
+                "stage_ms_per_launch": stage_ms,
+                "stage_timing": "CUDA events on the context stream between the stages of the batched mode's timed steps"}
         # the same launch against the integer issue rate (instructions from ncu)
         warp_inst = profile_number(prof, "inst_executed_warp_per_launch")
         if warp_inst:
@@ -610,7 +664,8 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
                            "inst_per_launch": lane_ops, "ops_per_pixel": lane_ops / pixels}
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args, pairs, params, lo)
     launches = {"batched": LAUNCHES_PER_CALL, "graph": LAUNCHES_PER_CALL, "plain": LAUNCHES_PER_CALL * n,
-                "learned_skip": LAUNCHES_PER_CALL + 2}
+                "learned_skip": LAUNCHES_PER_CALL + 2, "streams2": 2 * LAUNCHES_PER_CALL,
+                "graph_streams2": 2 * LAUNCHES_PER_CALL}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",

@@ -166,6 +166,7 @@ struct jslam_ctx {
     GrowBuf consts;  // pattern | cos | sin | corner table
     int8_t *d_pattern = nullptr;
     double *d_cos = nullptr, *d_sin = nullptr;
+    float *d_cosf = nullptr, *d_sinf = nullptr;
     uint32_t *d_lut = nullptr;
 
     // per-batch buffers
@@ -535,6 +536,8 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.pattern = ctx->d_pattern;
     b.bin_cos = ctx->d_cos;
     b.bin_sin = ctx->d_sin;
+    b.bin_cosf = ctx->d_cosf;
+    b.bin_sinf = ctx->d_sinf;
     b.err = reinterpret_cast<uint32_t *>(dcounts + 2 * cfg.max_pairs);
     b.prm = ctx->prm;
 
@@ -633,7 +636,8 @@ jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
     if (e == cudaSuccess) e = set_blur_weights(w);
     const size_t pat_bytes = (size_t)kBins * kPairs * 4;
     const size_t lut_off = pat_bytes + 2 * kBins * sizeof(double);
-    const size_t const_bytes = lut_off + kLutWords * sizeof(uint32_t);
+    const size_t f_off = lut_off + kLutWords * sizeof(uint32_t);
+    const size_t const_bytes = f_off + 2 * kBins * sizeof(float);
     if (e == cudaSuccess) e = ctx->consts.ensure(const_bytes + 512, false, nullptr);
     if (e == cudaSuccess) {
         std::vector<char> h(const_bytes, 0);
@@ -641,11 +645,15 @@ jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
         double *cs = reinterpret_cast<double *>(h.data() + pat_bytes);
         sector_tables(cs, cs + kBins);
         corner_table(c.p_min, c.p_max, reinterpret_cast<uint32_t *>(h.data() + lut_off));
+        float *cf = reinterpret_cast<float *>(h.data() + f_off);
+        for (int i = 0; i < 2 * kBins; ++i) cf[i] = static_cast<float>(cs[i]);
         e = cudaMemcpy(ctx->consts.ptr, h.data(), h.size(), cudaMemcpyHostToDevice);
         ctx->d_pattern = ctx->consts.as<int8_t>();
         ctx->d_cos = ctx->consts.as<double>(pat_bytes);
         ctx->d_sin = ctx->d_cos + kBins;
         ctx->d_lut = ctx->consts.as<uint32_t>(lut_off);
+        ctx->d_cosf = ctx->consts.as<float>(f_off);
+        ctx->d_sinf = ctx->d_cosf + kBins;
     }
     if (e == cudaSuccess) e = ctx->counts.ensure(sizeof(int32_t) * (2 * (size_t)c.max_pairs + 8), true, nullptr);
     if (e == cudaSuccess) {

@@ -138,6 +138,7 @@ struct Batch {
     int32_t *canon;                 // slot of each canonical position
     const int8_t *pattern;          // kBins x kPairs x 4
     const double *bin_cos, *bin_sin;
+    const float *bin_cosf, *bin_sinf;  // the same tables rounded to float (fast sector test)
     uint32_t *err;
     Params prm;
     int32_t skip_max_tiles, skip_max_cells;  // learned cell-skip launch shape

@@ -3,13 +3,15 @@
 // matching by descriptor-distance minimisation).
 //
 // k_orient_desc  one warp per keypoint of any image and level.  Lanes 0..30
-//                own one column of the radius-15 disk and walk its rows to
-//                accumulate the intensity moments m10, m01 on the raw level;
-//                lanes 0..29 each test one sector boundary in IEEE double
-//                (explicit round-to-nearest multiplies and subtract, so the
-//                sector equals the one the host-side definition gives); the
-//                256 BRIEF comparisons on the blurred level are issued 32 at a
-//                time and packed into words by a ballot.
+//                own one column of the radius-15 disk and load all its rows
+//                at once to accumulate the intensity moments m10, m01 on the
+//                raw level; lanes 0..26 stage the 27 x 27 blurred patch the
+//                BRIEF pattern reaches in shared memory; lanes 0..29 each test
+//                one sector boundary (float with an error margin, IEEE double
+//                with explicit rounding inside it, so the sector equals the
+//                one the host-side definition gives); the 256 BRIEF
+//                comparisons read the patch 32 at a time and are packed into
+//                words by a ballot.
 // k_match        one warp per left keypoint: for each right level within one
 //                of the keypoint's level, binary-searches the s0 row band in
 //                the canonical (level, y, x) list (Y is non-decreasing in y),
@@ -19,8 +21,13 @@
 
 namespace jslam {
 
+constexpr int kPatR = 13;                 // rotated BRIEF offsets lie in [-13, 13]
+constexpr int kPatW = 2 * kPatR + 1;      // 27
+constexpr int kPatPitch = kPatW + 1;
+
 __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
 {
+    __shared__ uint8_t s_patch[8][kPatW * kPatPitch];
     const int img = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -31,10 +38,22 @@ __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
     const LevelDesc &L = b.levels[I.level_base + lvl];
     const uint8_t *raw = L.raw;
     const int pitch = L.pitch;
+    const int bpitch = L.blur_pitch;
+    uint8_t *patch = s_patch[threadIdx.x >> 5];
 
-    // The keypoint is at least `border` (>= 16) from every edge, so the whole
-    // (2R+1)^2 square around it is inside the level: all 31 rows are loaded
-    // at once (no dependent chain) and the disk is applied as a mask.
+    // The keypoint is at least `border` (>= 16) from every edge, so the
+    // 31 x 31 square of the moment disk and the 27 x 27 patch of the BRIEF
+    // pattern are inside the level: every row is loaded at once (no
+    // dependent chain), lanes on consecutive columns (one or two sectors per
+    // row), and the disk is applied as a mask.
+    if (lane < kPatW) {
+        const uint8_t *src = L.blur + (size_t)(y - kPatR) * bpitch + (x - kPatR + lane);
+        uint32_t v[kPatW];
+#pragma unroll
+        for (int r = 0; r < kPatW; ++r) v[r] = __ldg(src + (size_t)r * bpitch);
+#pragma unroll
+        for (int r = 0; r < kPatW; ++r) patch[r * kPatPitch + lane] = (uint8_t)v[r];
+    }
     int m10 = 0, m01 = 0;
     if (lane < 2 * kDiskR + 1) {
         const int dx = lane - kDiskR;
@@ -59,12 +78,23 @@ __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
     }
 
     // Sector b is the one whose lower boundary has the moment vector on its
-    // left (cross product >= 0) and whose upper boundary does not.
+    // left (m01 cos - m10 sin >= 0 in IEEE double) and whose upper boundary
+    // does not.  The test runs in float first: |m| < 2^24 is exact, and the
+    // float result is within (|m01| + |m10|) 2^-22 of the exact value with
+    // the double table entries, so outside 2^-20 times that its sign is the
+    // double test's; lanes inside the margin (rare) take the double test.
     bool left_of = false;
     if (lane < kBins) {
-        const double t1 = __dmul_rn((double)m01, b.bin_cos[lane]);
-        const double t2 = __dmul_rn((double)m10, b.bin_sin[lane]);
-        left_of = __dsub_rn(t1, t2) >= 0.0;
+        const float fa = (float)m01, fb = (float)m10;
+        const float t = __fsub_rn(__fmul_rn(fa, __ldg(b.bin_cosf + lane)), __fmul_rn(fb, __ldg(b.bin_sinf + lane)));
+        const float margin = (fabsf(fa) + fabsf(fb)) * 0x1p-20f;
+        if (fabsf(t) > margin) {
+            left_of = t > 0.0f;
+        } else {
+            const double t1 = __dmul_rn((double)m01, b.bin_cos[lane]);
+            const double t2 = __dmul_rn((double)m10, b.bin_sin[lane]);
+            left_of = __dsub_rn(t1, t2) >= 0.0;
+        }
     }
     const uint32_t S = __ballot_sync(0xFFFFFFFFu, left_of) & ((1u << kBins) - 1u);
     const uint32_t next = (S >> 1) | ((S & 1u) << (kBins - 1));
@@ -72,15 +102,15 @@ __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
     const bool zero = (m10 == 0 && m01 == 0);
     const int bin = (zero || T == 0) ? 0 : __ffs(T) - 1;
 
-    const int bpitch = L.blur_pitch;
-    const uint8_t *blur = L.blur + (size_t)y * bpitch + x;
+    __syncwarp();  // the patch is complete
     const char4 *pat = reinterpret_cast<const char4 *>(b.pattern) + (size_t)bin * kPairs;
+    const uint8_t *centre = patch + kPatR * kPatPitch + kPatR;
     uint32_t myword = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
         const char4 pq = __ldg(pat + w * 32 + lane);
-        const int a = __ldg(blur + pq.y * bpitch + pq.x);
-        const int c = __ldg(blur + pq.w * bpitch + pq.z);
+        const int a = centre[pq.y * kPatPitch + pq.x];
+        const int c = centre[pq.w * kPatPitch + pq.z];
         const uint32_t word = __ballot_sync(0xFFFFFFFFu, a < c);
         if (lane == w) myword = word;
     }

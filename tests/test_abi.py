@@ -82,3 +82,34 @@ def test_cardinal_pretest_is_necessary(oracle):
     passes = ((f(0) | f(8)) & (f(4) | f(12))).astype(bool)
     assert passes[runs >= 8].all()
     assert not passes[runs == 7].all()
+
+
+def test_sector_float_margin_agrees_with_double(jslam):
+    """The orientation kernel decides each sector boundary in float when
+    |m01 cos - m10 sin| exceeds (|m01| + |m10|) 2^-20 and in IEEE double
+    otherwise.  Emulated here with numpy float32 / float64 (both round to
+    nearest, no fused operations) on random moments and on moments placed
+    next to every boundary: where float decides, it agrees with double."""
+    b = np.arange(30)
+    phi = 2 * np.pi * b / 30.0
+    c64, s64 = np.cos(phi), np.sin(phi)  # the argument holds for any table with |c|, |s| <= 1
+    c32, s32 = c64.astype(np.float32), s64.astype(np.float32)
+    rng = np.random.default_rng(0)
+    a = rng.integers(-(1 << 22), 1 << 22, 200000)
+    bb = rng.integers(-(1 << 22), 1 << 22, 200000)
+    # moments almost exactly along a boundary direction
+    k = rng.integers(0, 30, 200000)
+    r = rng.integers(1, 1 << 22, 200000).astype(np.float64)
+    a2 = np.round(r * s64[k]).astype(np.int64) + rng.integers(-2, 3, 200000)
+    b2 = np.round(r * c64[k]).astype(np.int64) + rng.integers(-2, 3, 200000)
+    m01 = np.concatenate([a, a2]); m10 = np.concatenate([bb, b2])
+    decided = fallback = 0
+    for j in range(30):
+        t64 = (m01 * c64[j]) - (m10 * s64[j])
+        fa, fb = m01.astype(np.float32), m10.astype(np.float32)
+        t32 = (fa * c32[j]).astype(np.float32) - (fb * s32[j]).astype(np.float32)
+        margin = (np.abs(fa) + np.abs(fb)) * np.float32(2.0 ** -20)
+        sure = np.abs(t32) > margin
+        assert np.array_equal((t32 > 0)[sure], (t64 >= 0)[sure])
+        decided += int(sure.sum()); fallback += int((~sure).sum())
+    assert fallback > 0 and decided > 10 * fallback  # half the samples sit on boundaries on purpose
