@@ -710,3 +710,118 @@ void or_match(const or_keypoints *Lk, const or_keypoints *Rk, const or_params *p
         }
     }
 }
+
+/* ------------------------------------------------------------------ */
+/* Correlation minimisation (Sec. III, middle-end stereo matching: the SLAM
+ * pipeline figure names it beside descriptor-distance minimisation; the
+ * text gives no detail).  Reading: the sub-pixel refinement of the stereo
+ * SLAM system the paper builds on, restated here.  For each left keypoint i
+ * with an accepted descriptor match j, on the left keypoint's level n of
+ * both raw pyramids (s = zeta^n):
+ *   xr0 = floor(X_j / s + 0.5), the match's s0 column at level n;
+ *   for shifts t = -L..L: the (2w+1)^2 patches centred on (x_i, y_i) in the
+ *   left level and on (xr0 + t, y_i) in the right level, each minus its own
+ *   centre pixel, and SAD(t) = sum of |left - right|; t* = the first
+ *   minimum; a window leaving the level rejects (SAD reported as none);
+ *   t* = -L or t* = L rejects (a minimum at the end of the search);
+ *   d1, d2, d3 = SAD(t* - 1), SAD(t*), SAD(t* + 1); the parabola through
+ *   them peaks at delta = (d1 - d3) / (2 (d1 + d3 - 2 d2)); a flat minimum
+ *   (d1 + d3 = 2 d2) or |delta| > 1 rejects;
+ *   disparity = s (x_i - xr0 - t* - delta) in s0 pixels; outside
+ *   [0, max_disp] rejects; depth = bf / max(disparity, 0.01) when bf > 0.
+ * Then, over the pair's matches that survived, median = the SAD at index
+ * count / 2 of the ascending list; a match with 10 SAD > 21 median (SAD
+ * above 2.1 times the median, in integers) is rejected as an outlier.  The
+ * decisions use integers; delta, disparity and depth are IEEE double,
+ * reported as float.  Outputs per left keypoint: disparity (-1 rejected),
+ * depth (0 rejected), SAD(t*) (0xFFFFFFFF when no SAD was computed).      */
+
+static void sp_levels(const uint8_t *L0, int32_t W0, int32_t H0, int32_t pitch0, const or_params *p,
+                      uint8_t **lev, int32_t *Wn, int32_t *Hn)
+{
+    int32_t c[OR_MAX_LEVELS];
+    or_level_geometry(W0, H0, p->levels, p->scale, p->cell, Wn, Hn, c);
+    for (int32_t n = 0; n < p->levels; ++n) {
+        lev[n] = (uint8_t *)malloc((size_t)Wn[n] * (size_t)Hn[n]);
+        if (n == 0) {
+            for (int32_t y = 0; y < H0; ++y) memcpy(lev[0] + (size_t)y * W0, L0 + (size_t)y * pitch0, (size_t)W0);
+        } else {
+            or_pyramid_level(L0, W0, H0, pitch0, p->scale, n, lev[n], Wn[n], Hn[n], Wn[n]);
+        }
+    }
+}
+
+static int cmp_u32(const void *a, const void *b)
+{
+    uint32_t x = *(const uint32_t *)a, y = *(const uint32_t *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+void or_subpixel(const uint8_t *left0, const uint8_t *right0, int32_t W0, int32_t H0, int32_t pitch0,
+                 const or_keypoints *Lk, const or_keypoints *Rk, const int32_t *right_idx,
+                 const or_params *p, int32_t w, int32_t L, double bf,
+                 float *disp_out, float *depth_out, uint32_t *sad_out)
+{
+    uint8_t *lv[OR_MAX_LEVELS], *rv[OR_MAX_LEVELS];
+    int32_t Wn[OR_MAX_LEVELS], Hn[OR_MAX_LEVELS];
+    sp_levels(left0, W0, H0, pitch0, p, lv, Wn, Hn);
+    sp_levels(right0, W0, H0, pitch0, p, rv, Wn, Hn);
+    uint32_t *kept = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(Lk->count > 0 ? Lk->count : 1));
+    int32_t n_kept = 0;
+    for (int32_t i = 0; i < Lk->count; ++i) {
+        disp_out[i] = -1.0f;
+        depth_out[i] = 0.0f;
+        sad_out[i] = 0xFFFFFFFFu;
+        int32_t j = right_idx[i];
+        if (j < 0) continue;
+        int32_t n = Lk->level[i], xi = Lk->x[i], yi = Lk->y[i];
+        double s = or_level_scale(p->scale, n);
+        int32_t xr0 = (int32_t)floor((double)Rk->X[j] / s + 0.5);
+        int32_t W = Wn[n], H = Hn[n];
+        if (xi - w < 0 || xi + w >= W || yi - w < 0 || yi + w >= H || xr0 - L - w < 0 || xr0 + L + w >= W)
+            continue;
+        const uint8_t *A = lv[n], *B = rv[n];
+        int32_t lc = A[(size_t)yi * W + xi];
+        int64_t sad[2 * 7 + 1] = { 0 };
+        int32_t best = 0;
+        for (int32_t t = -L; t <= L; ++t) {
+            int32_t rc = B[(size_t)yi * W + xr0 + t];
+            int64_t acc = 0;
+            for (int32_t dy = -w; dy <= w; ++dy)
+                for (int32_t dx = -w; dx <= w; ++dx) {
+                    int32_t a = (int32_t)A[(size_t)(yi + dy) * W + xi + dx] - lc;
+                    int32_t b = (int32_t)B[(size_t)(yi + dy) * W + xr0 + t + dx] - rc;
+                    acc += a > b ? a - b : b - a;
+                }
+            sad[t + L] = acc;
+            if (acc < sad[best]) best = t + L;
+        }
+        int32_t ts = best - L;
+        sad_out[i] = (uint32_t)sad[best];
+        if (ts == -L || ts == L) continue;
+        int64_t d1 = sad[best - 1], d2 = sad[best], d3 = sad[best + 1];
+        int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);
+        if (den == 0) continue;
+        if ((num < 0 ? -num : num) > den) continue;
+        int64_t q = (int64_t)xi - xr0 - ts;
+        /* disparity >= 0  <=>  q den >= num;  disparity <= max_disp  <=>  s (q den - num) <= max_disp den */
+        if (q * den < num) continue;
+        if (s * (double)(q * den - num) > (double)p->max_disp * (double)den) continue;
+        double delta = (double)num / (double)den;
+        double disp = s * ((double)q - delta);
+        disp_out[i] = (float)disp;
+        depth_out[i] = bf > 0.0 ? (float)(bf / (disp > 0.01 ? disp : 0.01)) : 0.0f;
+        kept[n_kept++] = (uint32_t)sad[best];
+    }
+    if (n_kept > 0) {
+        qsort(kept, (size_t)n_kept, sizeof(uint32_t), cmp_u32);
+        uint64_t median = kept[n_kept / 2];
+        for (int32_t i = 0; i < Lk->count; ++i)
+            if (disp_out[i] >= 0.0f && 10u * (uint64_t)sad_out[i] > 21u * median) {
+                disp_out[i] = -1.0f;
+                depth_out[i] = 0.0f;
+            }
+    }
+    free(kept);
+    for (int32_t n = 0; n < p->levels; ++n) { free(lv[n]); free(rv[n]); }
+}

@@ -135,6 +135,9 @@ def lib():
         L.or_match_band.argtypes = [i32, C.c_float, i32]
         L.or_match.argtypes = [C.POINTER(_Keypoints), C.POINTER(_Keypoints), C.POINTER(Params),
                                i32p, i16p, u16p]
+        f32p = np.ctypeslib.ndpointer(np.float32, flags="C")
+        L.or_subpixel.argtypes = [u8p, u8p, i32, i32, i32, C.POINTER(_Keypoints), C.POINTER(_Keypoints), i32p,
+                                  C.POINTER(Params), i32, i32, C.c_double, f32p, f32p, u32p]
         _lib = L
     return _lib
 
@@ -348,6 +351,27 @@ def match(kl: dict, kr: dict, p: FrontendParams):
     lib().or_match(C.byref(sl), C.byref(sr), C.byref(cp), idx, disp, dist)
     del keep_l, keep_r
     return idx[:n].copy(), disp[:n].copy(), dist[:n].copy()
+
+
+def subpixel(left: np.ndarray, right: np.ndarray, kl: dict, kr: dict, right_idx: np.ndarray,
+             p: FrontendParams, half_window: int = 5, search: int = 5, bf: float = 0.0):
+    """Correlation minimisation of the accepted matches (Sec. III middle-end):
+    per left keypoint the sub-pixel disparity (-1 rejected), depth (0
+    rejected) and best SAD (0xFFFFFFFF when none was computed)."""
+    left = np.ascontiguousarray(left, np.uint8)
+    right = np.ascontiguousarray(right, np.uint8)
+    assert left.shape == right.shape and 1 <= search <= 7 and half_window >= 1
+    sl, keep_l = _as_struct(kl)
+    sr, keep_r = _as_struct(kr)
+    n = kl["count"]
+    ridx = np.ascontiguousarray(np.concatenate([np.asarray(right_idx, np.int32)[:n], [-1]]), np.int32)
+    disp = np.zeros(n + 1, np.float32); depth = np.zeros(n + 1, np.float32); sad = np.zeros(n + 1, np.uint32)
+    cp = p.to_c()
+    H, W = left.shape
+    lib().or_subpixel(left, right, W, H, W, C.byref(sl), C.byref(sr), ridx, C.byref(cp), half_window, search,
+                      float(bf), disp, depth, sad)
+    del keep_l, keep_r
+    return {"disparity": disp[:n].copy(), "depth": depth[:n].copy(), "sad": sad[:n].copy()}
 
 
 def extract_pair(left: np.ndarray, right: np.ndarray, p: FrontendParams):
