@@ -74,6 +74,7 @@ KERNEL_SOURCES = {"k_pyramid": "k_detect.cu", "k_fast_cull": "k_detect.cu", "k_p
                   "k_pfa_finalize": "k_pyca.cu", "k_orient_desc": "k_orb_match.cu", "k_match": "k_orb_match.cu"}
 LAUNCHES_PER_CALL = 6  # pyramid, detect, PFA NMS, PFA final, ORB, match (exact path)
 SKIP_MODEL = os.path.join(ROOT, "paper_2410_04090_gb300", "skipnet_v1.bin")
+REFINE_BF = 386.1448  # fx * baseline (pixels x metres) of a KITTI-like stereo rig, for the depth output
 
 
 def parse_args():
@@ -554,12 +555,33 @@ def main():
                                    "frac": (tflops / bf16_peak) if (tflops and bf16_peak) else None,
                                    "peak_kind": "measured cuBLAS bf16 burst"}
 
+    # correlation minimisation (the middle-end's sub-pixel refinement, a step
+    # beyond the hot path): timed beside the headline on the batched context
+    refine = None
+    if not args.only_batched:
+        ref_ms = []
+
+        def step_refine():
+            fe.extract_batch(jobs)
+            fe.match()
+            fe.refine_matches(5, 5, REFINE_BF)
+
+        fe.enable_stage_timing(True)
+        ref_total = timed(step_refine, args.steps, lambda: ref_ms.append(fe.stage_times()["refine"]))
+        fe.enable_stage_timing(False)
+        fe.sync()
+        matched = sum(int((fe.matches(p)["right_idx"] >= 0).sum()) for p in range(n))
+        kept = sum(int((fe.refined(p)["disparity"] >= 0).sum()) for p in range(n))
+        refine = {"stage_ms": statistics.median(ref_ms), "value_with_refine": n * args.steps / (ref_total / 1e3),
+                  "unit": UNIT, "mode": "batched + jslam_refine_matches(half_window 5, search 5)",
+                  "refined_fraction_of_matches": kept / max(matched, 1)}
+
     e2e = None
     if not args.only_batched:
         e2e = run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, stream)
     if rank == 0:
         emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks,
-             tuning, skip_quality, dev.index)
+             tuning, skip_quality, dev.index, refine)
     fe.close()
     for extra in [graph_fe, skip_fe] + extra_fes:
         if extra:
@@ -635,7 +657,7 @@ def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, 
 
 
 def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks, tuning,
-         skip_quality, dev_index):
+         skip_quality, dev_index, refine=None):
     import numpy as np
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
@@ -672,7 +694,7 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
             "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
                        "pairs_per_step": n, "mode": args.mode, "detect_tile_px": list(tuning),
                        "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
-            "modes": mode_values, "learned_skip": skip_quality,
+            "modes": mode_values, "learned_skip": skip_quality, "refine": refine,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks.summary(), "gpu_launches": launches[args.mode] * args.steps,
             "keypoints_per_image_mean": float(np.mean(counts))}

@@ -127,6 +127,38 @@ typedef struct {
     const uint16_t *dist;         /* Hamming distance of the best candidate (65535: no candidate) */
 } jslam_matches;
 
+/* Correlation minimisation (Sec. III, middle-end stereo matching; the
+ * paper names the step and gives no detail, so this is the sub-pixel
+ * refinement of the stereo SLAM system it builds on, restated).  For every
+ * left keypoint of every pair of the last jslam_match with an accepted
+ * match j, on the left keypoint's level n (s = zeta^n) of both raw pyramids:
+ * xr0 = floor(X_j / s + 0.5); SAD(t) = sum over the (2w+1)^2 window of
+ * |(left - its centre) - (right shifted by t - its centre)| for t = -L..L;
+ * t* = the first minimum; rejected when a window leaves the level, t* is
+ * -L or L, the minimum is flat, the parabola offset delta = (d1 - d3) /
+ * (2 (d1 + d3 - 2 d2)) exceeds 1 in size, or the disparity s (x - xr0 - t*
+ * - delta) leaves [0, max_disp]; depth = bf / max(disparity, 0.01) when bf
+ * > 0.  Then matches whose SAD is above 2.1 times the pair's median SAD
+ * (of the surviving matches) are rejected.  Enqueued on the context stream
+ * after jslam_match; results in jslam_get_refined / the result block.
+ * JSLAM_ERR_ARG unless 1 <= half_window <= 10, 1 <= search <= 7, bf >= 0;
+ * JSLAM_ERR_STATE before jslam_match. */
+jslam_status jslam_refine_matches(jslam_ctx *ctx, int32_t half_window, int32_t search, float bf);
+
+/* Views of one pair's refinement, one entry per left keypoint. */
+typedef struct {
+    int32_t count;                /* == left keypoint count; -1 until jslam_sync() */
+    const float *disparity;       /* sub-pixel disparity in s0 pixels, -1 when rejected or unmatched */
+    const float *depth;           /* bf / disparity, 0 when rejected (or bf == 0) */
+    const uint32_t *sad;          /* SAD at the best shift; 0xFFFFFFFF when none was computed */
+} jslam_refined;
+
+/* Device views of pair `pair`'s refinement (after jslam_refine_matches). */
+jslam_status jslam_get_refined(jslam_ctx *ctx, int32_t pair, jslam_refined *out);
+
+/* Host views of the refinement inside a downloaded result block of pair `pair`. */
+jslam_status jslam_result_refined_view(jslam_ctx *ctx, int32_t pair, const void *block, jslam_refined *out);
+
 /* Device views of one pyramid level of one image (for consumers that share
  * the frontend's images, as the paper's middle-end does). */
 typedef struct {
@@ -219,7 +251,8 @@ enum {
     JSLAM_STAGE_PFA_FINAL = 4,    /* PFA aggregation, cap, canonical compaction */
     JSLAM_STAGE_ORB = 5,          /* orientation + descriptors */
     JSLAM_STAGE_MATCH = 6,        /* stereo row matching */
-    JSLAM_NUM_STAGES = 7
+    JSLAM_STAGE_REFINE = 7,       /* correlation minimisation (jslam_refine_matches) */
+    JSLAM_NUM_STAGES = 8
 };
 
 /* Turn per-stage timing on or off.  When on, every extraction and match

@@ -137,7 +137,7 @@ SideLayout side_layout(int C, size_t base)
 struct PairLayout {
     int capacity;
     SideLayout side[2];
-    size_t match_idx, disparity, dist, bytes;
+    size_t match_idx, disparity, dist, sub_disp, depth, corr, bytes;
 };
 
 PairLayout pair_layout(int max_feats)
@@ -150,6 +150,9 @@ PairLayout pair_layout(int max_feats)
     p.match_idx = o; o = align_up(o + (size_t)p.capacity * 4, 256);
     p.disparity = o; o = align_up(o + (size_t)p.capacity * 2, 256);
     p.dist = o; o = align_up(o + (size_t)p.capacity * 2, 256);
+    p.sub_disp = o; o = align_up(o + (size_t)p.capacity * 4, 256);
+    p.depth = o; o = align_up(o + (size_t)p.capacity * 4, 256);
+    p.corr = o; o = align_up(o + (size_t)p.capacity * 4, 256);
     p.bytes = o;
     return p;
 }
@@ -173,7 +176,7 @@ struct jslam_ctx {
     GrowBuf plan, levels, maps, scratch, results, staging, counts;
     int32_t *h_counts = nullptr;  // pinned mirror: 2 * max_pairs counts + error word
     bool synced = false;
-    bool have_extract = false, have_match = false;
+    bool have_extract = false, have_match = false, have_refine = false;
 
     // current plan
     std::vector<JobKey> keys;
@@ -442,6 +445,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 detect_box(std::min(L.bx * L.c, L.W), std::min(L.by * L.c, L.H), &L.box_w, &L.box_h);
                 L.image = img; L.level = l;
                 L.band = match_band(l, jobs[p].scale, cfg.row_band_px);
+                L.zeta = zeta_pow(jobs[p].scale, l);
                 const size_t pitch = align_up((size_t)L.W, 128);
                 // raw and blurred level, each padded so that whole-word and
                 // halo reads past the last row stay inside the buffer
@@ -503,6 +507,9 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
         P.match_idx = reinterpret_cast<int32_t *>(rblock + pl.match_idx);
         P.disparity = reinterpret_cast<int16_t *>(rblock + pl.disparity);
         P.dist = reinterpret_cast<uint16_t *>(rblock + pl.dist);
+        P.sub_disp = reinterpret_cast<float *>(rblock + pl.sub_disp);
+        P.depth = reinterpret_cast<float *>(rblock + pl.depth);
+        P.corr = reinterpret_cast<uint32_t *>(rblock + pl.corr);
     }
     pyr_base[n_levels] = pyr;
     fast_base[n_levels] = fast;
@@ -757,6 +764,7 @@ jslam_status jslam_extract_batch(jslam_ctx *ctx, const jslam_stereo_job *jobs, i
     }
     ctx->have_extract = true;
     ctx->have_match = false;
+    ctx->have_refine = false;
     ctx->synced = false;
     return enqueue_counts(ctx);
 }
@@ -784,7 +792,35 @@ jslam_status jslam_match(jslam_ctx *ctx)
         ctx->stage_done[JSLAM_STAGE_MATCH] = true;
     }
     ctx->have_match = true;
+    ctx->have_refine = false;
     return JSLAM_OK;
+}
+
+jslam_status jslam_refine_matches(jslam_ctx *ctx, int32_t half_window, int32_t search, float bf)
+{
+    if (!ctx) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (half_window < 1 || half_window > kRefineMaxW || search < 1 || search > kRefineMaxL || !(bf >= 0.0f))
+        return JSLAM_ERR_ARG;
+    if (!ctx->have_match) return JSLAM_ERR_STATE;
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    cudaError_t e = launch_refine(ctx->batch, half_window, search, (double)bf, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, e);
+    if (ctx->timing && ctx->stage_done[JSLAM_STAGE_MATCH]) {
+        if ((e = cudaEventRecord(ctx->events[JSLAM_STAGE_REFINE + 1], ctx->stream)) != cudaSuccess) return fail(ctx, e);
+        ctx->stage_done[JSLAM_STAGE_REFINE] = true;
+    }
+    ctx->have_refine = true;
+    return JSLAM_OK;
+}
+
+static void refined_views(const PairLayout &pl, const char *b, int32_t count, jslam_refined *out)
+{
+    out->count = count;
+    out->disparity = reinterpret_cast<const float *>(b + pl.sub_disp);
+    out->depth = reinterpret_cast<const float *>(b + pl.depth);
+    out->sad = reinterpret_cast<const uint32_t *>(b + pl.corr);
 }
 
 jslam_status jslam_sync(jslam_ctx *ctx)
@@ -830,6 +866,24 @@ jslam_status jslam_get_matches(jslam_ctx *ctx, int32_t pair, jslam_matches *out)
     out->right_idx = reinterpret_cast<const int32_t *>(rb + pl.match_idx);
     out->disparity = reinterpret_cast<const int16_t *>(rb + pl.disparity);
     out->dist = reinterpret_cast<const uint16_t *>(rb + pl.dist);
+    return JSLAM_OK;
+}
+
+jslam_status jslam_get_refined(jslam_ctx *ctx, int32_t pair, jslam_refined *out)
+{
+    if (!ctx || !out) return JSLAM_ERR_ARG;
+    if (!ctx->have_refine) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size()) return JSLAM_ERR_ARG;
+    refined_views(ctx->layouts[pair], ctx->results.as<char>(ctx->result_off[pair]), synced_count(ctx, 2 * pair), out);
+    return JSLAM_OK;
+}
+
+jslam_status jslam_result_refined_view(jslam_ctx *ctx, int32_t pair, const void *block, jslam_refined *out)
+{
+    if (!ctx || !block || !out) return JSLAM_ERR_ARG;
+    if (!ctx->have_refine) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size()) return JSLAM_ERR_ARG;
+    refined_views(ctx->layouts[pair], static_cast<const char *>(block), synced_count(ctx, 2 * pair), out);
     return JSLAM_OK;
 }
 
@@ -1084,8 +1138,11 @@ jslam_status jslam_graph_launch(jslam_ctx *ctx)
     if (e != cudaSuccess) return fail(ctx, e);
     ctx->have_extract = true;
     ctx->have_match = true;
+    ctx->have_refine = false;
     ctx->synced = false;
-    for (int i = 0; i < JSLAM_NUM_STAGES; ++i) ctx->stage_done[i] = ctx->graph_timed && ctx->timing;
+    // the graph holds extraction and matching (refinement is enqueued separately)
+    for (int i = 0; i < JSLAM_NUM_STAGES; ++i)
+        ctx->stage_done[i] = i <= JSLAM_STAGE_MATCH && ctx->graph_timed && ctx->timing;
     return JSLAM_OK;
 }
 

@@ -32,6 +32,7 @@ constexpr int kFastMaxCellsPerCta = 2048;  // cells x k per CTA
 constexpr int kLutWords = 2048;            // 2^16-entry corner bit table
 constexpr int kSkipC = 16;                 // channels of the learned cell-skip net
 constexpr int kSkipTileW = 26, kSkipTileH = 12;  // its logits per CTA (grid pitch 26 + 6 = 32)
+constexpr int kRefineMaxW = 10, kRefineMaxL = 7;  // correlation window half-size and search radius limits
 constexpr int kNmsThreads = 128;
 constexpr int kFinThreads = 1024;
 
@@ -68,6 +69,7 @@ struct LevelDesc {
     int32_t seg_base;        // first segment (cell row) of the level
     int32_t image, level;
     int32_t band;            // stereo row band for keypoints of this level
+    double zeta;             // zeta^n (repeated multiplication in double)
 };
 
 struct ImageDesc {
@@ -99,6 +101,9 @@ struct PairDesc {
     int32_t *match_idx;
     int16_t *disparity;
     uint16_t *dist;
+    float *sub_disp;         // correlation minimisation: sub-pixel disparity (-1 rejected)
+    float *depth;            //   depth bf / disparity (0 rejected)
+    uint32_t *corr;          //   SAD at the best shift (0xFFFFFFFF: none computed)
 };
 
 // Parameters fixed for a context.
@@ -152,6 +157,7 @@ cudaError_t launch_pfa_nms(const Batch &b, cudaStream_t stream);
 cudaError_t launch_pfa_finalize(const Batch &b, cudaStream_t stream);
 cudaError_t launch_orient_desc(const Batch &b, cudaStream_t stream);
 cudaError_t launch_match(const Batch &b, cudaStream_t stream);
+cudaError_t launch_refine(const Batch &b, int w, int L, double bf, cudaStream_t stream);
 cudaError_t launch_skipnet(const Batch &b, const SkipModelDev &m, float thresh, cudaStream_t stream);
 cudaError_t set_blur_weights(const int32_t w[7]);
 cudaError_t configure_kernels();

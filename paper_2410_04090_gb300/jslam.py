@@ -71,6 +71,13 @@ class Matches(C.Structure):
                 ("dist", C.c_void_p)]
 
 
+class Refined(C.Structure):
+    _fields_ = [("count", C.c_int32), ("disparity", C.c_void_p), ("depth", C.c_void_p), ("sad", C.c_void_p)]
+
+
+REFINED_FIELDS = (("disparity", np.float32), ("depth", np.float32), ("sad", np.uint32))
+
+
 class LevelView(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("raw_pitch", C.c_int32),
                 ("blurred_pitch", C.c_int32), ("raw", C.c_void_p), ("blurred", C.c_void_p)]
@@ -90,8 +97,9 @@ SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extra
            "jslam_level_geometry", "jslam_project", "jslam_match_band", "jslam_enable_stage_timing",
            "jslam_stage_times", "jslam_pfa_scores_static", "jslam_corner_table", "jslam_set_tuning",
            "jslam_autotune", "jslam_graph_capture", "jslam_graph_launch", "jslam_set_skip_model",
-           "jslam_get_skip_view", "jslam_result_range", "jslam_download_range")
-STAGES = ("pyramid", "skip", "detect", "pfa_nms", "pfa_final", "orb", "match")
+           "jslam_get_skip_view", "jslam_result_range", "jslam_download_range", "jslam_refine_matches",
+           "jslam_get_refined", "jslam_result_refined_view")
+STAGES = ("pyramid", "skip", "detect", "pfa_nms", "pfa_final", "orb", "match", "refine")
 
 _lib = None
 
@@ -122,6 +130,12 @@ def lib():
         L.jslam_get_matches.restype = st
         L.jslam_get_level.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.POINTER(LevelView)]
         L.jslam_get_level.restype = st
+        L.jslam_refine_matches.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_float]
+        L.jslam_refine_matches.restype = st
+        L.jslam_get_refined.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Refined)]
+        L.jslam_get_refined.restype = st
+        L.jslam_result_refined_view.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(Refined)]
+        L.jslam_result_refined_view.restype = st
         L.jslam_result_bytes.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_size_t)]
         L.jslam_result_bytes.restype = st
         L.jslam_download.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t]
@@ -347,6 +361,32 @@ class Frontend:
 
     def match(self):
         _check(lib().jslam_match(self._h), "jslam_match")
+
+    def refine_matches(self, half_window: int = 5, search: int = 5, bf: float = 0.0):
+        """Enqueue the correlation minimisation of the last match (sub-pixel
+        disparity and depth of every accepted match)."""
+        _check(lib().jslam_refine_matches(self._h, half_window, search, bf), "jslam_refine_matches")
+
+    def refined(self, pair: int = 0) -> dict:
+        r = Refined()
+        _check(lib().jslam_get_refined(self._h, pair, C.byref(r)), "jslam_get_refined")
+        n = max(r.count, 0)
+        out = {"count": r.count}
+        for name, dt in REFINED_FIELDS:
+            out[name] = _device_view(getattr(r, name), (n,), dt, self.device)
+        return out
+
+    def result_refined_view(self, pair: int, block) -> dict:
+        """Host arrays (copies) of the refinement inside a downloaded result block."""
+        base = block.ctypes.data if isinstance(block, np.ndarray) else block.data_ptr()
+        r = Refined()
+        _check(lib().jslam_result_refined_view(self._h, pair, base, C.byref(r)), "jslam_result_refined_view")
+        n = max(r.count, 0)
+        out = {"count": r.count}
+        for name, dt in REFINED_FIELDS:
+            buf = (C.c_char * (n * np.dtype(dt).itemsize)).from_address(getattr(r, name)) if n else b""
+            out[name] = np.frombuffer(buf, dtype=dt).copy() if n else np.zeros(0, dt)
+        return out
 
     def set_skip_model(self, blob, thresh: float = 0.0):
         """Enable the learned cell-skip proposal (blob: bytes of a model) or

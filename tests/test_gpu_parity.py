@@ -304,7 +304,14 @@ def test_stage_timing(J, oracle):
     fe.match()
     fe.sync()
     t = fe.stage_times()
-    assert set(t) == set(J.STAGES) and all(v > 0 for v in t.values()), t
+    assert set(t) == set(J.STAGES) and t["refine"] == 0.0, t      # refinement not run
+    assert all(v > 0 for k, v in t.items() if k != "refine"), t
+    fe.extract(l, r, p.levels, p.scale, p.fast_thresh, p.cell, p.max_feats)
+    fe.match()
+    fe.refine_matches(5, 5, 0.0)
+    fe.sync()
+    t = fe.stage_times()
+    assert all(v > 0 for v in t.values()), t
     fe.enable_stage_timing(False)
     fe.close()
 
