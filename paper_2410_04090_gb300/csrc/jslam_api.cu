@@ -446,6 +446,8 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 L.image = img; L.level = l;
                 L.band = match_band(l, jobs[p].scale, cfg.row_band_px);
                 L.zeta = zeta_pow(jobs[p].scale, l);
+                L.zeta_f = static_cast<float>(L.zeta);
+                L.zeta_inv_f = static_cast<float>(1.0 / L.zeta);
                 const size_t pitch = align_up((size_t)L.W, 128);
                 // raw and blurred level, each padded so that whole-word and
                 // halo reads past the last row stay inside the buffer

@@ -70,6 +70,7 @@ struct LevelDesc {
     int32_t image, level;
     int32_t band;            // stereo row band for keypoints of this level
     double zeta;             // zeta^n (repeated multiplication in double)
+    float zeta_f, zeta_inv_f; // zeta^n and 1 / zeta^n rounded to float
 };
 
 struct ImageDesc {

@@ -9,9 +9,9 @@
 //                  absolute differences of one shift over half of the rows,
 //                  a shuffle adds the halves, a warp minimum picks the first
 //                  minimum shift, and lane 0 takes the decisions in integers
-//                  and computes delta, disparity and depth with explicitly
-//                  rounded IEEE double operations (the same values the
-//                  host-side definition gives).
+//                  and computes delta, disparity and depth in float (the
+//                  host-side definition's doubles to a few float ulps; the
+//                  FP64 pipe is a small fraction of the FP32 rate here).
 // k_refine_median  one CTA per pair: the median SAD of the surviving matches
 //                  by a three-pass 8-bit radix select, then the matches above
 //                  2.1 times it are rejected.
@@ -23,8 +23,12 @@ constexpr int kRefW = kRefineMaxW, kRefL = kRefineMaxL;
 constexpr int kRefLeft = (2 * kRefW + 1) * (2 * kRefW + 1);
 constexpr int kRefRight = (2 * kRefW + 1) * (2 * kRefW + 2 * kRefL + 1);
 
-__global__ void __launch_bounds__(256) k_refine(Batch b, int w, int L, double bf)
+// WC > 0: the window half-size fixed at compile time (the default 5), so the
+// SAD loops unroll; WC == 0: any half-size given at run time.
+template <int WC>
+__global__ void __launch_bounds__(256) k_refine(Batch b, int w_rt, int L, double bf)
 {
+    const int w = WC > 0 ? WC : w_rt;
     __shared__ uint8_t s_left[8][kRefLeft];
     __shared__ uint8_t s_right[8][kRefRight];
     const int pair = blockIdx.y;
@@ -42,18 +46,23 @@ __global__ void __launch_bounds__(256) k_refine(Batch b, int w, int L, double bf
         const LevelDesc &A = b.levels[Il.level_base + n];
         const LevelDesc &B = b.levels[Ir.level_base + n];
         const double s = A.zeta;
-        const int xr0 = (int)floor(__dadd_rn(__ddiv_rn((double)Ir.out.X[j], s), 0.5));
+        // xr0 = floor(X / s + 0.5): in float, |X / s - q| < 2^-10 for X < 2^13,
+        // so a q more than 2^-8 away from a half-integer rounds as the double
+        // does; closer ones (rare) take the double computation
+        const int X = Ir.out.X[j];
+        const float q = __fmul_rn((float)X, A.zeta_inv_f);
+        const float fr = q - floorf(q);
+        int xr0 = (int)floorf(q + 0.5f);
+        if (fabsf(fr - 0.5f) < 0x1p-8f) xr0 = (int)floor(__dadd_rn(__ddiv_rn((double)X, s), 0.5));
         const int W = A.W, H = A.H;
         if (xi - w >= 0 && xi + w < W && yi - w >= 0 && yi + w < H && xr0 - L - w >= 0 && xr0 + L + w < W) {
             const int pw = 2 * w + 1, rw = 2 * (w + L) + 1;
             uint8_t *lp = s_left[wi], *rp = s_right[wi];
-            for (int e = lane; e < pw * pw; e += 32) {
-                const int r = e / pw, c = e - r * pw;
-                lp[e] = A.raw[(size_t)(yi - w + r) * A.pitch + (xi - w + c)];
-            }
-            for (int e = lane; e < pw * rw; e += 32) {
-                const int r = e / rw, c = e - r * rw;
-                rp[e] = B.raw[(size_t)(yi - w + r) * B.pitch + (xr0 - L - w + c)];
+            const uint8_t *la0 = A.raw + (size_t)(yi - w) * A.pitch + (xi - w);
+            const uint8_t *rb0 = B.raw + (size_t)(yi - w) * B.pitch + (xr0 - L - w);
+            for (int r = 0; r < pw; ++r) {
+                if (lane < pw) lp[r * pw + lane] = la0[(size_t)r * A.pitch + lane];
+                for (int c = lane; c < rw; c += 32) rp[r * rw + c] = rb0[(size_t)r * B.pitch + c];
             }
             __syncwarp();
             const int nsh = 2 * L + 1;
@@ -62,9 +71,22 @@ __global__ void __launch_bounds__(256) k_refine(Batch b, int w, int L, double bf
                 const int k = lane % nsh, half = lane / nsh;  // shift t = k - L
                 const int lc = lp[w * pw + w], rc = rp[w * rw + k + w];
                 const int r0 = half == 0 ? 0 : w, r1 = half == 0 ? w : pw;  // rows [0, w) and [w, 2w + 1)
-                for (int r = r0; r < r1; ++r) {
-                    const uint8_t *la = lp + r * pw, *ra = rp + r * rw + k;
-                    for (int c = 0; c < pw; ++c) part += abs(((int)la[c] - lc) - ((int)ra[c] - rc));
+                const int cc = lc - rc;  // |(l - lc) - (r - rc)| = |(l - r) - cc|
+                if (WC > 0) {
+#pragma unroll
+                    for (int rr = 0; rr < WC + 1; ++rr) {
+                        const int r = r0 + rr;
+                        if (r < r1) {
+                            const uint8_t *la = lp + r * (2 * WC + 1), *ra = rp + r * rw + k;
+#pragma unroll
+                            for (int c = 0; c < 2 * WC + 1; ++c) part += abs((int)la[c] - (int)ra[c] - cc);
+                        }
+                    }
+                } else {
+                    for (int r = r0; r < r1; ++r) {
+                        const uint8_t *la = lp + r * pw, *ra = rp + r * rw + k;
+                        for (int c = 0; c < pw; ++c) part += abs((int)la[c] - (int)ra[c] - cc);
+                    }
                 }
             }
             const int other = __shfl_down_sync(0xFFFFFFFFu, part, nsh);
@@ -83,14 +105,23 @@ __global__ void __launch_bounds__(256) k_refine(Batch b, int w, int L, double bf
             const int ts = kb - L;
             if (ts != -L && ts != L) {
                 const long long num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);
-                const long long q = (long long)xi - xr0 - ts;
                 // disparity >= 0 <=> q den >= num; <= max_disp <=> s (q den - num) <= max_disp den
-                if (den != 0 && (num < 0 ? -num : num) <= den && q * den >= num &&
-                    !(__dmul_rn(s, (double)(q * den - num)) > (double)b.prm.max_disp * (double)den)) {
-                    const double delta = __ddiv_rn((double)num, (double)den);
-                    const double disp = __dmul_rn(s, __dsub_rn((double)q, delta));
-                    disp_out = __double2float_rn(disp);
-                    depth_out = bf > 0.0 ? __double2float_rn(__ddiv_rn(bf, disp > 0.01 ? disp : 0.01)) : 0.0f;
+                const long long qi = (long long)xi - xr0 - ts;
+                bool ok = den != 0 && (num < 0 ? -num : num) <= den && qi * den >= num;
+                if (ok) {
+                    // s (q den - num) <= max_disp den, in float unless within a
+                    // relative 2^-18 of equality (float error < 2^-21 relative)
+                    const float lhs = __fmul_rn(A.zeta_f, (float)(qi * den - num));
+                    const float rhs = __fmul_rn((float)b.prm.max_disp, (float)den);
+                    if (lhs > rhs * (1.0f + 0x1p-18f)) ok = false;
+                    else if (!(lhs < rhs * (1.0f - 0x1p-18f)))
+                        ok = !(__dmul_rn(s, (double)(qi * den - num)) > (double)b.prm.max_disp * (double)den);
+                }
+                if (ok) {
+                    const float delta = __fdiv_rn((float)num, (float)den);
+                    const float disp = __fmul_rn(A.zeta_f, __fsub_rn((float)qi, delta));
+                    disp_out = disp;
+                    depth_out = bf > 0.0 ? __fdiv_rn((float)bf, fmaxf(disp, 0.01f)) : 0.0f;
                 }
             }
         }
@@ -153,7 +184,8 @@ cudaError_t launch_refine(const Batch &b, int w, int L, double bf, cudaStream_t 
 {
     if (b.n_pairs == 0 || b.max_capacity == 0) return cudaSuccess;
     dim3 grid((b.max_capacity + 7) / 8, b.n_pairs);
-    k_refine<<<grid, 256, 0, stream>>>(b, w, L, bf);
+    if (w == 5) k_refine<5><<<grid, 256, 0, stream>>>(b, w, L, bf);
+    else k_refine<0><<<grid, 256, 0, stream>>>(b, w, L, bf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_refine_median<<<b.n_pairs, 256, 0, stream>>>(b);

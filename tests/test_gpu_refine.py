@@ -1,5 +1,7 @@
 """Correlation minimisation (sub-pixel stereo refinement) on the GPU against
-the oracle: disparity, depth and SAD bit-exact per left keypoint."""
+the oracle: per left keypoint the SAD and every accept/reject decision are
+exact; disparity and depth, computed in float on the GPU from the same
+integers the oracle turns into doubles, agree within float rounding."""
 import numpy as np
 import pytest
 
@@ -24,15 +26,25 @@ def J():
 
 
 def _compare(got, want, what):
+    """Tolerance from the float path: delta = num / den, one subtraction and
+    one multiply by zeta^n (<= 3.6 at level 7), each rounded once: the
+    disparity is within 2e-6 max(1, d) of the double value, the depth within
+    the same relative error scaled by 1 / max(d, 0.01) plus one division."""
     n = len(want["disparity"])
     assert got["count"] == n, what
-    for f in ("sad", "disparity", "depth"):
-        g = np.asarray(got[f])[:n]
-        w = np.asarray(want[f])
-        if not np.array_equal(g, w):
-            bad = np.nonzero(g != w)[0]
-            raise AssertionError(f"{what}: {f} differs at {len(bad)} of {n}; first {bad[0]}: gpu {g[bad[0]]} "
-                                 f"oracle {w[bad[0]]}")
+    g_sad, w_sad = np.asarray(got["sad"])[:n], np.asarray(want["sad"])
+    assert np.array_equal(g_sad, w_sad), f"{what}: SAD differs at {np.nonzero(g_sad != w_sad)[0][:5]}"
+    gd = np.asarray(got["disparity"])[:n].astype(np.float64)
+    wd = np.asarray(want["disparity"]).astype(np.float64)
+    keep = wd >= 0
+    assert np.array_equal(gd >= 0, keep), f"{what}: accept/reject differs at {np.nonzero((gd >= 0) != keep)[0][:5]}"
+    assert (gd[~keep] == -1).all()
+    tol_d = 2e-6 * np.maximum(1.0, wd)
+    assert (np.abs(gd - wd)[keep] <= tol_d[keep]).all(), f"{what}: disparity {np.abs(gd - wd)[keep].max()}"
+    gz = np.asarray(got["depth"])[:n].astype(np.float64)
+    wz = np.asarray(want["depth"]).astype(np.float64)
+    tol_z = wz * (tol_d / np.maximum(wd, 0.01) + 1e-6)
+    assert (np.abs(gz - wz) <= tol_z).all() and (gz[~keep] == 0).all(), f"{what}: depth"
 
 
 def _pair(J, oracle, left, right, p, w=5, L=5, bf=BF):
