@@ -548,24 +548,30 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
             }
         }
         // cell state: 0 no corner yet, 1 primary-threshold corner, 2 skipped by
-        // the learned proposal (its centre projects into a skipped s0 cell)
+        // the learned proposal (its centre projects into a skipped s0 cell),
+        // 3 no pixel inside the evaluation border (never holds a corner, so it
+        // neither calls for the fallback pass nor joins it)
         int my_skipped = 0;
         for (int i = threadIdx.x; i < cells; i += kFastThreads) {
-            uint8_t st = 0;
-            if (I.skip) {
-                const int lcy = i / ncx, lcx = i - lcy * ncx;
-                const int px = min((G.ccx0 + lcx) * c + c / 2, W - 1), py = min((G.ccy0 + lcy) * c + c / 2, Hh - 1);
+            const int lcy = i / ncx, lcx = i - lcy * ncx;
+            const int cx0 = (G.ccx0 + lcx) * c, cy0 = (G.ccy0 + lcy) * c;
+            const bool evaluated = cx0 + c > border && cx0 < W - border && cy0 + c > border && cy0 < Hh - border;
+            uint8_t st = evaluated ? 0 : 3;
+            if (I.skip && evaluated) {
+                const int px = min(cx0 + c / 2, W - 1), py = min(cy0 + c / 2, Hh - 1);
                 const int X = __ldg(L.projx + px), Y = __ldg(L.projy + py);
                 st = I.skip[(Y / I.skip_c0) * I.skip_cells_x + X / I.skip_c0] ? 2 : 0;
-                my_skipped += st == 2;
             }
+            if (I.skip && st != 0) { st = 2; ++my_skipped; }  // skip mode: never-cells count as skipped
             has_hi[i] = st;
         }
         for (int i = threadIdx.x; i < cells * k; i += kFastThreads) sel[i] = 0;
         if (threadIdx.x == 0) { n_corner = 0; need_lo = 0; n_skipped = 0; n_cand[0] = n_cand[1] = 0; }
         __syncthreads();
-        if (my_skipped) atomicAdd(&n_skipped, my_skipped);
-        __syncthreads();
+        if (I.skip) {  // uniform: the skipped-cell count only matters in skip mode
+            if (my_skipped) atomicAdd(&n_skipped, my_skipped);
+            __syncthreads();
+        }
         const bool all_skipped = n_skipped == cells;
         const bool some_skipped = n_skipped > 0;  // tiles without skipped cells run as in exact mode
 
