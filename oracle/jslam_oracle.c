@@ -825,3 +825,46 @@ void or_subpixel(const uint8_t *left0, const uint8_t *right0, int32_t W0, int32_
     free(kept);
     for (int32_t n = 0; n < p->levels; ++n) { free(lv[n]); free(rv[n]); }
 }
+
+/* ------------------------------------------------------------------ */
+/* Feature tracking by projection (Sec. III, middle-end: feature matching and
+ * tracking, with the conic projections of map points; the text gives no
+ * detail).  Reading: the caller projects its map points (or the previous
+ * frame's keypoints) into the current frame with its own pose or motion
+ * model and passes, per query q, the predicted s0 position (u_q, v_q), the
+ * predicted level n_q and the 256-bit descriptor.  Candidates are the
+ * frame's keypoints k with level in [n_q - 1, n_q + 1] inside the square
+ * window |X_k - u_q| <= r_q, |Y_k - v_q| <= r_q, r_q = radius * zeta^n_q.
+ * The window test is a floating-point decision, taken in IEEE float like the
+ * GPU kernel: r_q = fl(radius * fl(zeta^n_q)), |fl(X_k - u_q)| <= r_q.  The
+ * best candidate minimises (Hamming distance, index); it is accepted when
+ * its distance is at most max_dist and, if another candidate exists, 10 best
+ * <= 9 second (ratio 0.9 against the second-smallest distance, in integers).
+ * Outputs: idx (-1 none or rejected) and dist (best distance, 0xFFFF when
+ * there is no candidate).                                                   */
+void or_track(const or_keypoints *Kf, float scale, const float *u, const float *v, const uint8_t *lvl,
+              const uint32_t *desc, int32_t n, float radius, int32_t max_dist,
+              int32_t *idx_out, uint16_t *dist_out)
+{
+    for (int32_t q = 0; q < n; ++q) {
+        float zf = (float)or_level_scale(scale, lvl[q]);
+        volatile float r = radius * zf;  /* one float rounding, no contraction */
+        int32_t best = -1, bd = 0x7fffffff, sd = 0x7fffffff;
+        for (int32_t k = 0; k < Kf->count; ++k) {
+            int32_t m = Kf->level[k];
+            if (m < (int32_t)lvl[q] - 1 || m > (int32_t)lvl[q] + 1) continue;
+            volatile float dx = (float)Kf->X[k] - u[q];
+            volatile float dy = (float)Kf->Y[k] - v[q];
+            if (fabsf(dx) > r || fabsf(dy) > r) continue;
+            int32_t d = 0;
+            for (int32_t w = 0; w < 8; ++w)
+                d += popcount32(desc[(size_t)q * 8 + w] ^ Kf->desc[(size_t)k * 8 + w]);
+            if (d < bd) { sd = bd; bd = d; best = k; }
+            else if (d < sd) { sd = d; }
+        }
+        if (best < 0) { idx_out[q] = -1; dist_out[q] = 0xFFFF; continue; }
+        dist_out[q] = (uint16_t)bd;
+        int ok = bd <= max_dist && (sd == 0x7fffffff || 10 * bd <= 9 * sd);
+        idx_out[q] = ok ? best : -1;
+    }
+}

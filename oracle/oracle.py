@@ -136,6 +136,8 @@ def lib():
         L.or_match.argtypes = [C.POINTER(_Keypoints), C.POINTER(_Keypoints), C.POINTER(Params),
                                i32p, i16p, u16p]
         f32p = np.ctypeslib.ndpointer(np.float32, flags="C")
+        L.or_track.argtypes = [C.POINTER(_Keypoints), C.c_float, f32p, f32p, u8p, u32p, i32, C.c_float, i32,
+                               i32p, u16p]
         L.or_subpixel.argtypes = [u8p, u8p, i32, i32, i32, C.POINTER(_Keypoints), C.POINTER(_Keypoints), i32p,
                                   C.POINTER(Params), i32, i32, C.c_double, f32p, f32p, u32p]
         _lib = L
@@ -372,6 +374,23 @@ def subpixel(left: np.ndarray, right: np.ndarray, kl: dict, kr: dict, right_idx:
                       float(bf), disp, depth, sad)
     del keep_l, keep_r
     return {"disparity": disp[:n].copy(), "depth": depth[:n].copy(), "sad": sad[:n].copy()}
+
+
+def track(kf: dict, scale: float, u, v, level, desc, radius: float, max_dist: int = 100):
+    """Feature tracking by projection (Sec. III middle-end): per query the
+    index of the matched keypoint of `kf` (-1 none/rejected) and the best
+    Hamming distance (0xFFFF: no candidate)."""
+    sk, keep = _as_struct(kf)
+    n = len(u)
+    u = np.ascontiguousarray(np.concatenate([np.asarray(u, np.float32), [0]]), np.float32)
+    v = np.ascontiguousarray(np.concatenate([np.asarray(v, np.float32), [0]]), np.float32)
+    lv = np.ascontiguousarray(np.concatenate([np.asarray(level, np.uint8), [0]]), np.uint8)
+    ds = np.ascontiguousarray(np.concatenate([np.asarray(desc, np.uint32).reshape(-1), np.zeros(8, np.uint32)]),
+                              np.uint32)
+    idx = np.zeros(n + 1, np.int32); dist = np.zeros(n + 1, np.uint16)
+    lib().or_track(C.byref(sk), scale, u, v, lv, ds, n, radius, max_dist, idx, dist)
+    del keep
+    return idx[:n].copy(), dist[:n].copy()
 
 
 def extract_pair(left: np.ndarray, right: np.ndarray, p: FrontendParams):
