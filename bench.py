@@ -576,12 +576,42 @@ def main():
                   "unit": UNIT, "mode": "batched + jslam_refine_matches(half_window 5, search 5)",
                   "refined_fraction_of_matches": kept / max(matched, 1)}
 
+    # feature tracking by projection (middle-end): frame k's left keypoints,
+    # predicted at their own s0 positions, tracked into frame k + 1's left image
+    track = None
+    if not args.only_batched and n >= 2:
+        fe.extract_batch(jobs); fe.sync()
+        qs = []
+        import numpy as np
+        for k in range(n - 1):
+            kp = jslam.to_numpy(fe.keypoints(k, 0))
+            c = kp["count"]
+            up = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a[:c], dt)).to(dev)
+            qs.append((up(kp["X"], np.float32), up(kp["Y"], np.float32), up(kp["level"], np.uint8),
+                       up(np.asarray(kp["desc"], np.uint32).view(np.int32), np.int32)))
+        n_q = sum(int(q[0].numel()) for q in qs)
+        hits = []
+
+        def step_track():
+            hits.clear()
+            for k, (u, v, lv, dsc) in enumerate(qs):
+                hits.append(fe.track(k + 1, 0, u, v, lv, dsc, 8.0, 100)[0])
+
+        for _ in range(2):
+            step_track()
+        track_ms = timed(step_track, min(args.steps, 10))
+        fe.sync()
+        tracked = sum(int((h >= 0).sum()) for h in hits)
+        track = {"queries_per_step": n_q, "calls_per_step": n - 1, "ms_per_step": track_ms / min(args.steps, 10),
+                 "queries_per_s": n_q / (track_ms / min(args.steps, 10) / 1e3), "tracked_fraction": tracked / max(n_q, 1),
+                 "mode": "jslam_track(radius 8, max_dist 100), previous frame's left keypoints into the next frame"}
+
     e2e = None
     if not args.only_batched:
         e2e = run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, stream)
     if rank == 0:
         emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks,
-             tuning, skip_quality, dev.index, refine)
+             tuning, skip_quality, dev.index, refine, track)
     fe.close()
     for extra in [graph_fe, skip_fe] + extra_fes:
         if extra:
@@ -657,7 +687,7 @@ def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, 
 
 
 def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks, tuning,
-         skip_quality, dev_index, refine=None):
+         skip_quality, dev_index, refine=None, track=None):
     import numpy as np
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
@@ -694,7 +724,7 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
             "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
                        "pairs_per_step": n, "mode": args.mode, "detect_tile_px": list(tuning),
                        "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
-            "modes": mode_values, "learned_skip": skip_quality, "refine": refine,
+            "modes": mode_values, "learned_skip": skip_quality, "refine": refine, "track": track,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks.summary(), "gpu_launches": launches[args.mode] * args.steps,
             "keypoints_per_image_mean": float(np.mean(counts))}

@@ -145,6 +145,27 @@ typedef struct {
  * JSLAM_ERR_STATE before jslam_match. */
 jslam_status jslam_refine_matches(jslam_ctx *ctx, int32_t half_window, int32_t search, float bf);
 
+/* Feature tracking by projection (Sec. III, middle-end feature tracking;
+ * the paper gives no detail, so this is a restatement of the usual search
+ * by projection).  The caller projects its map points (or the previous
+ * frame's keypoints) into the frame with its own pose or motion model; for
+ * each of the n queries (device arrays: predicted s0 position u, v, predicted
+ * level, 8-word descriptor) the kernel searches the keypoints of `side` of
+ * pair `pair` of the last extraction at levels level-1..level+1 inside the
+ * square window |X - u| <= r, |Y - v| <= r with r = radius * zeta^level
+ * (window test in IEEE float), and keeps the smallest (Hamming distance,
+ * index).  It is accepted when its distance is <= max_dist and, when
+ * another candidate exists, 10 best <= 9 second (ratio 0.9 against the
+ * second-smallest distance).  Writes out_idx (canonical keypoint index, -1
+ * none or rejected) and out_dist (best distance, 0xFFFF: no candidate),
+ * caller-owned device arrays of n entries.  Levels >= 8 have no candidates.
+ * Enqueued on the context stream.  JSLAM_ERR_ARG for bad sizes, pointers,
+ * radius (< 0) or max_dist (outside 0..256); JSLAM_ERR_STATE before an
+ * extraction; n == 0 returns JSLAM_OK. */
+jslam_status jslam_track(jslam_ctx *ctx, int32_t pair, int32_t side, const float *u, const float *v,
+                         const uint8_t *level, const uint32_t *desc, int32_t n, float radius, int32_t max_dist,
+                         int32_t *out_idx, uint16_t *out_dist);
+
 /* Views of one pair's refinement, one entry per left keypoint. */
 typedef struct {
     int32_t count;                /* == left keypoint count; -1 until jslam_sync() */

@@ -840,13 +840,14 @@ void or_subpixel(const uint8_t *left0, const uint8_t *right0, int32_t W0, int32_
  * best candidate minimises (Hamming distance, index); it is accepted when
  * its distance is at most max_dist and, if another candidate exists, 10 best
  * <= 9 second (ratio 0.9 against the second-smallest distance, in integers).
- * Outputs: idx (-1 none or rejected) and dist (best distance, 0xFFFF when
- * there is no candidate).                                                   */
+ * A predicted level of 8 or more has no candidates.  Outputs: idx (-1 none
+ * or rejected) and dist (best distance, 0xFFFF when there is no candidate). */
 void or_track(const or_keypoints *Kf, float scale, const float *u, const float *v, const uint8_t *lvl,
               const uint32_t *desc, int32_t n, float radius, int32_t max_dist,
               int32_t *idx_out, uint16_t *dist_out)
 {
     for (int32_t q = 0; q < n; ++q) {
+        if (lvl[q] >= OR_MAX_LEVELS) { idx_out[q] = -1; dist_out[q] = 0xFFFF; continue; }
         float zf = (float)or_level_scale(scale, lvl[q]);
         volatile float r = radius * zf;  /* one float rounding, no contraction */
         int32_t best = -1, bd = 0x7fffffff, sd = 0x7fffffff;

@@ -185,6 +185,7 @@ struct jslam_ctx {
     std::vector<ImageDesc> h_images;
     std::vector<LevelDesc> h_levels;
     std::vector<size_t> staging_off;
+    std::vector<float> pair_scale;  // scale factor of each pair of the current plan
     Batch batch{};
     Params prm{};
 
@@ -555,6 +556,8 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     ctx->plan_skip = ctx->skip_on;
     ctx->layouts = layouts;
     ctx->result_off = result_off;
+    ctx->pair_scale.resize(n);
+    for (int p = 0; p < n; ++p) ctx->pair_scale[p] = jobs[p].scale;
     ctx->h_images.assign(images, images + n_img);
     ctx->h_levels.assign(levels, levels + n_levels);
     return JSLAM_OK;
@@ -815,6 +818,31 @@ jslam_status jslam_refine_matches(jslam_ctx *ctx, int32_t half_window, int32_t s
     }
     ctx->have_refine = true;
     return JSLAM_OK;
+}
+
+jslam_status jslam_track(jslam_ctx *ctx, int32_t pair, int32_t side, const float *u, const float *v,
+                         const uint8_t *level, const uint32_t *desc, int32_t n, float radius, int32_t max_dist,
+                         int32_t *out_idx, uint16_t *out_dist)
+{
+    if (!ctx) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (n < 0 || side < 0 || side > 1 || !(radius >= 0.0f && radius < 1e6f) || max_dist < 0 || max_dist > 256)
+        return JSLAM_ERR_ARG;
+    if (n > 0 && (!u || !v || !level || !desc || !out_idx || !out_dist)) return JSLAM_ERR_ARG;
+    if (!ctx->have_extract) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size()) return JSLAM_ERR_ARG;
+    if (n == 0) return JSLAM_OK;
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    TrackArgs a;
+    a.image = 2 * pair + side;
+    a.n = n;
+    a.max_dist = max_dist;
+    a.radius = radius;
+    for (int l = 0; l < kMaxLevels; ++l) a.zeta_f[l] = static_cast<float>(zeta_pow(ctx->pair_scale[pair], l));
+    a.u = u; a.v = v; a.level = level; a.desc = desc;
+    a.out_idx = out_idx; a.out_dist = out_dist;
+    return fail(ctx, launch_track(ctx->batch, a, ctx->stream));
 }
 
 static void refined_views(const PairLayout &pl, const char *b, int32_t count, jslam_refined *out)

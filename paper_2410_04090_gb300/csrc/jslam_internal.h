@@ -159,6 +159,19 @@ cudaError_t launch_pfa_finalize(const Batch &b, cudaStream_t stream);
 cudaError_t launch_orient_desc(const Batch &b, cudaStream_t stream);
 cudaError_t launch_match(const Batch &b, cudaStream_t stream);
 cudaError_t launch_refine(const Batch &b, int w, int L, double bf, cudaStream_t stream);
+
+// Feature tracking by projection: caller-projected queries against one image's keypoints.
+struct TrackArgs {
+    int32_t image, n, max_dist;
+    float radius;
+    float zeta_f[kMaxLevels];  // zeta^n rounded to float
+    const float *u, *v;
+    const uint8_t *level;
+    const uint32_t *desc;
+    int32_t *out_idx;
+    uint16_t *out_dist;
+};
+cudaError_t launch_track(const Batch &b, const TrackArgs &a, cudaStream_t stream);
 cudaError_t launch_skipnet(const Batch &b, const SkipModelDev &m, float thresh, cudaStream_t stream);
 cudaError_t set_blur_weights(const int32_t w[7]);
 cudaError_t configure_kernels();

@@ -207,6 +207,79 @@ __global__ void __launch_bounds__(256) k_match(Batch b)
     }
 }
 
+// Feature tracking by projection (middle-end): one warp per query.  For each
+// level of the band the warp search narrows the frame's canonical list to a
+// conservative Y range; lanes take the exact float window test and the
+// Hamming distance, and a warp reduction keeps the smallest (distance,
+// index) and the second-smallest distance.
+__global__ void __launch_bounds__(256) k_track(Batch b, TrackArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (q >= a.n) return;
+    const ImageDesc &I = b.images[a.image];
+    const int lv = a.level[q];
+    unsigned long long best = ~0ull;   // distance << 32 | index
+    uint32_t second = 0xFFFFFFFFu;
+    if (lv < kMaxLevels) {
+        const float u = a.u[q], v = a.v[q];
+        const float r = __fmul_rn(a.radius, a.zeta_f[lv]);
+        uint32_t dq[8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) dq[w] = __ldg(a.desc + (size_t)q * 8 + w);
+        const KpOut &o = I.out;
+        const int m_lo = max(0, lv - 1), m_hi = min(I.levels - 1, lv + 1);
+        const int ylo = (int)floorf(v - r) - 1, yhi = (int)ceilf(v + r) + 1;  // covers every Y that can pass
+        for (int m = m_lo; m <= m_hi; ++m) {
+            const int s = I.level_start[m], e = I.level_start[m + 1];
+            const int z0 = warp_lower_bound_Y(o.Y, s, e, ylo, lane);
+            const int z1 = warp_lower_bound_Y(o.Y, z0, e, yhi + 1, lane);
+            for (int j = z0 + lane; j < z1; j += 32) {
+                const float dx = __fsub_rn((float)o.X[j], u), dy = __fsub_rn((float)o.Y[j], v);
+                if (fabsf(dx) > r || fabsf(dy) > r) continue;
+                const uint4 *dr = reinterpret_cast<const uint4 *>(o.desc + (size_t)j * 8);
+                const uint4 r0 = dr[0], r1 = dr[1];
+                const uint32_t d = __popc(dq[0] ^ r0.x) + __popc(dq[1] ^ r0.y) + __popc(dq[2] ^ r0.z) +
+                                   __popc(dq[3] ^ r0.w) + __popc(dq[4] ^ r1.x) + __popc(dq[5] ^ r1.y) +
+                                   __popc(dq[6] ^ r1.z) + __popc(dq[7] ^ r1.w);
+                const unsigned long long key = ((unsigned long long)d << 32) | (unsigned)j;
+                if (key < best) {
+                    second = min(second, (uint32_t)(best >> 32));
+                    best = key;
+                } else {
+                    second = min(second, d);
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xFFFFFFFFu, best, off);
+            const uint32_t os = __shfl_xor_sync(0xFFFFFFFFu, second, off);
+            const unsigned long long lo = ob < best ? ob : best, hi = ob < best ? best : ob;
+            second = min(min(second, os), (uint32_t)(hi >> 32));
+            best = lo;
+        }
+    }
+    if (lane == 0) {
+        if (best == ~0ull) {
+            a.out_idx[q] = -1;
+            a.out_dist[q] = 0xFFFF;
+        } else {
+            const uint32_t d = (uint32_t)(best >> 32);
+            const bool ok = (int)d <= a.max_dist && (second == 0xFFFFFFFFu || 10u * d <= 9u * second);
+            a.out_idx[q] = ok ? (int)(best & 0xFFFFFFFFu) : -1;
+            a.out_dist[q] = (uint16_t)d;
+        }
+    }
+}
+
+cudaError_t launch_track(const Batch &b, const TrackArgs &a, cudaStream_t stream)
+{
+    if (a.n == 0) return cudaSuccess;
+    k_track<<<(a.n + 7) / 8, 256, 0, stream>>>(b, a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_match(const Batch &b, cudaStream_t stream)
 {
     if (b.n_pairs == 0 || b.max_capacity == 0) return cudaSuccess;

@@ -98,7 +98,7 @@ SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extra
            "jslam_stage_times", "jslam_pfa_scores_static", "jslam_corner_table", "jslam_set_tuning",
            "jslam_autotune", "jslam_graph_capture", "jslam_graph_launch", "jslam_set_skip_model",
            "jslam_get_skip_view", "jslam_result_range", "jslam_download_range", "jslam_refine_matches",
-           "jslam_get_refined", "jslam_result_refined_view")
+           "jslam_get_refined", "jslam_result_refined_view", "jslam_track")
 STAGES = ("pyramid", "skip", "detect", "pfa_nms", "pfa_final", "orb", "match", "refine")
 
 _lib = None
@@ -130,6 +130,9 @@ def lib():
         L.jslam_get_matches.restype = st
         L.jslam_get_level.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.POINTER(LevelView)]
         L.jslam_get_level.restype = st
+        L.jslam_track.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_int32, C.c_float, C.c_int32, C.c_void_p, C.c_void_p]
+        L.jslam_track.restype = st
         L.jslam_refine_matches.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_float]
         L.jslam_refine_matches.restype = st
         L.jslam_get_refined.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Refined)]
@@ -366,6 +369,26 @@ class Frontend:
         """Enqueue the correlation minimisation of the last match (sub-pixel
         disparity and depth of every accepted match)."""
         _check(lib().jslam_refine_matches(self._h, half_window, search, bf), "jslam_refine_matches")
+
+    def track(self, pair: int, side: int, u, v, level, desc, radius: float, max_dist: int = 100):
+        """Enqueue tracking of caller-projected queries (CUDA tensors: u, v
+        float32 [n], level uint8 [n], desc int32/uint32 [n, 8]) against the
+        keypoints of (pair, side); returns (idx int32 [n], dist uint16-as-int32
+        [n]) CUDA tensors, valid after sync()."""
+        import torch
+        n = int(u.numel())
+        for t, dt in ((u, torch.float32), (v, torch.float32), (level, torch.uint8)):
+            if not (t.is_cuda and t.dtype == dt and t.is_contiguous() and t.numel() == n):
+                raise ValueError("u, v: float32 and level: uint8 contiguous CUDA tensors of the same length")
+        if not (desc.is_cuda and desc.dtype in (torch.int32, torch.uint32) and desc.is_contiguous()
+                and desc.numel() == 8 * n):
+            raise ValueError("desc: contiguous int32 CUDA tensor of shape [n, 8]")
+        idx = torch.empty(n, dtype=torch.int32, device=u.device)
+        dist = torch.empty(n, dtype=torch.int16, device=u.device)
+        _check(lib().jslam_track(self._h, pair, side, u.data_ptr(), v.data_ptr(), level.data_ptr(), desc.data_ptr(),
+                                 n, radius, max_dist, idx.data_ptr(), dist.data_ptr()), "jslam_track")
+        self._keep_track = (u, v, level, desc, idx, dist)
+        return idx, dist
 
     def refined(self, pair: int = 0) -> dict:
         r = Refined()
