@@ -606,12 +606,29 @@ def main():
                  "queries_per_s": n_q / (track_ms / min(args.steps, 10) / 1e3), "tracked_fraction": tracked / max(n_q, 1),
                  "mode": "jslam_track(radius 8, max_dist 100), previous frame's left keypoints into the next frame"}
 
+    # the paper's feature-culling kernels (CRF-matrix + MLPT/TEWA) as an
+    # ablation beside the fused detection kernel, on the same batch
+    fc_abl = None
+    if not args.only_batched:
+        crf, fc = [], []
+        fe.extract_batch(jobs)
+        for _ in range(5):
+            fe.fc_ablation(8)
+            fe.sync()
+            t = fe.fc_ablation_times()
+            crf.append(t["crf_ms"]); fc.append(t["fc_ms"])
+        fc_abl = {"crf_matrix_ms": statistics.median(crf[1:]), "mlpt_tewa_fc_ms": statistics.median(fc[1:]),
+                  "n_max": 8, "fused_detect_ms": stage_acc["detect"] / args.steps,
+                  "note": "paper scheme: CRF-matrix of every level written to HBM (primary threshold), then "
+                          "per-level MLPT/TEWA culling kernels; fused: FAST + BR + culling + PFA scatter in one "
+                          "persistent kernel, no CRF-matrix"}
+
     e2e = None
     if not args.only_batched:
         e2e = run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, stream)
     if rank == 0:
         emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks,
-             tuning, skip_quality, dev.index, refine, track)
+             tuning, skip_quality, dev.index, refine, track, fc_abl)
     fe.close()
     for extra in [graph_fe, skip_fe] + extra_fes:
         if extra:
@@ -687,7 +704,7 @@ def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, 
 
 
 def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks, tuning,
-         skip_quality, dev_index, refine=None, track=None):
+         skip_quality, dev_index, refine=None, track=None, fc_abl=None):
     import numpy as np
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
@@ -725,6 +742,7 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
                        "pairs_per_step": n, "mode": args.mode, "detect_tile_px": list(tuning),
                        "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
             "modes": mode_values, "learned_skip": skip_quality, "refine": refine, "track": track,
+            "fc_ablation": fc_abl,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks.summary(), "gpu_launches": launches[args.mode] * args.steps,
             "keypoints_per_image_mean": float(np.mean(counts))}

@@ -166,6 +166,31 @@ jslam_status jslam_track(jslam_ctx *ctx, int32_t pair, int32_t side, const float
                          const uint8_t *level, const uint32_t *desc, int32_t n, float radius, int32_t max_dist,
                          int32_t *out_idx, uint16_t *out_dist);
 
+/* Feature Culling the paper's way, kept as an ablation baseline (Sec.
+ * II-C-1; no counterpart in the exact path, which culls inside detection
+ * without a CRF-matrix): for the last extraction, writes the CRF-matrix of
+ * every level (response of primary-threshold corners, 0 elsewhere) to
+ * device memory, then culls it per cell with Multi-Location-Per-Thread
+ * passes under Thread-Efficient Warp Allocation (blocks 128 threads wide
+ * holding whole cells, N_t = ceil(c / n_max) threads tall).  Each cell's
+ * result is the key response << 16 | (0xFFFF - index in cell) of its
+ * strongest corner (0: none) -- with the fallback threshold off, the same
+ * keys the fused detection kernel produced.  Enqueued on the context
+ * stream, timed by its own events.  JSLAM_ERR_ARG when k_per_cell != 1,
+ * n_max < 1 or ceil(c / n_max) > 8 at some level; JSLAM_ERR_STATE before an
+ * extraction. */
+jslam_status jslam_fc_ablation(jslam_ctx *ctx, int32_t n_max);
+
+/* Device views of one level's per-cell keys (cells_y x cells_x, row-major)
+ * from the ablation and from the fused detection kernel. */
+jslam_status jslam_fc_ablation_view(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t level,
+                                    const uint32_t **ablation_keys, const uint32_t **fused_keys,
+                                    int32_t *cells_x, int32_t *cells_y);
+
+/* Milliseconds of the ablation's CRF-matrix kernel and of its culling
+ * kernels (after jslam_sync). */
+jslam_status jslam_fc_ablation_times(jslam_ctx *ctx, float *crf_ms, float *fc_ms);
+
 /* Views of one pair's refinement, one entry per left keypoint. */
 typedef struct {
     int32_t count;                /* == left keypoint count; -1 until jslam_sync() */

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libjslam.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CUDA_SOURCES = ["k_detect.cu", "k_pyca.cu", "k_orb_match.cu", "k_refine.cu", "k_skipnet.cu", "jslam_api.cu", "pfa_static.cu"]
+CUDA_SOURCES = ["k_detect.cu", "k_pyca.cu", "k_orb_match.cu", "k_refine.cu", "k_fc_ablation.cu", "k_skipnet.cu", "jslam_api.cu", "pfa_static.cu"]
 HOST_SOURCES = ["tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -186,6 +186,12 @@ struct jslam_ctx {
     std::vector<LevelDesc> h_levels;
     std::vector<size_t> staging_off;
     std::vector<float> pair_scale;  // scale factor of each pair of the current plan
+    size_t slot_count = 0;          // candidate slots of the current plan
+    // feature-culling ablation (the paper's CRF-matrix + MLPT/TEWA kernels)
+    GrowBuf abl;
+    std::vector<uint64_t> abl_off;
+    cudaEvent_t abl_ev[3] = {};
+    bool have_ablation = false;
     Batch batch{};
     Params prm{};
 
@@ -556,6 +562,8 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     ctx->plan_skip = ctx->skip_on;
     ctx->layouts = layouts;
     ctx->result_off = result_off;
+    ctx->slot_count = (size_t)n_slots;
+    ctx->have_ablation = false;
     ctx->pair_scale.resize(n);
     for (int p = 0; p < n; ++p) ctx->pair_scale[p] = jobs[p].scale;
     ctx->h_images.assign(images, images + n_img);
@@ -843,6 +851,84 @@ jslam_status jslam_track(jslam_ctx *ctx, int32_t pair, int32_t side, const float
     a.u = u; a.v = v; a.level = level; a.desc = desc;
     a.out_idx = out_idx; a.out_dist = out_dist;
     return fail(ctx, launch_track(ctx->batch, a, ctx->stream));
+}
+
+jslam_status jslam_fc_ablation(jslam_ctx *ctx, int32_t n_max)
+{
+    if (!ctx) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (!ctx->have_extract) return JSLAM_ERR_STATE;
+    if (n_max < 1 || ctx->cfg.k_per_cell != 1) return JSLAM_ERR_ARG;
+    const std::vector<LevelDesc> &lv = ctx->h_levels;
+    int level_c[kMaxLevels] = {}, level_cy[kMaxLevels] = {}, level_bx[kMaxLevels] = {};
+    int max_levels = 0, max_pixels = 0;
+    ctx->abl_off.assign(lv.size(), 0);
+    uint64_t total = 0;
+    for (size_t i = 0; i < lv.size(); ++i) {
+        const LevelDesc &L = lv[i];
+        ctx->abl_off[i] = total;
+        total += (uint64_t)L.W * (uint64_t)L.H;
+        max_pixels = std::max(max_pixels, L.W * L.H);
+        max_levels = std::max(max_levels, L.level + 1);
+        level_c[L.level] = std::max(level_c[L.level], L.c);
+        level_cy[L.level] = std::max(level_cy[L.level], L.cells_y);
+        const int cpb = 128 / L.c;
+        level_bx[L.level] = std::max(level_bx[L.level], (L.cells_x + cpb - 1) / cpb);
+    }
+    for (int l = 0; l < max_levels; ++l)
+        if ((level_c[l] + n_max - 1) / n_max > 8) return JSLAM_ERR_ARG;  // 128 x N_t <= 1024 threads
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    const size_t off_bytes = align_up(lv.size() * sizeof(uint64_t), 256);
+    const size_t key_bytes = align_up(ctx->slot_count * sizeof(uint32_t), 256);
+    cudaError_t e = ctx->abl.ensure(off_bytes + key_bytes + total * sizeof(uint16_t) + 256, false, nullptr);
+    if (e != cudaSuccess) return fail(ctx, e);
+    for (cudaEvent_t &ev : ctx->abl_ev)
+        if (!ev && (e = cudaEventCreate(&ev)) != cudaSuccess) return fail(ctx, e);
+    uint64_t *d_off = ctx->abl.as<uint64_t>();
+    uint32_t *d_keys = ctx->abl.as<uint32_t>(off_bytes);
+    uint16_t *d_crf = ctx->abl.as<uint16_t>(off_bytes + key_bytes);
+    // ctx->abl_off stays alive (and unchanged) until the next call, after this copy ran
+    if ((e = cudaMemcpyAsync(d_off, ctx->abl_off.data(), lv.size() * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                             ctx->stream)) != cudaSuccess)
+        return fail(ctx, e);
+    if ((e = cudaEventRecord(ctx->abl_ev[0], ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    e = launch_fc_ablation(ctx->batch, d_crf, d_off, d_keys, level_bx, max_pixels, max_levels, level_cy, level_c,
+                           n_max, ctx->stream, ctx->abl_ev[1]);
+    if (e != cudaSuccess) return fail(ctx, e);
+    if ((e = cudaEventRecord(ctx->abl_ev[2], ctx->stream)) != cudaSuccess) return fail(ctx, e);
+    ctx->have_ablation = true;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_fc_ablation_view(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t level,
+                                    const uint32_t **ablation_keys, const uint32_t **fused_keys, int32_t *cells_x,
+                                    int32_t *cells_y)
+{
+    if (!ctx || !ablation_keys || !fused_keys || !cells_x || !cells_y) return JSLAM_ERR_ARG;
+    if (!ctx->have_ablation) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size() || side < 0 || side > 1) return JSLAM_ERR_ARG;
+    const int img = 2 * pair + side;
+    int base = -1, nl = 0;
+    for (size_t i = 0; i < ctx->h_levels.size(); ++i)
+        if (ctx->h_levels[i].image == img) { if (base < 0) base = (int)i; ++nl; }
+    if (level < 0 || level >= nl) return JSLAM_ERR_ARG;
+    const LevelDesc &L = ctx->h_levels[base + level];
+    const size_t off_bytes = align_up(ctx->h_levels.size() * sizeof(uint64_t), 256);
+    *ablation_keys = ctx->abl.as<uint32_t>(off_bytes) + L.slot_base;
+    *fused_keys = ctx->batch.slots + L.slot_base;
+    *cells_x = L.cells_x;
+    *cells_y = L.cells_y;
+    return JSLAM_OK;
+}
+
+jslam_status jslam_fc_ablation_times(jslam_ctx *ctx, float *crf_ms, float *fc_ms)
+{
+    if (!ctx || !crf_ms || !fc_ms) return JSLAM_ERR_ARG;
+    if (!ctx->have_ablation) return JSLAM_ERR_STATE;
+    cudaError_t e = cudaEventElapsedTime(crf_ms, ctx->abl_ev[0], ctx->abl_ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(fc_ms, ctx->abl_ev[1], ctx->abl_ev[2]);
+    return fail(ctx, e);
 }
 
 static void refined_views(const PairLayout &pl, const char *b, int32_t count, jslam_refined *out)
@@ -1192,8 +1278,11 @@ void jslam_destroy(jslam_ctx *ctx)
     ctx->counts.release();
     ctx->skipw.release();
     ctx->skipbuf.release();
+    ctx->abl.release();
     if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
     for (cudaEvent_t ev : ctx->events)
+        if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : ctx->abl_ev)
         if (ev) cudaEventDestroy(ev);
     if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);

@@ -172,6 +172,9 @@ struct TrackArgs {
     uint16_t *out_dist;
 };
 cudaError_t launch_track(const Batch &b, const TrackArgs &a, cudaStream_t stream);
+cudaError_t launch_fc_ablation(const Batch &b, uint16_t *crf, const uint64_t *off, uint32_t *keys,
+                               const int *level_blocks, int max_pixels, int max_levels, const int *level_cells_y,
+                               const int *level_c, int n_max, cudaStream_t stream, cudaEvent_t mid);
 cudaError_t launch_skipnet(const Batch &b, const SkipModelDev &m, float thresh, cudaStream_t stream);
 cudaError_t set_blur_weights(const int32_t w[7]);
 cudaError_t configure_kernels();

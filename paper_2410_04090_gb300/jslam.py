@@ -98,7 +98,8 @@ SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extra
            "jslam_stage_times", "jslam_pfa_scores_static", "jslam_corner_table", "jslam_set_tuning",
            "jslam_autotune", "jslam_graph_capture", "jslam_graph_launch", "jslam_set_skip_model",
            "jslam_get_skip_view", "jslam_result_range", "jslam_download_range", "jslam_refine_matches",
-           "jslam_get_refined", "jslam_result_refined_view", "jslam_track")
+           "jslam_get_refined", "jslam_result_refined_view", "jslam_track", "jslam_fc_ablation",
+           "jslam_fc_ablation_view", "jslam_fc_ablation_times")
 STAGES = ("pyramid", "skip", "detect", "pfa_nms", "pfa_final", "orb", "match", "refine")
 
 _lib = None
@@ -133,6 +134,13 @@ def lib():
         L.jslam_track.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_int32, C.c_float, C.c_int32, C.c_void_p, C.c_void_p]
         L.jslam_track.restype = st
+        L.jslam_fc_ablation.argtypes = [C.c_void_p, C.c_int32]
+        L.jslam_fc_ablation.restype = st
+        L.jslam_fc_ablation_view.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p),
+                                             C.POINTER(C.c_void_p), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.jslam_fc_ablation_view.restype = st
+        L.jslam_fc_ablation_times.argtypes = [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float)]
+        L.jslam_fc_ablation_times.restype = st
         L.jslam_refine_matches.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_float]
         L.jslam_refine_matches.restype = st
         L.jslam_get_refined.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Refined)]
@@ -389,6 +397,25 @@ class Frontend:
                                  n, radius, max_dist, idx.data_ptr(), dist.data_ptr()), "jslam_track")
         self._keep_track = (u, v, level, desc, idx, dist)
         return idx, dist
+
+    def fc_ablation(self, n_max: int = 8):
+        """Enqueue the paper-style feature culling (CRF-matrix + MLPT/TEWA) of
+        the last extraction (an ablation baseline)."""
+        _check(lib().jslam_fc_ablation(self._h, n_max), "jslam_fc_ablation")
+
+    def fc_ablation_keys(self, pair: int, side: int, level: int):
+        """(ablation keys, fused-kernel keys) of one level as [cells_y, cells_x] CUDA tensors."""
+        a, f = C.c_void_p(), C.c_void_p()
+        cx, cy = C.c_int32(), C.c_int32()
+        _check(lib().jslam_fc_ablation_view(self._h, pair, side, level, C.byref(a), C.byref(f), C.byref(cx),
+                                            C.byref(cy)), "jslam_fc_ablation_view")
+        shape = (cy.value, cx.value)
+        return _device_view(a.value, shape, np.uint32, self.device), _device_view(f.value, shape, np.uint32, self.device)
+
+    def fc_ablation_times(self):
+        a, b = C.c_float(), C.c_float()
+        _check(lib().jslam_fc_ablation_times(self._h, C.byref(a), C.byref(b)), "jslam_fc_ablation_times")
+        return {"crf_ms": a.value, "fc_ms": b.value}
 
     def refined(self, pair: int = 0) -> dict:
         r = Refined()
