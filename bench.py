@@ -8,10 +8,11 @@ KITTI-shaped sequence (1241x376 u8, 8 levels, scale 1.2, FAST 20 with
 fallback 7, 32x32 cells, 2000 features per image).
 
 Modes, each timed over the same steps:
-  graph_streams2  the step's pairs split over two contexts on two streams, each
-                  half captured once as a CUDA graph and replayed (fork/join by
-                  events) -- the headline
-  streams2        the same two halves as plain batched calls
+  graph_streams4  the step's pairs split over four contexts on four streams,
+                  each part captured once as a CUDA graph and replayed
+                  (fork/join by events) -- the headline
+  graph_streams2  the same with two parts
+  streams4/2      the same parts as plain batched calls
   batched         all pairs of the step in one C-ABI call (one launch per stage)
   graph           the batched call captured once as a CUDA graph and replayed
   plain           one C-ABI call per stereo pair
@@ -85,8 +86,9 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="kitti_1241x376_L8", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--frames", type=int, default=100, help="pairs per step (sequence workloads)")
-    ap.add_argument("--mode", choices=["batched", "graph", "plain", "streams2", "graph_streams2"],
-                    default="graph_streams2", help="the headline mode (the others are timed beside it)")
+    ap.add_argument("--mode", choices=["batched", "graph", "plain", "streams2", "graph_streams2", "streams4",
+                                       "graph_streams4"],
+                    default="graph_streams4", help="the headline mode (the others are timed beside it)")
     ap.add_argument("--cpu-pairs", type=int, default=12, help="pairs in the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, nargs=2, metavar=("W", "H"),
@@ -432,48 +434,52 @@ def main():
         graph_fe.graph_capture(jobs)
         modes["graph"] = step_graph
         modes["plain"] = step_plain
-    if not args.only_batched and n >= 2:
-        # the step's pairs split over two contexts on two streams (fork and
-        # join on the timing stream): one half's kernels fill the other's
-        # launch gaps and kernel tails
-        half = (n + 1) // 2
-        dims2 = dict(dims, max_pairs=half)
-        s2 = torch.cuda.Stream(device=dev)
-        fa = jslam.Frontend(device=dev.index, stream=stream, **dims2)
-        fb = jslam.Frontend(device=dev.index, stream=s2, **dims2)
-        part = [fa.prepare_batch([jslam.Job(l, r, **p) for l, r, p in zip(lefts[:half], rights[:half], params[:half])]),
-                fb.prepare_batch([jslam.Job(l, r, **p) for l, r, p in zip(lefts[half:], rights[half:], params[half:])])]
-        ga = jslam.Frontend(device=dev.index, stream=stream, **dims2)
-        gb = jslam.Frontend(device=dev.index, stream=s2, **dims2)
-        for c in (fa, fb, ga, gb):
-            c.set_tuning(*tuning)
-        ga.graph_capture(part[0])
-        gb.graph_capture(part[1])
-        extra_fes += [fa, fb, ga, gb]
+    def split_modes(S):
+        """The step's pairs split over S contexts on S streams (fork and join
+        on the timing stream): one part's kernels fill the others' launch
+        gaps and kernel tails.  Returns (plain step, graph-replay step)."""
+        bounds = [round(i * n / S) for i in range(S + 1)]
+        streams = [stream] + [torch.cuda.Stream(device=dev) for _ in range(S - 1)]
+        plain, graphs, parts = [], [], []
+        for i in range(S):
+            sl = slice(bounds[i], bounds[i + 1])
+            d = dict(dims, max_pairs=max(1, bounds[i + 1] - bounds[i]))
+            fp = jslam.Frontend(device=dev.index, stream=streams[i], **d)
+            fg = jslam.Frontend(device=dev.index, stream=streams[i], **d)
+            part = fp.prepare_batch([jslam.Job(l, r, **p) for l, r, p in zip(lefts[sl], rights[sl], params[sl])])
+            for c in (fp, fg):
+                c.set_tuning(*tuning)
+            fg.graph_capture(part)
+            plain.append(fp); graphs.append(fg); parts.append(part)
+            extra_fes.extend([fp, fg])
 
         def fork_join(body):
             ev = torch.cuda.Event()
             ev.record(stream)
-            s2.wait_event(ev)
+            for s_ in streams[1:]:
+                s_.wait_event(ev)
             body()
-            ev2 = torch.cuda.Event()
-            ev2.record(s2)
-            stream.wait_event(ev2)
+            for s_ in streams[1:]:
+                e_ = torch.cuda.Event()
+                e_.record(s_)
+                stream.wait_event(e_)
 
-        def step_streams2():
+        def step_plain_split():
             def body():
-                fa.extract_batch(part[0]); fa.match()
-                fb.extract_batch(part[1]); fb.match()
+                for fp, part in zip(plain, parts):
+                    fp.extract_batch(part)
+                    fp.match()
             fork_join(body)
 
-        def step_graph_streams2():
-            def body():
-                ga.graph_launch()
-                gb.graph_launch()
-            fork_join(body)
+        def step_graph_split():
+            fork_join(lambda: [fg.graph_launch() for fg in graphs])
 
-        modes["streams2"] = step_streams2
-        modes["graph_streams2"] = step_graph_streams2
+        return step_plain_split, step_graph_split
+
+    if not args.only_batched:
+        for S in (2, 4):
+            if n >= S:
+                modes[f"streams{S}"], modes[f"graph_streams{S}"] = split_modes(S)
     if args.mode not in modes:
         args.mode = "batched"
     for _ in range(args.warmup):
@@ -734,7 +740,8 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args, pairs, params, lo)
     launches = {"batched": LAUNCHES_PER_CALL, "graph": LAUNCHES_PER_CALL, "plain": LAUNCHES_PER_CALL * n,
                 "learned_skip": LAUNCHES_PER_CALL + 2, "streams2": 2 * LAUNCHES_PER_CALL,
-                "graph_streams2": 2 * LAUNCHES_PER_CALL}
+                "graph_streams2": 2 * LAUNCHES_PER_CALL, "streams4": 4 * LAUNCHES_PER_CALL,
+                "graph_streams4": 4 * LAUNCHES_PER_CALL}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
