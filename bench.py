@@ -253,6 +253,22 @@ def oracle_params(O, p, lo):
 
 # ------------------------------------------------------------------ reference arm
 
+def max_over_ranks(dist, values, device):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest
+    rank sets the whole-job time); identity without a process group."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_value(pairs_per_rank_step, steps, world, total_ms):
+    """Stereo pairs/s of the whole job: every rank processes its own replica
+    of the step's pairs, the time is the slowest rank's."""
+    return pairs_per_rank_step * steps * world / (total_ms / 1e3)
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -510,16 +526,13 @@ def main():
         total_ms = timed_mode(args.mode)
         other_ms = {m: timed_mode(m) for m in modes if m != args.mode}
 
-    t = torch.tensor([total_ms] + list(other_ms.values()), dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    vals = t.tolist()
+    vals = max_over_ranks(dist, [total_ms] + list(other_ms.values()), dev)
     total_ms = vals[0]
     pairs_done = n * args.steps * world
-    value = pairs_done / (total_ms / 1e3)
+    value = whole_job_value(n, args.steps, world, total_ms)
     mode_values = {args.mode: value}
     for m, ms in zip(other_ms, vals[1:]):
-        mode_values[m] = pairs_done / (ms / 1e3)
+        mode_values[m] = whole_job_value(n, args.steps, world, ms)
 
     # keypoint counts of the last batch (for algorithmic bytes)
     fe.extract_batch(jobs); fe.match(); fe.sync()
@@ -696,10 +709,7 @@ def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, 
     t1 = time.perf_counter()
     run(args.steps, 1)
     serial_s = time.perf_counter() - t1
-    te = torch.tensor([e2e_s, serial_s], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_s, serial_s = te.tolist()
+    e2e_s, serial_s = max_over_ranks(dist, [e2e_s, serial_s], dev)
     nb, _ = fe.result_range(0, n)
     fe2.close()
     return {"value": pairs_done / e2e_s, "unit": UNIT,
