@@ -129,6 +129,27 @@ def test_parameter_variants(J, oracle, kw):
     _check_pair(J, oracle, pair.left, pair.right, p)
 
 
+def test_maximum_image_size(J, oracle):
+    """The largest accepted image, 4096 x 4096 with 8 levels and 4000 features:
+    keypoints, descriptors and angles against the oracle (one image, used as
+    both sides, keeps the oracle's share of the test to one extraction)."""
+    import torch
+    img = scenes.random_image(4096, 4096, 5)
+    p = params_from(oracle, levels=8, max_feats=4000, fast_thresh_lo=7)
+    fe = frontend_for(J, p, max_width=4096, max_height=4096, max_pairs=1)
+    t = torch.from_numpy(img).cuda()
+    fe.extract(t, t, p.levels, p.scale, p.fast_thresh, p.cell, p.max_feats)
+    fe.match()
+    fe.sync()
+    want = oracle.extract_image(img, p)
+    compare_keypoints(J.to_numpy(fe.keypoints(0, 0)), want, "4096 left")
+    compare_keypoints(J.to_numpy(fe.keypoints(0, 1)), want, "4096 right")
+    m = J.to_numpy(fe.matches(0))
+    n = want["count"]
+    assert (m["right_idx"][:n] == np.arange(n)).mean() > 0.99  # identical images match themselves
+    fe.close()
+
+
 def test_minimum_size_levels(J, oracle):
     # the deepest level is exactly 2 * border + 1 pixels on its short side
     W0 = H0 = int(np.ceil(39 * 1.2 ** 3))
