@@ -6,9 +6,9 @@
 //             writes it (level 0: an aligned copy of the input), and writes its
 //             7-tap Gaussian (Sec. III, streamlined multiscale detection and
 //             extraction: Gaussian filtering before ORB).
-// k_fast_cull one CTA per block of culling cells of any (image, level): stages
-//             the raw tile plus a 3-pixel halo in shared memory, evaluates the
-//             16-pixel ring of every pixel (Sec. II-A, Eq. 1 labels, Eq. 3
+// k_fast_cull persistent CTAs over blocks of culling cells of any (image,
+//             level): stage the raw tile plus its halo in shared memory (TMA),
+//             evaluate the 16-pixel ring of every pixel (Sec. II-A, Eq. 1 labels, Eq. 3
 //             bounded run length; Sec. III bit masks and SAD response), keeps
 //             the top-k corners of each cell (Sec. II-C-1, Feature Culling)
 //             and adds each survivor to the s0 score map (Sec. II-C-2, PFA
@@ -259,13 +259,16 @@ cudaError_t launch_pyramid(const Batch &b, cudaStream_t stream)
 // TMA (one 2-D tensor map per level) into one of two shared-memory buffers
 // while the CTA works on the other, with an mbarrier per buffer.  Per tile:
 //   1. primary threshold: every thread classifies 4 horizontally adjacent
-//      pixels at once.  For each of the 16 ring offsets the 4 ring bytes are
-//      compared with the 4 per-pixel thresholds by byte-wise carries (no
-//      carry crosses a byte), and the flags are gathered into per-pixel
-//      16-bit bright / dark masks; the corner test of Eq. 3 is one look-up
-//      per mask in the 64 Ki-entry bit table of Sec. III (built on the host
+//      pixels at once (one 32-bit word of centres).  (a) Cardinal pre-test:
+//      the ring positions 0, 4, 8, 12 are compared with the 4 per-pixel
+//      thresholds by byte-wise carries (no carry crosses a byte); groups
+//      with a pixel that may hold an arc of P_min >= 8 are compacted.  (b)
+//      Full test of those groups: all 16 positions, the flags gathered into
+//      per-pixel 16-bit bright / dark masks, and the corner test of Eq. 3 as
+//      a look-up in the 64 Ki-entry bit table of Sec. III (built on the host
 //      for P_min, P_max).  Corners go to a compacted list and mark their cell;
-//   2. fallback threshold, only for pixels of cells left without a corner;
+//   2. fallback threshold, only for pixels of cells left without a corner
+//      (cells with no pixel inside the border never ask for it);
 //   3. for each listed corner the SAD response is computed and the cell's
 //      top-k is kept by atomicMax on the key response << 16 | (0xFFFF -
 //      index in cell) (strongest first, then smaller y, then smaller x);
