@@ -72,7 +72,8 @@ WORKLOAD_DESC = {
 KERNELS = {"pyramid": "k_pyramid", "detect": "k_fast_cull", "pfa_nms": "k_pfa_nms",
            "pfa_final": "k_pfa_finalize", "orb": "k_orient_desc", "match": "k_match"}
 KERNEL_SOURCES = {"k_pyramid": "k_detect.cu", "k_fast_cull": "k_detect.cu", "k_pfa_nms": "k_pyca.cu",
-                  "k_pfa_finalize": "k_pyca.cu", "k_orient_desc": "k_orb_match.cu", "k_match": "k_orb_match.cu"}
+                  "k_pfa_finalize": "k_pyca.cu", "k_orient_desc": "k_orb_match.cu", "k_match": "k_orb_match.cu",
+                  "k_skipnet": "k_skipnet.cu"}
 LAUNCHES_PER_CALL = 6  # pyramid, detect, PFA NMS, PFA final, ORB, match (exact path)
 SKIP_MODEL = os.path.join(ROOT, "paper_2410_04090_gb300", "skipnet_v1.bin")
 REFINE_BF = 386.1448  # fx * baseline (pixels x metres) of a KITTI-like stereo rig, for the depth output
@@ -207,6 +208,17 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def code_hash(path):
+    """First 16 hex digits of the SHA-256 of a source file's code: comments
+    and whitespace removed, so that only a change of the code makes an ncu
+    summary taken from it stale."""
+    import re
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()[:16]
+
+
 def profile_summary(kernel, workload):
     """Key/value lines of the committed ncu summary of this kernel on this
     workload, or None if there is none or the kernel's source changed since."""
@@ -221,8 +233,7 @@ def profile_summary(kernel, workload):
             k, v = ln.split(":", 1)
             vals[k.strip()] = v.strip()
     src = os.path.join(ROOT, "paper_2410_04090_gb300", "csrc", KERNEL_SOURCES[kernel])
-    cur = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return vals if vals.get("source_sha256_16") == cur else None
+    return vals if vals.get("source_code_sha256_16") == code_hash(src) else None
 
 
 def profile_number(vals, key):
