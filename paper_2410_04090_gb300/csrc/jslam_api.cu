@@ -12,7 +12,7 @@
 #include "tables.h"
 
 namespace jslam {
-int fast_smem_bytes(int max_box, int max_px, int max_cells, int k);
+int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, int max_planes);
 }
 
 using namespace jslam;
@@ -295,7 +295,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     std::vector<size_t> result_off(n);
     size_t result_bytes = 0, level_bytes = 0, map_bytes = 0, staging_bytes = 0, table_bytes = 0;
     int n_levels = 0, n_slots = 0, n_segs = 0, max_cap = 0;
-    int max_box = 0, max_px = 0, max_cells = 0;
+    int max_box = 0, max_px = 0, max_cells = 0, max_planes = 0;
     for (int p = 0; p < n; ++p) {
         geo[p] = level_geometry(jobs[p].left.width, jobs[p].left.height, jobs[p].levels, jobs[p].scale, jobs[p].cell);
         layouts[p] = pair_layout(jobs[p].max_feats);
@@ -318,6 +318,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 int bw, bh;
                 detect_box(tw, th, &bw, &bh);
                 max_box = std::max(max_box, bw * bh);
+                max_planes = std::max(max_planes, bh * ((bw + 31) / 32 + 1) * 32);
                 max_px = std::max(max_px, tw * th);
                 max_cells = std::max(max_cells, bx * by);
             }
@@ -538,7 +539,9 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.n_images = n_img; b.n_levels = n_levels; b.n_pairs = n; b.n_segments = n_segs;
     b.pyr_tiles = pyr; b.fast_tiles = fast; b.max_capacity = max_cap;
     b.fast_max_box = max_box; b.fast_max_px = max_px; b.fast_max_cells = max_cells;
-    b.fast_smem = fast_smem_bytes(max_box, max_px, max_cells, k);
+    b.fast_bits = ctx->prm.p_min == 9 && ctx->prm.p_max == 13;
+    b.fast_max_planes = max_planes;
+    b.fast_smem = fast_smem_bytes(max_box, max_px, max_cells, k, b.fast_bits ? max_planes : 0);
     b.corner_lut = ctx->d_lut;
     b.skip_max_tiles = skip_max_tiles;
     b.skip_max_cells = skip_max_cells;

@@ -135,6 +135,8 @@ struct Batch {
     int32_t max_capacity;           // largest keypoint capacity of any image
     int32_t fast_smem;              // dynamic shared memory of the detection kernel
     int32_t fast_max_box, fast_max_px, fast_max_cells;  // its tile layout maxima
+    int32_t fast_max_planes;        // bit-plane bytes of the largest tile box
+    int32_t fast_bits;              // 1: bit-sliced ring test (P_min = 9, P_max = 13)
     const uint32_t *corner_lut;     // bit m: P_min <= longest circular run of m <= P_max
     uint32_t *slots;                // candidate keys per slot
     uint32_t *slot_k;               // PFA scores seen by each slot

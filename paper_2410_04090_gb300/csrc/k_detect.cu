@@ -287,15 +287,17 @@ constexpr uint32_t kH = 0x80808080u, kL7 = 0x7F7F7F7Fu;
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
 
 struct FastLayout {
-    int buf0, buf1, clist, ckey, cand, has_hi, sel, bar, total;
+    int buf0, buf1, clist, ckey, cand, planes, has_hi, sel, bar, total;
 };
 
 __host__ __device__ inline int fast_align(int v, int a) { return (v + a - 1) / a * a; }
 
 // A group is 4 pixels of a row; a tile of max_px pixels whose rows hold at
 // most kFastMaxTile pixels has at most max_px / 4 + kFastMaxTile groups.
-// `cand` lists the groups that pass the cardinal pre-test.
-__host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int max_cells, int k)
+// `cand` lists the groups that pass the cardinal pre-test (table path);
+// `planes` holds the bit-planes of the tile box (bit-sliced path, max_planes
+// bytes: box rows x (chunks + 1) x 8 words).
+__host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int max_cells, int k, int max_planes)
 {
     FastLayout l;
     int o = kLutWords * 4;
@@ -303,7 +305,8 @@ __host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int m
     l.buf1 = o;  o += fast_align(max_box, 128);
     l.clist = o; o += fast_align(max_px * 2, 16);
     l.ckey = o;  o += k > 1 ? fast_align(max_px * 4, 16) : 0;
-    l.cand = o;  o += fast_align((max_px / 4 + kFastMaxTile) * 2, 16);
+    l.cand = o;  o += max_planes > 0 ? 0 : fast_align((max_px / 4 + kFastMaxTile) * 2, 16);
+    l.planes = o; o += fast_align(max_planes, 16);
     l.has_hi = o; o += fast_align(max_cells, 16);
     l.sel = o;   o += fast_align(max_cells * k * 4, 16);
     l.bar = o;   o += 16;
@@ -480,19 +483,162 @@ __device__ __forceinline__ uint32_t group_pretest(const uint32_t *base, int wpr,
     return (((x >> 7) * 0x00204081u) >> 21) & 0xFu;
 }
 
+// ---- bit-sliced ring test (P_min = 9, P_max = 13): 32 pixels per word, bit
+// j of word i = bit i of pixel j's byte.  a > b for 8-bit numbers: the carry
+// out of a + ~b, one majority per bit; c + e: a ripple adder against the
+// constant's bit masks, returning the carry out.
+
+// Bit-planes of a 32-byte chunk (bytes j of words a, z in memory order):
+// output word i, bit j = bit i of byte j.  Each 8-byte block is an 8 x 8 bit
+// matrix (row = byte, column = bit) transposed by three delta swaps (2 x 2,
+// 4 x 4 and 8 x 8 sub-blocks); byte i of the transposed block b is then byte
+// b of output word i.
+__device__ __forceinline__ void bs_transpose(uint4 a, uint4 z, uint4 *dst)
+{
+    uint32_t w[8] = { a.x, a.y, a.z, a.w, z.x, z.y, z.z, z.w };
+#pragma unroll
+    for (int blk = 0; blk < 4; ++blk) {
+        uint32_t lo = w[2 * blk], hi = w[2 * blk + 1], t;
+        t = (lo ^ (lo >> 7)) & 0x00AA00AAu;  lo ^= t ^ (t << 7);
+        t = (hi ^ (hi >> 7)) & 0x00AA00AAu;  hi ^= t ^ (t << 7);
+        t = (lo ^ (lo >> 14)) & 0x0000CCCCu; lo ^= t ^ (t << 14);
+        t = (hi ^ (hi >> 14)) & 0x0000CCCCu; hi ^= t ^ (t << 14);
+        t = (lo ^ (hi << 4)) & 0xF0F0F0F0u;  lo ^= t; hi ^= t >> 4;
+        w[2 * blk] = lo; w[2 * blk + 1] = hi;
+    }
+    uint32_t o[8];
+#pragma unroll
+    for (int half = 0; half < 2; ++half)
+#pragma unroll
+        for (int i = 0; i < 4; i += 2) {
+            const uint32_t sel = (uint32_t)i | ((uint32_t)(4 + i) << 4) | ((uint32_t)(i + 1) << 8) |
+                                 ((uint32_t)(5 + i) << 12);
+            const uint32_t A = __byte_perm(w[half], w[2 + half], sel);
+            const uint32_t B = __byte_perm(w[4 + half], w[6 + half], sel);
+            o[4 * half + i] = __byte_perm(A, B, 0x5410u);
+            o[4 * half + i + 1] = __byte_perm(A, B, 0x7632u);
+        }
+    dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+    dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+}
+
+__device__ __forceinline__ uint32_t bs_greater(const uint32_t (&a)[8], const uint32_t (&b)[8])
+{
+    uint32_t c = a[0] & ~b[0];
+#pragma unroll
+    for (int i = 1; i < 8; ++i) c = maj3(a[i], ~b[i], c);
+    return c;
+}
+
+__device__ __forceinline__ uint32_t bs_add_const(const uint32_t (&c)[8], uint32_t e, uint32_t (&t)[8])
+{
+    uint32_t k = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint32_t E = 0u - ((e >> i) & 1u);
+        t[i] = c[i] ^ E ^ k;
+        k = maj3(c[i], E, k);
+    }
+    return k;
+}
+
+// Longest circular run of the 16 flag words in [9, 13]: a run of 9 is a
+// window of 8 and the position after it; of 14: windows of 8, 4 and 2.
+__device__ __forceinline__ uint32_t bs_run_9_13(const uint32_t (&F)[16])
+{
+    uint32_t A2[16], A4[16], A8[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) A2[q] = F[q] & F[(q + 1) & 15];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) A4[q] = A2[q] & A2[(q + 2) & 15];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) A8[q] = A4[q] & A4[(q + 4) & 15];
+    uint32_t r9 = 0, r14 = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        r9 |= A8[q] & F[(q + 8) & 15];
+        r14 |= A8[q] & A4[(q + 8) & 15] & A2[(q + 12) & 15];
+    }
+    return r9 & ~r14;
+}
+
+// Corner bits of the 32 pixels of tile row py, chunk m (pixels 32 m + j).
+// `planes`: box rows of `pstride` chunks of 8 words; tile pixel 0 sits at box
+// column sb, so pixel 32 m + j + dx is bit sb + dx + j of chunks (m, m + 1).
+__device__ __forceinline__ uint32_t bs_corners(const uint32_t *planes, int pstride, int py, int m, int sb, int eps)
+{
+    constexpr int RDX[16] = { 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1 };
+    constexpr int RDY[16] = { 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1, 0, 1, 2, 3 };
+    uint32_t C[8], Tb[8], Td[8];
+    {
+        const uint4 *r = reinterpret_cast<const uint4 *>(planes + ((py + 3) * pstride + m) * 8);
+        const uint4 l0 = r[0], l1 = r[1], h0 = r[2], h1 = r[3];
+        const uint32_t lo[8] = { l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w };
+        const uint32_t hi[8] = { h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w };
+#pragma unroll
+        for (int i = 0; i < 8; ++i) C[i] = __funnelshift_r(lo[i], hi[i], sb);
+    }
+    const uint32_t nb = bs_add_const(C, (uint32_t)eps, Tb);      // C + eps >= 256: never brighter
+    uint32_t nd = 0;                                              // C < eps: never darker
+    if (eps > 0) nd = ~bs_add_const(C, (uint32_t)(256 - eps), Td);
+    else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) Td[i] = C[i];
+    }
+    uint32_t Fb[16], Fd[16];
+#pragma unroll
+    for (int dy = 3; dy >= -3; --dy) {
+        const uint4 *r = reinterpret_cast<const uint4 *>(planes + ((py + 3 + dy) * pstride + m) * 8);
+        const uint4 l0 = r[0], l1 = r[1], h0 = r[2], h1 = r[3];
+        const uint32_t lo[8] = { l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w };
+        const uint32_t hi[8] = { h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w };
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            if (RDY[q] != dy) continue;
+            uint32_t P[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) P[i] = __funnelshift_r(lo[i], hi[i], sb + RDX[q]);
+            Fb[q] = bs_greater(P, Tb) & ~nb;
+            Fd[q] = bs_greater(Td, P) & ~nd;
+        }
+    }
+    return bs_run_9_13(Fb) | bs_run_9_13(Fd);
+}
+
+// Bits j of the 32 pixels of tile row chunk px0..px0+31 whose cell state
+// (row of states `st`, cells of c pixels) satisfies keep(state).
+template <typename Keep>
+__device__ __forceinline__ uint32_t cell_bits(const uint8_t *st, int px0, int tw, int c, uint32_t cinv, Keep keep)
+{
+    const int x_last = min(px0 + 31, tw - 1);
+    const int c0 = (int)(((uint32_t)px0 * cinv) >> 16), c1 = (int)(((uint32_t)x_last * cinv) >> 16);
+    uint32_t bits = 0;
+    for (int cx = c0; cx <= c1; ++cx) {
+        if (!keep(st[cx])) continue;
+        const int a = max(cx * c - px0, 0), z = min((cx + 1) * c - px0, 32);
+        bits |= (z >= 32 ? 0xFFFFFFFFu : ((1u << z) - 1u)) & (0xFFFFFFFFu << a);
+    }
+    return bits;
+}
+
 __device__ __forceinline__ int div_small(int v, uint32_t cinv) { return (int)(((uint32_t)v * cinv) >> 16); }
 
+// kBits: the bit-sliced ring test (P_min = 9, P_max = 13); otherwise the
+// byte-lane test with the cardinal pre-test and the corner table (any
+// P_min, P_max).
+template <bool kBits>
 __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int n_corner, need_lo, n_skipped, n_cand[2];
     const int k = b.prm.k, border = b.prm.border, p_min = b.prm.p_min;
-    const FastLayout lay = fast_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k);
+    const FastLayout lay = fast_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k, kBits ? b.fast_max_planes : 0);
     uint32_t *lut = reinterpret_cast<uint32_t *>(smem);
     uint8_t *const buf0 = smem + lay.buf0, *const buf1 = smem + lay.buf1;
     uint16_t *clist = reinterpret_cast<uint16_t *>(smem + lay.clist);
     uint32_t *ckey = reinterpret_cast<uint32_t *>(smem + lay.ckey);
     uint16_t *cand = reinterpret_cast<uint16_t *>(smem + lay.cand);
+    uint32_t *planes = reinterpret_cast<uint32_t *>(smem + lay.planes);
     uint8_t *has_hi = smem + lay.has_hi;
     uint32_t *sel = reinterpret_cast<uint32_t *>(smem + lay.sel);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
@@ -587,6 +733,24 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
         const int gw = max(g1 - g0, 0), nitems = max(r1 - r0, 0) * gw;
         // word of tile column 0 (pixel x0 - 4) within a box row
         const uint32_t *words = reinterpret_cast<const uint32_t *>(tb) + (G.delta >> 2);
+        // bit-sliced path: bit-planes of the whole box, one 32-byte chunk per
+        // thread, plus a zero chunk closing every row (rows are a multiple of
+        // 16 bytes, so a row's last chunk may hold only 16)
+        const int nbc = (rowb + 31) >> 5, pstride = nbc + 1;
+        if (kBits && !all_skipped) {
+            for (int ci = threadIdx.x; ci < L.box_h * pstride; ci += kFastThreads) {
+                const int r = ci / pstride, kc = ci - r * pstride;
+                uint4 a = make_uint4(0u, 0u, 0u, 0u), z = a;
+                if (kc < nbc) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(tb + r * rowb + 32 * kc);
+                    a = src[0];
+                    if (32 * kc + 16 < rowb) z = src[1];
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(planes + ci * 8);
+                bs_transpose(a, z, dst);
+            }
+            __syncthreads();
+        }
 
         // 1./2. per threshold pass: (a) cardinal pre-test of every group, the
         // survivors compacted with their pixel masks (entry: row << 9 | group
@@ -601,6 +765,54 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
                     if (!has_hi[i]) need_lo = 1;
                 __syncthreads();
                 if (!need_lo) break;
+            }
+            if (kBits) {
+                // bit-sliced: one item = 32 pixels of a tile row inside the border band
+                const int nch = (tw + 31) >> 5, sb = G.delta + 4;
+                const int items = max(r1 - r0, 0) * nch;
+                for (int base = warp * 32; base < items; base += kFastThreads) {
+                    const int it = base + lane;
+                    uint32_t bits = 0;
+                    int py = 0, px0 = 0;
+                    if (it < items) {
+                        const int rr = it / nch, m = it - rr * nch;
+                        py = r0 + rr;
+                        px0 = 32 * m;
+                        const int lo = min(max(plo - px0, 0), 32), hi = min(max(phi - px0, 0), 32);
+                        uint32_t valid = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & (lo >= 32 ? 0u : (0xFFFFFFFFu << lo));
+                        const uint8_t *strow = has_hi + div_small(py, cinv) * ncx;
+                        if (pass == 1 && valid)  // fallback pass: only cells without a corner (and not skipped)
+                            valid &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st == 0; });
+                        if (valid) {
+                            bits = bs_corners(planes, pstride, py, m, sb, eps) & valid;
+                            if (bits && pass == 0 && some_skipped)
+                                bits &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st != 2; });
+                        }
+                    }
+                    // warp-aggregated append of this iteration's corners
+                    const int cnt = __popc(bits);
+                    int incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                        if (lane >= o) incl += y;
+                    }
+                    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                    int start = 0;
+                    if (lane == 31 && total) start = atomicAdd(&n_corner, total);
+                    start = __shfl_sync(0xFFFFFFFFu, start, 31) + incl - cnt;
+                    if (bits) {
+                        const int crow = div_small(py, cinv) * ncx;
+                        do {
+                            const int j = __ffs(bits) - 1;
+                            bits &= bits - 1;
+                            const int px = px0 + j;
+                            clist[start++] = (uint16_t)((py << 7) | px);
+                            if (pass == 0) has_hi[crow + div_small(px, cinv)] = 1;
+                        } while (bits);
+                    }
+                }
+                continue;
             }
             const uint32_t e0 = (uint32_t)eps * 0x01010101u, e1 = (uint32_t)(eps + 1) * 0x01010101u;
             const int gstep_y = gw > 0 ? kFastThreads / gw : 0, gstep_x = kFastThreads - gstep_y * gw;
@@ -734,35 +946,41 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
     }
 }
 
-int fast_smem_bytes(int max_box, int max_px, int max_cells, int k)
+int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, int max_planes)
 {
-    return fast_layout(max_box, max_px, max_cells, k).total;
+    return fast_layout(max_box, max_px, max_cells, k, max_planes).total;
 }
 
 cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream)
 {
     if (b.fast_tiles == 0) return cudaSuccess;
-    static int cached_smem = -1, cached_blocks = 0, n_sm = 0;
+    static int cached_smem = -1, cached_blocks = 0, n_sm = 0, cached_bits = -1;
     cudaError_t e;
     if (n_sm == 0) {
         int dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     }
-    if (cached_smem != b.fast_smem) {
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, k_fast_cull, kFastThreads,
-                                                               b.fast_smem)) != cudaSuccess)
-            return e;
+    if (cached_smem != b.fast_smem || cached_bits != b.fast_bits) {
+        e = b.fast_bits ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, k_fast_cull<true>,
+                                                                         kFastThreads, b.fast_smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, k_fast_cull<false>,
+                                                                         kFastThreads, b.fast_smem);
+        if (e != cudaSuccess) return e;
         cached_smem = b.fast_smem;
+        cached_bits = b.fast_bits;
     }
     const int grid = std::min(b.fast_tiles, std::max(1, cached_blocks) * n_sm);
-    k_fast_cull<<<grid, kFastThreads, b.fast_smem, stream>>>(b);
+    if (b.fast_bits) k_fast_cull<true><<<grid, kFastThreads, b.fast_smem, stream>>>(b);
+    else k_fast_cull<false><<<grid, kFastThreads, b.fast_smem, stream>>>(b);
     return cudaGetLastError();
 }
 
 cudaError_t configure_kernels()
 {
-    return cudaFuncSetAttribute(k_fast_cull, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_fast_cull<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_fast_cull<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace jslam
