@@ -287,17 +287,15 @@ constexpr uint32_t kH = 0x80808080u, kL7 = 0x7F7F7F7Fu;
 __device__ __forceinline__ uint32_t maj3(uint32_t a, uint32_t b, uint32_t c) { return (a & b) | (c & (a | b)); }
 
 struct FastLayout {
-    int buf0, buf1, clist, ckey, cand, planes, has_hi, sel, bar, total;
+    int buf0, buf1, clist, ckey, cand, has_hi, sel, bar, total;
 };
 
 __host__ __device__ inline int fast_align(int v, int a) { return (v + a - 1) / a * a; }
 
 // A group is 4 pixels of a row; a tile of max_px pixels whose rows hold at
 // most kFastMaxTile pixels has at most max_px / 4 + kFastMaxTile groups.
-// `cand` lists the groups that pass the cardinal pre-test (table path);
-// `planes` holds the bit-planes of the tile box (bit-sliced path, max_planes
-// bytes: box rows x (chunks + 1) x 8 words).
-__host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int max_cells, int k, int max_planes)
+// `cand` lists the groups that pass the cardinal pre-test.
+__host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int max_cells, int k)
 {
     FastLayout l;
     int o = kLutWords * 4;
@@ -305,11 +303,35 @@ __host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int m
     l.buf1 = o;  o += fast_align(max_box, 128);
     l.clist = o; o += fast_align(max_px * 2, 16);
     l.ckey = o;  o += k > 1 ? fast_align(max_px * 4, 16) : 0;
-    l.cand = o;  o += max_planes > 0 ? 0 : fast_align((max_px / 4 + kFastMaxTile) * 2, 16);
-    l.planes = o; o += fast_align(max_planes, 16);
+    l.cand = o;  o += fast_align((max_px / 4 + kFastMaxTile) * 2, 16);
     l.has_hi = o; o += fast_align(max_cells, 16);
     l.sel = o;   o += fast_align(max_cells * k * 4, 16);
     l.bar = o;   o += 16;
+    l.total = o;
+    return l;
+}
+
+// Shared memory of the bit-sliced kernel: the two tile boxes, the box's
+// bit-planes (max_planes bytes: box rows x (chunks + 1) x 8 words), one
+// window of corner entries per warp, and the corner list and keys only for
+// k > 1 (k = 1 takes each cell's best corner as it is found).
+constexpr int kBitsWin = 256;
+struct BitsLayout {
+    int buf0, buf1, planes, wbuf, clist, ckey, has_hi, sel, bar, total;
+};
+__host__ __device__ inline BitsLayout bits_layout(int max_box, int max_px, int max_cells, int k, int max_planes)
+{
+    BitsLayout l;
+    int o = 0;
+    l.buf0 = o;   o += fast_align(max_box, 128);
+    l.buf1 = o;   o += fast_align(max_box, 128);
+    l.planes = o; o += fast_align(max_planes, 16);
+    l.wbuf = o;   o += kFastThreads / 32 * kBitsWin * 2;
+    l.clist = o;  o += k > 1 ? fast_align(max_px * 2, 16) : 0;
+    l.ckey = o;   o += k > 1 ? fast_align(max_px * 4, 16) : 0;
+    l.has_hi = o; o += fast_align(max_cells, 16);
+    l.sel = o;    o += fast_align(max_cells * k * 4, 16);
+    l.bar = o;    o += 16;
     l.total = o;
     return l;
 }
@@ -623,22 +645,19 @@ __device__ __forceinline__ uint32_t cell_bits(const uint8_t *st, int px0, int tw
 
 __device__ __forceinline__ int div_small(int v, uint32_t cinv) { return (int)(((uint32_t)v * cinv) >> 16); }
 
-// kBits: the bit-sliced ring test (P_min = 9, P_max = 13); otherwise the
-// byte-lane test with the cardinal pre-test and the corner table (any
+// Byte-lane ring test with the cardinal pre-test and the corner table (any
 // P_min, P_max).
-template <bool kBits>
 __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int n_corner, need_lo, n_skipped, n_cand[2];
     const int k = b.prm.k, border = b.prm.border, p_min = b.prm.p_min;
-    const FastLayout lay = fast_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k, kBits ? b.fast_max_planes : 0);
+    const FastLayout lay = fast_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k);
     uint32_t *lut = reinterpret_cast<uint32_t *>(smem);
     uint8_t *const buf0 = smem + lay.buf0, *const buf1 = smem + lay.buf1;
     uint16_t *clist = reinterpret_cast<uint16_t *>(smem + lay.clist);
     uint32_t *ckey = reinterpret_cast<uint32_t *>(smem + lay.ckey);
     uint16_t *cand = reinterpret_cast<uint16_t *>(smem + lay.cand);
-    uint32_t *planes = reinterpret_cast<uint32_t *>(smem + lay.planes);
     uint8_t *has_hi = smem + lay.has_hi;
     uint32_t *sel = reinterpret_cast<uint32_t *>(smem + lay.sel);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
@@ -733,25 +752,6 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
         const int gw = max(g1 - g0, 0), nitems = max(r1 - r0, 0) * gw;
         // word of tile column 0 (pixel x0 - 4) within a box row
         const uint32_t *words = reinterpret_cast<const uint32_t *>(tb) + (G.delta >> 2);
-        // bit-sliced path: bit-planes of the whole box, one 32-byte chunk per
-        // thread, plus a zero chunk closing every row (rows are a multiple of
-        // 16 bytes, so a row's last chunk may hold only 16)
-        const int nbc = (rowb + 31) >> 5, pstride = nbc + 1;
-        if (kBits && !all_skipped) {
-            for (int ci = threadIdx.x; ci < L.box_h * pstride; ci += kFastThreads) {
-                const int r = ci / pstride, kc = ci - r * pstride;
-                uint4 a = make_uint4(0u, 0u, 0u, 0u), z = a;
-                if (kc < nbc) {
-                    const uint4 *src = reinterpret_cast<const uint4 *>(tb + r * rowb + 32 * kc);
-                    a = src[0];
-                    if (32 * kc + 16 < rowb) z = src[1];
-                }
-                uint4 *dst = reinterpret_cast<uint4 *>(planes + ci * 8);
-                bs_transpose(a, z, dst);
-            }
-            __syncthreads();
-        }
-
         // 1./2. per threshold pass: (a) cardinal pre-test of every group, the
         // survivors compacted with their pixel masks (entry: row << 9 | group
         // << 4 | mask); (b) full ring test of the survivors, corners pushed to
@@ -765,54 +765,6 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
                     if (!has_hi[i]) need_lo = 1;
                 __syncthreads();
                 if (!need_lo) break;
-            }
-            if (kBits) {
-                // bit-sliced: one item = 32 pixels of a tile row inside the border band
-                const int nch = (tw + 31) >> 5, sb = G.delta + 4;
-                const int items = max(r1 - r0, 0) * nch;
-                for (int base = warp * 32; base < items; base += kFastThreads) {
-                    const int it = base + lane;
-                    uint32_t bits = 0;
-                    int py = 0, px0 = 0;
-                    if (it < items) {
-                        const int rr = it / nch, m = it - rr * nch;
-                        py = r0 + rr;
-                        px0 = 32 * m;
-                        const int lo = min(max(plo - px0, 0), 32), hi = min(max(phi - px0, 0), 32);
-                        uint32_t valid = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & (lo >= 32 ? 0u : (0xFFFFFFFFu << lo));
-                        const uint8_t *strow = has_hi + div_small(py, cinv) * ncx;
-                        if (pass == 1 && valid)  // fallback pass: only cells without a corner (and not skipped)
-                            valid &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st == 0; });
-                        if (valid) {
-                            bits = bs_corners(planes, pstride, py, m, sb, eps) & valid;
-                            if (bits && pass == 0 && some_skipped)
-                                bits &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st != 2; });
-                        }
-                    }
-                    // warp-aggregated append of this iteration's corners
-                    const int cnt = __popc(bits);
-                    int incl = cnt;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                        if (lane >= o) incl += y;
-                    }
-                    const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                    int start = 0;
-                    if (lane == 31 && total) start = atomicAdd(&n_corner, total);
-                    start = __shfl_sync(0xFFFFFFFFu, start, 31) + incl - cnt;
-                    if (bits) {
-                        const int crow = div_small(py, cinv) * ncx;
-                        do {
-                            const int j = __ffs(bits) - 1;
-                            bits &= bits - 1;
-                            const int px = px0 + j;
-                            clist[start++] = (uint16_t)((py << 7) | px);
-                            if (pass == 0) has_hi[crow + div_small(px, cinv)] = 1;
-                        } while (bits);
-                    }
-                }
-                continue;
             }
             const uint32_t e0 = (uint32_t)eps * 0x01010101u, e1 = (uint32_t)(eps + 1) * 0x01010101u;
             const int gstep_y = gw > 0 ? kFastThreads / gw : 0, gstep_x = kFastThreads - gstep_y * gw;
@@ -946,9 +898,245 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
     }
 }
 
+// Bit-sliced ring test (P_min = 9, P_max = 13), the same results as
+// k_fast_cull.  Per tile: cell states, tile bytes, bit-planes, one barrier;
+// each threshold pass classifies 32 pixels of a row per thread, and every
+// warp scores its own corners right away through a window of entries in
+// shared memory (k = 1: atomic maximum of the cell's key; k > 1: corner list
+// for the top-k rounds); a barrier ends each pass.  The counters of a tile
+// live in one of two sets by tile parity, so the set of the next tile is
+// cleared while the current one is in use, without a barrier of its own.
+__global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
+{
+    extern __shared__ __align__(128) uint8_t smem[];
+    // per set: corners listed (k > 1), skipped cells, cells open at the
+    // start (state 0), open cells that got a primary-threshold corner
+    __shared__ int cnt[2][4];
+    const int k = b.prm.k, border = b.prm.border;
+    const BitsLayout lay = bits_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k, b.fast_max_planes);
+    uint8_t *const buf0 = smem + lay.buf0, *const buf1 = smem + lay.buf1;
+    uint32_t *planes = reinterpret_cast<uint32_t *>(smem + lay.planes);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint16_t *wbuf = reinterpret_cast<uint16_t *>(smem + lay.wbuf) + warp * kBitsWin;
+    uint16_t *clist = reinterpret_cast<uint16_t *>(smem + lay.clist);
+    uint32_t *ckey = reinterpret_cast<uint32_t *>(smem + lay.ckey);
+    uint8_t *has_hi = smem + lay.has_hi;
+    uint32_t *sel = reinterpret_cast<uint32_t *>(smem + lay.sel);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
+
+    if ((smem_u32(buf0) | smem_u32(buf1)) & 127u) {
+        if (threadIdx.x == 0) atomicOr(b.err, kErrDecode);
+        return;
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (threadIdx.x < 8) cnt[threadIdx.x >> 2][threadIdx.x & 3] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0 && blockIdx.x < b.fast_tiles) issue_tile(b, blockIdx.x, buf0, &bars[0]);
+    uint32_t phase0 = 0u, phase1 = 0u;
+
+    int it = 0;
+    for (int t = blockIdx.x; t < b.fast_tiles; t += gridDim.x, ++it) {
+        const int cur = it & 1;
+        int *const C = cnt[cur];
+        const TileGeom G = tile_geom(b, t);
+        const LevelDesc &L = b.levels[G.li];
+        const ImageDesc &I = b.images[L.image];
+        if (threadIdx.x == 0) {
+            // the buffer's and the other set's readers finished at the barrier
+            // that ended the previous tile
+            if (t + (int)gridDim.x < b.fast_tiles) issue_tile(b, t + gridDim.x, cur ? buf0 : buf1, &bars[cur ^ 1]);
+            cnt[cur ^ 1][0] = cnt[cur ^ 1][1] = cnt[cur ^ 1][2] = cnt[cur ^ 1][3] = 0;
+        }
+        const int c = L.c, cells_x = L.cells_x, W = L.W, Hh = L.H;
+        const uint32_t cinv = (uint32_t)L.cinv;
+        const int ncx = G.ncx, x0 = G.x0, y0 = G.y0, tw = G.tw, th = G.th;
+        const int rowb = L.box_w;
+        const int cells = ncx * G.ncy;
+        uint8_t *tb = cur ? buf1 : buf0;
+
+        // cell states (as in k_fast_cull) and cleared selections: they do
+        // not depend on the tile bytes, so they go before the tile wait
+        int my_skipped = 0, my_open = 0;
+        for (int i = threadIdx.x; i < cells; i += kFastThreads) {
+            const int lcy = i / ncx, lcx = i - lcy * ncx;
+            const int cx0 = (G.ccx0 + lcx) * c, cy0 = (G.ccy0 + lcy) * c;
+            const bool evaluated = cx0 + c > border && cx0 < W - border && cy0 + c > border && cy0 < Hh - border;
+            uint8_t st = evaluated ? 0 : 3;
+            if (I.skip && evaluated) {
+                const int px = min(cx0 + c / 2, W - 1), py = min(cy0 + c / 2, Hh - 1);
+                const int X = __ldg(L.projx + px), Y = __ldg(L.projy + py);
+                st = I.skip[(Y / I.skip_c0) * I.skip_cells_x + X / I.skip_c0] ? 2 : 0;
+            }
+            if (I.skip && st != 0) { st = 2; ++my_skipped; }
+            my_open += st == 0;
+            has_hi[i] = st;
+        }
+        for (int i = threadIdx.x; i < cells * k; i += kFastThreads) sel[i] = 0;
+        if (my_skipped) atomicAdd(&C[1], my_skipped);
+        if (my_open) atomicAdd(&C[2], my_open);
+        if (I.skip) __syncthreads();  // uniform: a tile whose cells are all skipped builds no planes
+        const bool all_skipped = I.skip && C[1] == cells;
+
+        if (L.tmap) {
+            if (!wait_tile(&bars[cur], cur ? phase1 : phase0)) {
+                if (threadIdx.x == 0) atomicOr(b.err, kErrTimeout);
+                return;
+            }
+            if (cur) phase1 ^= 1u; else phase0 ^= 1u;
+        } else {
+            const int wpr = rowb >> 2;
+            uint32_t *tw32 = reinterpret_cast<uint32_t *>(tb);
+            for (int i = threadIdx.x; i < L.box_h * wpr; i += kFastThreads) {
+                const int r = i / wpr, wi = i - r * wpr;
+                const uint8_t *row = L.raw + (size_t)min(max(G.ys + r, 0), Hh - 1) * L.pitch;
+                const int gx = G.xs + 4 * wi;
+                uint32_t v = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v |= (uint32_t)__ldg(row + min(max(gx + q, 0), W - 1)) << (8 * q);
+                tw32[i] = v;
+            }
+            __syncthreads();
+        }
+        // bit-planes of the box, one 32-byte chunk per thread, plus a zero
+        // chunk closing every row (a row's last chunk may hold only 16 bytes)
+        const int nbc = (rowb + 31) >> 5, pstride = nbc + 1;
+        if (!all_skipped) {
+            for (int ci = threadIdx.x; ci < L.box_h * pstride; ci += kFastThreads) {
+                const int r = ci / pstride, kc = ci - r * pstride;
+                uint4 a = make_uint4(0u, 0u, 0u, 0u), z = a;
+                if (kc < nbc) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(tb + r * rowb + 32 * kc);
+                    a = src[0];
+                    if (32 * kc + 16 < rowb) z = src[1];
+                }
+                bs_transpose(a, z, reinterpret_cast<uint4 *>(planes + ci * 8));
+            }
+        }
+        __syncthreads();
+        const bool some_skipped = C[1] > 0;
+
+        const int plo = max(border - x0, 0), phi = min(W - border - x0, tw);
+        const int r0 = max(border - y0, 0), r1 = min(Hh - border - y0, th);
+        const int nch = (tw + 31) >> 5, sb = G.delta + 4;
+        const int items = max(r1 - r0, 0) * nch;
+        const uint8_t *tbytes = tb + G.delta;  // pixel (x, y) at (y - y0 + 3) * rowb + (x - x0 + 4)
+        for (int pass = 0; pass < 2 && !all_skipped; ++pass) {
+            const int eps = pass == 0 ? I.eps_hi : I.eps_lo;
+            // fallback pass only while an open cell got no corner
+            if (pass == 1 && (eps <= 0 || C[3] >= C[2])) break;
+            for (int base = warp * 32; base < items; base += kFastThreads) {
+                const int itm = base + lane;
+                uint32_t bits = 0;
+                int py = 0, px0 = 0;
+                if (itm < items) {
+                    const int rr = itm / nch, m = itm - rr * nch;
+                    py = r0 + rr;
+                    px0 = 32 * m;
+                    const int lo = min(max(plo - px0, 0), 32), hi = min(max(phi - px0, 0), 32);
+                    uint32_t valid = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & (lo >= 32 ? 0u : (0xFFFFFFFFu << lo));
+                    const uint8_t *strow = has_hi + div_small(py, cinv) * ncx;
+                    if (pass == 1 && valid)  // only cells without a corner (and not skipped)
+                        valid &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st == 0; });
+                    if (valid) {
+                        bits = bs_corners(planes, pstride, py, m, sb, eps) & valid;
+                        if (bits && pass == 0 && some_skipped)
+                            bits &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st != 2; });
+                    }
+                }
+                // the warp's corners in order, scored through windows of kBitsWin entries
+                const int nb = __popc(bits);
+                int incl = nb;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+                const int crow = div_small(py, cinv) * ncx;
+                for (int w0 = 0; w0 < total; w0 += kBitsWin) {
+                    uint32_t bb = bits;
+                    for (int id = incl - nb; bb && id < w0 + kBitsWin; ++id) {
+                        const int j = __ffs(bb) - 1;
+                        bb &= bb - 1;
+                        if (id < w0) continue;
+                        const int px = px0 + j;
+                        wbuf[id - w0] = (uint16_t)((py << 7) | px);
+                        if (pass == 0) {
+                            const int cell = crow + div_small(px, cinv);
+                            if (has_hi[cell] == 0) {
+                                // first corner of an open cell: mark it and count it once
+                                const uint32_t sh = 8u * (uint32_t)(cell & 3);
+                                const uint32_t old = atomicOr(reinterpret_cast<uint32_t *>(has_hi) + (cell >> 2), 1u << sh);
+                                if (((old >> sh) & 0xFFu) == 0u) atomicAdd(&C[3], 1);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    const int n = min(total - w0, kBitsWin);
+                    int lbase = 0;
+                    if (k > 1) {
+                        if (lane == 0) lbase = atomicAdd(&C[0], n);
+                        lbase = __shfl_sync(0xFFFFFFFFu, lbase, 0);
+                    }
+                    for (int i = lane; i < n; i += 32) {
+                        const int e = wbuf[i];
+                        const int cy_ = e >> 7, cx_ = e & 127;
+                        const uint8_t *pp = tbytes + (cy_ + 3) * rowb + (cx_ + 4);
+                        const int ic = pp[0];
+                        int r = 0;
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) r += abs((int)pp[c_ring_dy[q] * rowb + c_ring_dx[q]] - ic);
+                        const int ccy = div_small(cy_, cinv), ccx = div_small(cx_, cinv);
+                        const uint32_t inidx = (uint32_t)((cy_ - ccy * c) * c + (cx_ - ccx * c));
+                        const uint32_t key = ((uint32_t)r << 16) | (0xFFFFu - inidx);
+                        if (k == 1) atomicMax(&sel[ccy * ncx + ccx], key);
+                        else { clist[lbase + i] = (uint16_t)e; ckey[lbase + i] = key; }
+                    }
+                    __syncwarp();
+                }
+            }
+            __syncthreads();  // selections, marks and counts of this pass complete
+        }
+        if (k > 1) {
+            const int nc = C[0];
+            for (int j = 0; j < k; ++j) {
+                for (int i = threadIdx.x; i < nc; i += kFastThreads) {
+                    const int e = clist[i];
+                    const int cell = div_small(e >> 7, cinv) * ncx + div_small(e & 127, cinv);
+                    const uint32_t key = ckey[i];
+                    if (j == 0 || key < sel[cell * k + j - 1]) atomicMax(&sel[cell * k + j], key);
+                }
+                __syncthreads();
+            }
+        }
+
+        // slots and the s0 score map (as in k_fast_cull)
+        for (int e = threadIdx.x; e < cells * k; e += kFastThreads) {
+            const int cell = e / k, j = e - cell * k;
+            const int lcy = cell / ncx;
+            const int gcx = G.ccx0 + cell - lcy * ncx, gcy = G.ccy0 + lcy;
+            const uint32_t key = sel[e];
+            b.slots[L.slot_base + (gcy * cells_x + gcx) * k + j] = key;
+            if (key) {
+                const int inidx = 0xFFFF - (int)(key & 0xFFFFu);
+                const int x = gcx * c + inidx % c, y = gcy * c + inidx / c;
+                if (x >= W || y >= Hh) { atomicOr(b.err, kErrDecode); continue; }
+                const int X = __ldg(L.projx + x), Y = __ldg(L.projy + y);
+                atomicAdd(I.map + (size_t)Y * I.W0 + X, (1u << 16) + (key >> 16));
+            }
+        }
+        __syncthreads();  // every reader of this buffer, the planes and this set is done
+    }
+}
+
 int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, int max_planes)
 {
-    return fast_layout(max_box, max_px, max_cells, k, max_planes).total;
+    return max_planes > 0 ? bits_layout(max_box, max_px, max_cells, k, max_planes).total
+                          : fast_layout(max_box, max_px, max_cells, k).total;
 }
 
 cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream)
@@ -962,25 +1150,25 @@ cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream)
         if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     }
     if (cached_smem != b.fast_smem || cached_bits != b.fast_bits) {
-        e = b.fast_bits ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, k_fast_cull<true>,
-                                                                         kFastThreads, b.fast_smem)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, k_fast_cull<false>,
-                                                                         kFastThreads, b.fast_smem);
+        e = b.fast_bits ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, k_fast_bits, kFastThreads,
+                                                                         b.fast_smem)
+                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, k_fast_cull, kFastThreads,
+                                                                         b.fast_smem);
         if (e != cudaSuccess) return e;
         cached_smem = b.fast_smem;
         cached_bits = b.fast_bits;
     }
     const int grid = std::min(b.fast_tiles, std::max(1, cached_blocks) * n_sm);
-    if (b.fast_bits) k_fast_cull<true><<<grid, kFastThreads, b.fast_smem, stream>>>(b);
-    else k_fast_cull<false><<<grid, kFastThreads, b.fast_smem, stream>>>(b);
+    if (b.fast_bits) k_fast_bits<<<grid, kFastThreads, b.fast_smem, stream>>>(b);
+    else k_fast_cull<<<grid, kFastThreads, b.fast_smem, stream>>>(b);
     return cudaGetLastError();
 }
 
 cudaError_t configure_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fast_cull<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_fast_bits, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_fast_cull<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return cudaFuncSetAttribute(k_fast_cull, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 }  // namespace jslam
