@@ -564,24 +564,38 @@ __device__ __forceinline__ uint32_t bs_add_const(const uint32_t (&c)[8], uint32_
     return k;
 }
 
-// Longest circular run of the 16 flag words in [9, 13]: a run of 9 is a
-// window of 8 and the position after it; of 14: windows of 8, 4 and 2.
+// Longest circular run of the 16 flag words in [9, 13], with three-input
+// ANDs: A3 = windows of 3, A9 = three A3 end to end, a run of 14 = an A9
+// followed by two overlapping A3 (positions q + 9 .. q + 13).
 __device__ __forceinline__ uint32_t bs_run_9_13(const uint32_t (&F)[16])
 {
-    uint32_t A2[16], A4[16], A8[16];
+    uint32_t A3[16];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) A2[q] = F[q] & F[(q + 1) & 15];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) A4[q] = A2[q] & A2[(q + 2) & 15];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) A8[q] = A4[q] & A4[(q + 4) & 15];
+    for (int q = 0; q < 16; ++q) A3[q] = F[q] & F[(q + 1) & 15] & F[(q + 2) & 15];
     uint32_t r9 = 0, r14 = 0;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-        r9 |= A8[q] & F[(q + 8) & 15];
-        r14 |= A8[q] & A4[(q + 8) & 15] & A2[(q + 12) & 15];
+        const uint32_t a9 = A3[q] & A3[(q + 3) & 15] & A3[(q + 6) & 15];
+        r9 |= a9;
+        r14 |= a9 & A3[(q + 9) & 15] & A3[(q + 11) & 15];
     }
     return r9 & ~r14;
+}
+
+// Bounded-rectification response of the pixel at p (rows rowb bytes apart):
+// the sum of |ring pixel - centre| over the 16 ring positions, the ring
+// bytes packed four to a word (rows +-3: dx = -1, 0, 1; rows +-2: dx = +-2;
+// rows +-1 and 0: dx = +-3) and summed by byte-SIMD absolute differences.
+__device__ __forceinline__ int ring_sad(const uint8_t *p, int rowb)
+{
+    const uint8_t *u3 = p + 3 * rowb, *d3 = p - 3 * rowb, *u2 = p + 2 * rowb, *d2 = p - 2 * rowb;
+    const uint8_t *u1 = p + rowb, *d1 = p - rowb;
+    const uint32_t w0 = (uint32_t)u3[-1] | ((uint32_t)u3[0] << 8) | ((uint32_t)u3[1] << 16) | ((uint32_t)d3[-1] << 24);
+    const uint32_t w1 = (uint32_t)d3[0] | ((uint32_t)d3[1] << 8) | ((uint32_t)u2[-2] << 16) | ((uint32_t)u2[2] << 24);
+    const uint32_t w2 = (uint32_t)d2[-2] | ((uint32_t)d2[2] << 8) | ((uint32_t)u1[-3] << 16) | ((uint32_t)u1[3] << 24);
+    const uint32_t w3 = (uint32_t)d1[-3] | ((uint32_t)d1[3] << 8) | ((uint32_t)p[-3] << 16) | ((uint32_t)p[3] << 24);
+    const uint32_t cc = (uint32_t)p[0] * 0x01010101u;
+    return (int)(__vsadu4(w0, cc) + __vsadu4(w1, cc) + __vsadu4(w2, cc) + __vsadu4(w3, cc));
 }
 
 // Corner bits of the 32 pixels of tile row py, chunk m (pixels 32 m + j).
@@ -600,13 +614,19 @@ __device__ __forceinline__ uint32_t bs_corners(const uint32_t *planes, int pstri
 #pragma unroll
         for (int i = 0; i < 8; ++i) C[i] = __funnelshift_r(lo[i], hi[i], sb);
     }
-    const uint32_t nb = bs_add_const(C, (uint32_t)eps, Tb);      // C + eps >= 256: never brighter
-    uint32_t nd = 0;                                              // C < eps: never darker
-    if (eps > 0) nd = ~bs_add_const(C, (uint32_t)(256 - eps), Td);
-    else {
+    // a centre with C + eps >= 256 is never brighter (threshold 255, which
+    // no P exceeds); one with C < eps never darker (threshold 0)
+    const uint32_t nb = bs_add_const(C, (uint32_t)eps, Tb);
+    if (eps > 0) {
+        const uint32_t nd = ~bs_add_const(C, (uint32_t)(256 - eps), Td);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) Td[i] &= ~nd;
+    } else {
 #pragma unroll
         for (int i = 0; i < 8; ++i) Td[i] = C[i];
     }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) Tb[i] |= nb;
     uint32_t Fb[16], Fd[16];
 #pragma unroll
     for (int dy = 3; dy >= -3; --dy) {
@@ -620,8 +640,8 @@ __device__ __forceinline__ uint32_t bs_corners(const uint32_t *planes, int pstri
             uint32_t P[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) P[i] = __funnelshift_r(lo[i], hi[i], sb + RDX[q]);
-            Fb[q] = bs_greater(P, Tb) & ~nb;
-            Fd[q] = bs_greater(Td, P) & ~nd;
+            Fb[q] = bs_greater(P, Tb);
+            Fd[q] = bs_greater(Td, P);
         }
     }
     return bs_run_9_13(Fb) | bs_run_9_13(Fd);
@@ -1001,27 +1021,30 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
             }
             __syncthreads();
         }
-        // bit-planes of the box, one 32-byte chunk per thread, plus a zero
-        // chunk closing every row (a row's last chunk may hold only 16 bytes)
+        // bit-planes of the box rows [r0, r1 + 6) that the evaluated rows
+        // [r0, r1) read, chunks 0..nch (an item of chunk m reads m and m + 1),
+        // one 32-byte chunk per thread; chunks at or past the box's end
+        // (a row's last may hold only 16 bytes) are zero
+        const int plo = max(border - x0, 0), phi = min(W - border - x0, tw);
+        const int r0 = max(border - y0, 0), r1 = min(Hh - border - y0, th);
+        const int nch = (tw + 31) >> 5, sb = G.delta + 4;
         const int nbc = (rowb + 31) >> 5, pstride = nbc + 1;
         if (!all_skipped) {
-            for (int ci = threadIdx.x; ci < L.box_h * pstride; ci += kFastThreads) {
-                const int r = ci / pstride, kc = ci - r * pstride;
+            const int nrows = max(r1 - r0, 0) > 0 ? r1 - r0 + 6 : 0;
+            for (int ci = threadIdx.x; ci < nrows * (nch + 1); ci += kFastThreads) {
+                const int rr = ci / (nch + 1), kc = ci - rr * (nch + 1), r = r0 + rr;
                 uint4 a = make_uint4(0u, 0u, 0u, 0u), z = a;
                 if (kc < nbc) {
                     const uint4 *src = reinterpret_cast<const uint4 *>(tb + r * rowb + 32 * kc);
                     a = src[0];
                     if (32 * kc + 16 < rowb) z = src[1];
                 }
-                bs_transpose(a, z, reinterpret_cast<uint4 *>(planes + ci * 8));
+                bs_transpose(a, z, reinterpret_cast<uint4 *>(planes + (r * pstride + kc) * 8));
             }
         }
         __syncthreads();
         const bool some_skipped = C[1] > 0;
 
-        const int plo = max(border - x0, 0), phi = min(W - border - x0, tw);
-        const int r0 = max(border - y0, 0), r1 = min(Hh - border - y0, th);
-        const int nch = (tw + 31) >> 5, sb = G.delta + 4;
         const int items = max(r1 - r0, 0) * nch;
         const uint8_t *tbytes = tb + G.delta;  // pixel (x, y) at (y - y0 + 3) * rowb + (x - x0 + 4)
         for (int pass = 0; pass < 2 && !all_skipped; ++pass) {
@@ -1056,24 +1079,28 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
                     if (lane >= o) incl += y;
                 }
                 const int total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-                const int crow = div_small(py, cinv) * ncx;
+                if (pass == 0 && bits) {
+                    // mark the open cells that got a corner, each counted once
+                    const int crow = div_small(py, cinv) * ncx;
+                    const int ca = div_small(px0 + __ffs(bits) - 1, cinv), cz = div_small(px0 + 31 - __clz(bits), cinv);
+                    for (int cx = ca; cx <= cz; ++cx) {
+                        const int a = max(cx * c - px0, 0), z = min((cx + 1) * c - px0, 32);
+                        const uint32_t span = (z >= 32 ? 0xFFFFFFFFu : ((1u << z) - 1u)) & (0xFFFFFFFFu << a);
+                        const int cell = crow + cx;
+                        if ((bits & span) && has_hi[cell] == 0) {
+                            const uint32_t sh = 8u * (uint32_t)(cell & 3);
+                            const uint32_t old = atomicOr(reinterpret_cast<uint32_t *>(has_hi) + (cell >> 2), 1u << sh);
+                            if (((old >> sh) & 0xFFu) == 0u) atomicAdd(&C[3], 1);
+                        }
+                    }
+                }
+                const int ebase = (py << 7) | px0;  // entry of pixel px0 + j: ebase + j
                 for (int w0 = 0; w0 < total; w0 += kBitsWin) {
                     uint32_t bb = bits;
                     for (int id = incl - nb; bb && id < w0 + kBitsWin; ++id) {
                         const int j = __ffs(bb) - 1;
                         bb &= bb - 1;
-                        if (id < w0) continue;
-                        const int px = px0 + j;
-                        wbuf[id - w0] = (uint16_t)((py << 7) | px);
-                        if (pass == 0) {
-                            const int cell = crow + div_small(px, cinv);
-                            if (has_hi[cell] == 0) {
-                                // first corner of an open cell: mark it and count it once
-                                const uint32_t sh = 8u * (uint32_t)(cell & 3);
-                                const uint32_t old = atomicOr(reinterpret_cast<uint32_t *>(has_hi) + (cell >> 2), 1u << sh);
-                                if (((old >> sh) & 0xFFu) == 0u) atomicAdd(&C[3], 1);
-                            }
-                        }
+                        if (id >= w0) wbuf[id - w0] = (uint16_t)(ebase + j);
                     }
                     __syncwarp();
                     const int n = min(total - w0, kBitsWin);
@@ -1086,10 +1113,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
                         const int e = wbuf[i];
                         const int cy_ = e >> 7, cx_ = e & 127;
                         const uint8_t *pp = tbytes + (cy_ + 3) * rowb + (cx_ + 4);
-                        const int ic = pp[0];
-                        int r = 0;
-#pragma unroll
-                        for (int q = 0; q < 16; ++q) r += abs((int)pp[c_ring_dy[q] * rowb + c_ring_dx[q]] - ic);
+                        const int r = ring_sad(pp, rowb);
                         const int ccy = div_small(cy_, cinv), ccx = div_small(cx_, cinv);
                         const uint32_t inidx = (uint32_t)((cy_ - ccy * c) * c + (cx_ - ccx * c));
                         const uint32_t key = ((uint32_t)r << 16) | (0xFFFFu - inidx);
