@@ -318,7 +318,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 int bw, bh;
                 detect_box(tw, th, &bw, &bh);
                 max_box = std::max(max_box, bw * bh);
-                max_planes = std::max(max_planes, bh * ((bw + 31) / 32 + 1) * 32);
+                max_planes = std::max(max_planes, bh * bs_row_units((tw + 31) / 32) * 16);
                 max_px = std::max(max_px, tw * th);
                 max_cells = std::max(max_cells, bx * by);
             }
@@ -375,6 +375,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
             n_fast_tiles += 2 * (size_t)(((cx + bx - 1) / bx) * ((cy + by - 1) / by));
         }
     const size_t o_ftl = reserve(sizeof(int32_t) * (n_fast_tiles + 1));
+    const size_t o_trec = reserve(sizeof(TileRec) * (n_fast_tiles + 1));
     const size_t o_lstart = reserve(sizeof(int32_t) * (kMaxLevels + 1) * n_img);
     const size_t o_tmaps = reserve(sizeof(CUtensorMap) * (size_t)n_levels);
     const size_t o_tables = reserve(table_bytes + 256);
@@ -525,6 +526,46 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     fast_base[n_levels] = fast;
     seg_level[n_segs] = n_levels - 1;
 
+    // detection tile records (the device-side tile geometry, evaluated here)
+    auto trec = reinterpret_cast<TileRec *>(host.data() + o_trec);
+    for (int l = 0; l < n_levels; ++l) {
+        const LevelDesc &L = levels[l];
+        const ImageDesc &I = images[L.image];
+        const int ctas_x = (L.cells_x + L.bx - 1) / L.bx;
+        for (int t = fast_base[l]; t < fast_base[l + 1]; ++t) {
+            TileRec &R = trec[t];
+            const int tt = t - fast_base[l], ty = tt / ctas_x;
+            R.ccx0 = (tt - ty * ctas_x) * L.bx;
+            R.ccy0 = ty * L.by;
+            R.ncx = std::min(L.bx, L.cells_x - R.ccx0);
+            R.ncy = std::min(L.by, L.cells_y - R.ccy0);
+            R.x0 = R.ccx0 * L.c;
+            R.y0 = R.ccy0 * L.c;
+            R.tw = std::min(R.ncx * L.c, L.W - R.x0);
+            R.th = std::min(R.ncy * L.c, L.H - R.y0);
+            R.xs = L.tmap ? ((R.x0 - 4) & ~15) : R.x0 - 4;
+            R.ys = R.y0 - 3;
+            R.delta = R.x0 - 4 - R.xs;
+            R.c = L.c; R.cells_x = L.cells_x; R.W = L.W; R.H = L.H; R.cinv = L.cinv;
+            R.box_w = L.box_w; R.box_h = L.box_h; R.slot_base = L.slot_base; R.pitch = L.pitch;
+            R.eps_hi = I.eps_hi; R.eps_lo = I.eps_lo; R.W0 = I.W0;
+            R.skip_c0 = I.skip_c0; R.skip_cells_x = I.skip_cells_x;
+            // projection ranges, widened to 16-byte boundaries (inside the
+            // level's table, whose size is rounded up to 16 bytes)
+            const uintptr_t ax = reinterpret_cast<uintptr_t>(L.projx + R.x0);
+            const uintptr_t ay = reinterpret_cast<uintptr_t>(L.projy + R.y0);
+            const uintptr_t bx0 = ax & ~(uintptr_t)15, by0 = ay & ~(uintptr_t)15;
+            R.prj_src_x = reinterpret_cast<const uint16_t *>(bx0);
+            R.prj_src_y = reinterpret_cast<const uint16_t *>(by0);
+            R.prj_off_x = (int)(ax - bx0) / 2;
+            R.prj_off_y = (int)(ay - by0) / 2;
+            R.prj_bytes_x = (int)align_up((size_t)(ax - bx0) + 2 * (size_t)R.tw, 16);
+            R.prj_bytes_y = (int)align_up((size_t)(ay - by0) + 2 * (size_t)R.th, 16);
+            R.pad_ = 0;
+            R.raw = L.raw; R.tmap = L.tmap; R.map = I.map; R.skip = I.skip;
+        }
+    }
+
     e = cudaMemcpyAsync(ctx->plan.ptr, host.data(), off, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return fail(ctx, e);
 
@@ -536,6 +577,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.fast_tile_base = reinterpret_cast<const int32_t *>(dplan + o_fast);
     b.seg_level = reinterpret_cast<const int32_t *>(dplan + o_seg);
     b.fast_tile_level = reinterpret_cast<const int32_t *>(dplan + o_ftl);
+    b.tile_rec = reinterpret_cast<const TileRec *>(dplan + o_trec);
     b.n_images = n_img; b.n_levels = n_levels; b.n_pairs = n; b.n_segments = n_segs;
     b.pyr_tiles = pyr; b.fast_tiles = fast; b.max_capacity = max_cap;
     b.fast_max_box = max_box; b.fast_max_px = max_px; b.fast_max_cells = max_cells;

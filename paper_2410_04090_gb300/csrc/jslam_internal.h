@@ -28,6 +28,12 @@ constexpr int kMaxImages = 256;    // images per batch (two per stereo pair)
 constexpr int kPyrTW = 128, kPyrTH = 32, kPyrThreads = 256;
 // Detection tile: at most this many pixels a side (host picks cells per CTA).
 constexpr int kFastMaxTile = 128, kFastThreads = 256;
+
+// Row stride of the bit-planes in 16-byte units for a tile of nch 32-pixel
+// chunks: chunks 0..nch (32 bytes each) and a 16-byte pad, an odd count, so
+// that the 128-bit loads of two neighbouring rows fall on the two halves of
+// the shared-memory banks.
+__host__ __device__ inline int bs_row_units(int nch) { return 2 * (nch + 1) + 1; }
 constexpr int kFastMaxCellsPerCta = 2048;  // cells x k per CTA
 constexpr int kLutWords = 2048;            // 2^16-entry corner bit table
 constexpr int kSkipC = 16;                 // channels of the learned cell-skip net
@@ -122,6 +128,27 @@ struct Inputs {
 };
 
 // Everything the kernels of one extraction need.
+// One detection tile of the bit-sliced kernel, prepared on the host: the
+// tile's place in its level, the level's and image's scalars, and the
+// 16-byte-aligned ranges of the level's s0 projection tables that cover the
+// tile's columns and rows.  The kernel copies it into shared memory with a
+// bulk copy, so no chain of descriptor loads precedes a tile.
+constexpr int kPrjBytes = 288;  // staged projection bytes per axis: 2 x 128 + alignment slack, rounded to 16
+struct __align__(16) TileRec {
+    int32_t ccx0, ccy0, ncx, ncy, x0, y0, tw, th, xs, ys, delta;
+    int32_t c, cells_x, W, H, cinv, box_w, box_h, slot_base, pitch;
+    int32_t eps_hi, eps_lo, W0, skip_c0, skip_cells_x;
+    int32_t prj_bytes_x, prj_bytes_y;  // bulk copy sizes (multiples of 16)
+    int32_t prj_off_x, prj_off_y;      // element offset of x0 / y0 in the staged copies
+    int32_t pad_;
+    const uint8_t *raw;
+    const CUtensorMap *tmap;           // nullptr: the box is loaded with plain loads
+    const uint16_t *prj_src_x, *prj_src_y;
+    uint32_t *map;
+    const uint8_t *skip;
+};
+static_assert(sizeof(TileRec) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
 struct Batch {
     const ImageDesc *images;
     const LevelDesc *levels;
@@ -137,6 +164,7 @@ struct Batch {
     int32_t fast_max_box, fast_max_px, fast_max_cells;  // its tile layout maxima
     int32_t fast_max_planes;        // bit-plane bytes of the largest tile box
     int32_t fast_bits;              // 1: bit-sliced ring test (P_min = 9, P_max = 13)
+    const TileRec *tile_rec;        // one per detection tile
     const uint32_t *corner_lut;     // bit m: P_min <= longest circular run of m <= P_max
     uint32_t *slots;                // candidate keys per slot
     uint32_t *slot_k;               // PFA scores seen by each slot

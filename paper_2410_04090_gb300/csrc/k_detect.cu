@@ -311,13 +311,15 @@ __host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int m
     return l;
 }
 
-// Shared memory of the bit-sliced kernel: the two tile boxes, the box's
-// bit-planes (max_planes bytes: box rows x (chunks + 1) x 8 words), one
-// window of corner entries per warp, and the corner list and keys only for
-// k > 1 (k = 1 takes each cell's best corner as it is found).
+// Dynamic shared memory of the bit-sliced kernel: the two tile boxes, the
+// box's bit-planes (max_planes bytes: box rows of (chunks + 1) x 8 words and
+// a 16-byte pad, see bs_row_units), the corner list and keys only for k > 1
+// (k = 1 takes each cell's best corner as it is found), cell states and
+// selections.  The fixed-size parts (corner windows, tile records, staged
+// projections, mbarriers) are static arrays of the kernel.
 constexpr int kBitsWin = 256;
 struct BitsLayout {
-    int buf0, buf1, planes, wbuf, clist, ckey, has_hi, sel, bar, total;
+    int buf0, buf1, planes, clist, ckey, has_hi, sel, total;
 };
 __host__ __device__ inline BitsLayout bits_layout(int max_box, int max_px, int max_cells, int k, int max_planes)
 {
@@ -326,12 +328,10 @@ __host__ __device__ inline BitsLayout bits_layout(int max_box, int max_px, int m
     l.buf0 = o;   o += fast_align(max_box, 128);
     l.buf1 = o;   o += fast_align(max_box, 128);
     l.planes = o; o += fast_align(max_planes, 16);
-    l.wbuf = o;   o += kFastThreads / 32 * kBitsWin * 2;
     l.clist = o;  o += k > 1 ? fast_align(max_px * 2, 16) : 0;
     l.ckey = o;   o += k > 1 ? fast_align(max_px * 4, 16) : 0;
     l.has_hi = o; o += fast_align(max_cells, 16);
     l.sel = o;    o += fast_align(max_cells * k * 4, 16);
-    l.bar = o;    o += 16;
     l.total = o;
     return l;
 }
@@ -599,15 +599,16 @@ __device__ __forceinline__ int ring_sad(const uint8_t *p, int rowb)
 }
 
 // Corner bits of the 32 pixels of tile row py, chunk m (pixels 32 m + j).
-// `planes`: box rows of `pstride` chunks of 8 words; tile pixel 0 sits at box
-// column sb, so pixel 32 m + j + dx is bit sb + dx + j of chunks (m, m + 1).
-__device__ __forceinline__ uint32_t bs_corners(const uint32_t *planes, int pstride, int py, int m, int sb, int eps)
+// `planes`: box rows of `ru` 16-byte units, chunk m at unit 2 m; tile pixel 0
+// sits at box column sb, so pixel 32 m + j + dx is bit sb + dx + j of chunks
+// (m, m + 1).
+__device__ __forceinline__ uint32_t bs_corners(const uint32_t *planes, int ru, int py, int m, int sb, int eps)
 {
     constexpr int RDX[16] = { 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1 };
     constexpr int RDY[16] = { 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1, 0, 1, 2, 3 };
     uint32_t C[8], Tb[8], Td[8];
     {
-        const uint4 *r = reinterpret_cast<const uint4 *>(planes + ((py + 3) * pstride + m) * 8);
+        const uint4 *r = reinterpret_cast<const uint4 *>(planes) + (py + 3) * ru + 2 * m;
         const uint4 l0 = r[0], l1 = r[1], h0 = r[2], h1 = r[3];
         const uint32_t lo[8] = { l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w };
         const uint32_t hi[8] = { h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w };
@@ -630,7 +631,7 @@ __device__ __forceinline__ uint32_t bs_corners(const uint32_t *planes, int pstri
     uint32_t Fb[16], Fd[16];
 #pragma unroll
     for (int dy = 3; dy >= -3; --dy) {
-        const uint4 *r = reinterpret_cast<const uint4 *>(planes + ((py + 3 + dy) * pstride + m) * 8);
+        const uint4 *r = reinterpret_cast<const uint4 *>(planes) + (py + 3 + dy) * ru + 2 * m;
         const uint4 l0 = r[0], l1 = r[1], h0 = r[2], h1 = r[3];
         const uint32_t lo[8] = { l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w };
         const uint32_t hi[8] = { h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w };
@@ -918,117 +919,179 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
     }
 }
 
+// Bulk copy of tile record t into shared memory, completing on `bar`.
+__device__ __forceinline__ void fetch_rec(const Batch &b, int t, TileRec *dst, uint64_t *bar)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"((uint32_t)sizeof(TileRec)) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(b.tile_rec + t)),
+                 "r"((uint32_t)sizeof(TileRec)), "r"(smem_u32(bar)) : "memory");
+}
+
+// The tile box (TMA, levels with a tensor map) and the tile's projection
+// ranges (bulk copies) of record R, all completing on `bar`.
+__device__ __forceinline__ void issue_rec_tile(const TileRec &R, uint8_t *buf, uint8_t *prj, uint64_t *bar)
+{
+    const uint32_t box = R.tmap ? (uint32_t)(R.box_w * R.box_h) : 0u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(box + (uint32_t)(R.prj_bytes_x + R.prj_bytes_y)) : "memory");
+    if (R.tmap)
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+            ::"r"(smem_u32(buf)), "l"(reinterpret_cast<uint64_t>(R.tmap)), "r"(R.xs), "r"(R.ys), "r"(smem_u32(bar))
+            : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(prj)), "l"(reinterpret_cast<uint64_t>(R.prj_src_x)), "r"((uint32_t)R.prj_bytes_x),
+                 "r"(smem_u32(bar)) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(prj + kPrjBytes)), "l"(reinterpret_cast<uint64_t>(R.prj_src_y)),
+                 "r"((uint32_t)R.prj_bytes_y), "r"(smem_u32(bar)) : "memory");
+}
+
 // Bit-sliced ring test (P_min = 9, P_max = 13), the same results as
-// k_fast_cull.  Per tile: cell states, tile bytes, bit-planes, one barrier;
+// k_fast_cull.  Tiles come with host-made records: thread 0 fetches the
+// record of the tile after next and, once the next tile's record is in,
+// issues that tile's box and projection ranges, so every tile starts from
+// shared memory.  Per tile: tile wait, cell states, bit-planes, one barrier;
 // each threshold pass classifies 32 pixels of a row per thread, and every
 // warp scores its own corners right away through a window of entries in
 // shared memory (k = 1: atomic maximum of the cell's key; k > 1: corner list
-// for the top-k rounds); a barrier ends each pass.  The counters of a tile
-// live in one of two sets by tile parity, so the set of the next tile is
-// cleared while the current one is in use, without a barrier of its own.
+// for the top-k rounds); a barrier ends each pass and one the tile.  The
+// counters of a tile live in one of two sets by tile parity, so the set of
+// the next tile is cleared while the current one is in use.
 __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     // per set: corners listed (k > 1), skipped cells, cells open at the
     // start (state 0), open cells that got a primary-threshold corner
     __shared__ int cnt[2][4];
+    __shared__ int s_abort;
+    __shared__ uint32_t s_rph;  // thread 0: parity of the next completion of each record barrier (bit s)
+    __shared__ __align__(16) uint16_t s_wbuf[kFastThreads / 32][kBitsWin];
+    __shared__ __align__(16) TileRec recs[3];
+    __shared__ __align__(16) uint8_t s_prj[2][2 * kPrjBytes];  // per box: x range, y range
+    __shared__ __align__(8) uint64_t bars[5];                   // [0..1] boxes, [2..4] records
     const int k = b.prm.k, border = b.prm.border;
     const BitsLayout lay = bits_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k, b.fast_max_planes);
     uint8_t *const buf0 = smem + lay.buf0, *const buf1 = smem + lay.buf1;
     uint32_t *planes = reinterpret_cast<uint32_t *>(smem + lay.planes);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint16_t *wbuf = reinterpret_cast<uint16_t *>(smem + lay.wbuf) + warp * kBitsWin;
+    uint16_t *wbuf = s_wbuf[warp];
     uint16_t *clist = reinterpret_cast<uint16_t *>(smem + lay.clist);
     uint32_t *ckey = reinterpret_cast<uint32_t *>(smem + lay.ckey);
     uint8_t *has_hi = smem + lay.has_hi;
     uint32_t *sel = reinterpret_cast<uint32_t *>(smem + lay.sel);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar);
 
     if ((smem_u32(buf0) | smem_u32(buf1)) & 127u) {
         if (threadIdx.x == 0) atomicOr(b.err, kErrDecode);
         return;
     }
+    const int grid = (int)gridDim.x;
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])) : "memory");
+        for (int i = 0; i < 5; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+        const int t0 = blockIdx.x;
+        if (t0 < b.fast_tiles) {
+            fetch_rec(b, t0, &recs[0], &bars[2]);
+            if (t0 + grid < b.fast_tiles) fetch_rec(b, t0 + grid, &recs[1], &bars[3]);
+            if (wait_tile(&bars[2], 0u)) issue_rec_tile(recs[0], buf0, s_prj[0], &bars[0]);
+            else { atomicOr(b.err, kErrTimeout); s_abort = 1; }
+        }
+        s_rph = 1u;
     }
     if (threadIdx.x < 8) cnt[threadIdx.x >> 2][threadIdx.x & 3] = 0;
     __syncthreads();
-    if (threadIdx.x == 0 && blockIdx.x < b.fast_tiles) issue_tile(b, blockIdx.x, buf0, &bars[0]);
-    uint32_t phase0 = 0u, phase1 = 0u;
+    if (s_abort) return;
+    uint32_t phases = 0u;  // bit p: parity of the next completion of box barrier p
 
     int it = 0;
-    for (int t = blockIdx.x; t < b.fast_tiles; t += gridDim.x, ++it) {
-        const int cur = it & 1;
+    for (int t = blockIdx.x; t < b.fast_tiles; t += grid, ++it) {
+        const int cur = it & 1, s3 = it % 3;
         int *const C = cnt[cur];
-        const TileGeom G = tile_geom(b, t);
-        const LevelDesc &L = b.levels[G.li];
-        const ImageDesc &I = b.images[L.image];
+        const TileRec &R = recs[s3];
+        const uint16_t *prj = reinterpret_cast<const uint16_t *>(s_prj[cur]);
         if (threadIdx.x == 0) {
-            // the buffer's and the other set's readers finished at the barrier
-            // that ended the previous tile
-            if (t + (int)gridDim.x < b.fast_tiles) issue_tile(b, t + gridDim.x, cur ? buf0 : buf1, &bars[cur ^ 1]);
+            // the next tile's record was fetched one tile ago; the slot of the
+            // tile after it, the other box and its projections were last read
+            // before the barrier that ended the previous tile
+            if (t + grid < b.fast_tiles) {
+                const int sn = s3 == 2 ? 0 : s3 + 1;
+                if (wait_tile(&bars[2 + sn], (s_rph >> sn) & 1u))
+                    issue_rec_tile(recs[sn], cur ? buf0 : buf1, s_prj[cur ^ 1], &bars[cur ^ 1]);
+                else { atomicOr(b.err, kErrTimeout); s_abort = 1; }
+                s_rph ^= 1u << sn;
+                if (t + 2 * grid < b.fast_tiles) {
+                    const int sa = s3 == 0 ? 2 : s3 - 1;
+                    fetch_rec(b, t + 2 * grid, &recs[sa], &bars[2 + sa]);
+                }
+            }
             cnt[cur ^ 1][0] = cnt[cur ^ 1][1] = cnt[cur ^ 1][2] = cnt[cur ^ 1][3] = 0;
         }
-        const int c = L.c, cells_x = L.cells_x, W = L.W, Hh = L.H;
-        const uint32_t cinv = (uint32_t)L.cinv;
-        const int ncx = G.ncx, x0 = G.x0, y0 = G.y0, tw = G.tw, th = G.th;
-        const int rowb = L.box_w;
-        const int cells = ncx * G.ncy;
-        uint8_t *tb = cur ? buf1 : buf0;
-
-        // cell states (as in k_fast_cull) and cleared selections: they do
-        // not depend on the tile bytes, so they go before the tile wait
+        uint8_t *const tb = cur ? buf1 : buf0;
+        // the box and the projections (every tile waits: the projections
+        // come on the same barrier whether or not the box does)
+        if (!wait_tile(&bars[cur], (phases >> cur) & 1u)) {
+            if (threadIdx.x == 0) atomicOr(b.err, kErrTimeout);
+            return;
+        }
+        phases ^= 1u << cur;
+        bool all_skipped;
+        {
+        // record fields are read where needed (shared memory): values read
+        // before a barrier are not carried across it
+        const int c = R.c, W = R.W, Hh = R.H, x0 = R.x0, y0 = R.y0, rowb = R.box_w;
+        const int ncx = R.ncx, cells = ncx * R.ncy;
+        if (!R.tmap) {
+            // levels whose tiles cannot start on a word boundary: plain loads
+            // (box rows of box_w bytes, delta = 0)
+            const int wpr = rowb >> 2;
+            uint32_t *tw32 = reinterpret_cast<uint32_t *>(tb);
+            for (int i = threadIdx.x; i < R.box_h * wpr; i += kFastThreads) {
+                const int r = i / wpr, wi = i - r * wpr;
+                const uint8_t *row = R.raw + (size_t)min(max(R.ys + r, 0), Hh - 1) * R.pitch;
+                const int gx = R.xs + 4 * wi;
+                uint32_t v = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v |= (uint32_t)__ldg(row + min(max(gx + q, 0), W - 1)) << (8 * q);
+                tw32[i] = v;
+            }
+        }
+        // cell states (as in k_fast_cull) and cleared selections
         int my_skipped = 0, my_open = 0;
         for (int i = threadIdx.x; i < cells; i += kFastThreads) {
             const int lcy = i / ncx, lcx = i - lcy * ncx;
-            const int cx0 = (G.ccx0 + lcx) * c, cy0 = (G.ccy0 + lcy) * c;
+            const int cx0 = (R.ccx0 + lcx) * c, cy0 = (R.ccy0 + lcy) * c;
             const bool evaluated = cx0 + c > border && cx0 < W - border && cy0 + c > border && cy0 < Hh - border;
             uint8_t st = evaluated ? 0 : 3;
-            if (I.skip && evaluated) {
+            if (R.skip && evaluated) {
                 const int px = min(cx0 + c / 2, W - 1), py = min(cy0 + c / 2, Hh - 1);
-                const int X = __ldg(L.projx + px), Y = __ldg(L.projy + py);
-                st = I.skip[(Y / I.skip_c0) * I.skip_cells_x + X / I.skip_c0] ? 2 : 0;
+                const int X = prj[R.prj_off_x + px - x0], Y = prj[kPrjBytes / 2 + R.prj_off_y + py - y0];
+                st = R.skip[(Y / R.skip_c0) * R.skip_cells_x + X / R.skip_c0] ? 2 : 0;
             }
-            if (I.skip && st != 0) { st = 2; ++my_skipped; }
+            if (R.skip && st != 0) { st = 2; ++my_skipped; }
             my_open += st == 0;
             has_hi[i] = st;
         }
         for (int i = threadIdx.x; i < cells * k; i += kFastThreads) sel[i] = 0;
         if (my_skipped) atomicAdd(&C[1], my_skipped);
         if (my_open) atomicAdd(&C[2], my_open);
-        if (I.skip) __syncthreads();  // uniform: a tile whose cells are all skipped builds no planes
-        const bool all_skipped = I.skip && C[1] == cells;
+        // a box loaded with plain loads, the cell states and, in skip mode,
+        // the skipped count are complete before the planes
+        if (!R.tmap || R.skip) __syncthreads();
+        all_skipped = R.skip && C[1] == cells;
 
-        if (L.tmap) {
-            if (!wait_tile(&bars[cur], cur ? phase1 : phase0)) {
-                if (threadIdx.x == 0) atomicOr(b.err, kErrTimeout);
-                return;
-            }
-            if (cur) phase1 ^= 1u; else phase0 ^= 1u;
-        } else {
-            const int wpr = rowb >> 2;
-            uint32_t *tw32 = reinterpret_cast<uint32_t *>(tb);
-            for (int i = threadIdx.x; i < L.box_h * wpr; i += kFastThreads) {
-                const int r = i / wpr, wi = i - r * wpr;
-                const uint8_t *row = L.raw + (size_t)min(max(G.ys + r, 0), Hh - 1) * L.pitch;
-                const int gx = G.xs + 4 * wi;
-                uint32_t v = 0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) v |= (uint32_t)__ldg(row + min(max(gx + q, 0), W - 1)) << (8 * q);
-                tw32[i] = v;
-            }
-            __syncthreads();
-        }
         // bit-planes of the box rows [r0, r1 + 6) that the evaluated rows
         // [r0, r1) read, chunks 0..nch (an item of chunk m reads m and m + 1),
         // one 32-byte chunk per thread; chunks at or past the box's end
         // (a row's last may hold only 16 bytes) are zero
-        const int plo = max(border - x0, 0), phi = min(W - border - x0, tw);
-        const int r0 = max(border - y0, 0), r1 = min(Hh - border - y0, th);
-        const int nch = (tw + 31) >> 5, sb = G.delta + 4;
-        const int nbc = (rowb + 31) >> 5, pstride = nbc + 1;
+        const int r0 = max(border - y0, 0), r1 = min(Hh - border - y0, R.th);
+        const int nch = (R.tw + 31) >> 5;
+        const int nbc = (rowb + 31) >> 5, ru = bs_row_units(nch);
         if (!all_skipped) {
             const int nrows = max(r1 - r0, 0) > 0 ? r1 - r0 + 6 : 0;
             for (int ci = threadIdx.x; ci < nrows * (nch + 1); ci += kFastThreads) {
@@ -1039,16 +1102,24 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
                     a = src[0];
                     if (32 * kc + 16 < rowb) z = src[1];
                 }
-                bs_transpose(a, z, reinterpret_cast<uint4 *>(planes + (r * pstride + kc) * 8));
+                bs_transpose(a, z, reinterpret_cast<uint4 *>(planes) + r * ru + 2 * kc);
             }
         }
+        }
         __syncthreads();
+        if (s_abort) return;  // thread 0 could not start the next tile
         const bool some_skipped = C[1] > 0;
 
+        {
+        const int c = R.c, W = R.W, Hh = R.H, x0 = R.x0, y0 = R.y0, tw = R.tw, rowb = R.box_w, ncx = R.ncx;
+        const uint32_t cinv = (uint32_t)R.cinv;
+        const int plo = max(border - x0, 0), phi = min(W - border - x0, tw);
+        const int r0 = max(border - y0, 0), r1 = min(Hh - border - y0, R.th);
+        const int nch = (tw + 31) >> 5, sb = R.delta + 4, ru = bs_row_units(nch);
         const int items = max(r1 - r0, 0) * nch;
-        const uint8_t *tbytes = tb + G.delta;  // pixel (x, y) at (y - y0 + 3) * rowb + (x - x0 + 4)
+        const uint8_t *tbytes = tb + R.delta;  // pixel (x, y) at (y - y0 + 3) * rowb + (x - x0 + 4)
         for (int pass = 0; pass < 2 && !all_skipped; ++pass) {
-            const int eps = pass == 0 ? I.eps_hi : I.eps_lo;
+            const int eps = pass == 0 ? R.eps_hi : R.eps_lo;
             // fallback pass only while an open cell got no corner
             if (pass == 1 && (eps <= 0 || C[3] >= C[2])) break;
             for (int base = warp * 32; base < items; base += kFastThreads) {
@@ -1065,7 +1136,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
                     if (pass == 1 && valid)  // only cells without a corner (and not skipped)
                         valid &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st == 0; });
                     if (valid) {
-                        bits = bs_corners(planes, pstride, py, m, sb, eps) & valid;
+                        bits = bs_corners(planes, ru, py, m, sb, eps) & valid;
                         if (bits && pass == 0 && some_skipped)
                             bits &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st != 2; });
                     }
@@ -1125,8 +1196,10 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
             }
             __syncthreads();  // selections, marks and counts of this pass complete
         }
+        }
         if (k > 1) {
-            const int nc = C[0];
+            const uint32_t cinv = (uint32_t)R.cinv;
+            const int ncx = R.ncx, nc = C[0];
             for (int j = 0; j < k; ++j) {
                 for (int i = threadIdx.x; i < nc; i += kFastThreads) {
                     const int e = clist[i];
@@ -1138,22 +1211,24 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
             }
         }
 
-        // slots and the s0 score map (as in k_fast_cull)
+        // slots and the s0 score map (as in k_fast_cull), projections from
+        // the staged ranges
+        const int c = R.c, ncx = R.ncx, cells = ncx * R.ncy;
         for (int e = threadIdx.x; e < cells * k; e += kFastThreads) {
             const int cell = e / k, j = e - cell * k;
             const int lcy = cell / ncx;
-            const int gcx = G.ccx0 + cell - lcy * ncx, gcy = G.ccy0 + lcy;
+            const int gcx = R.ccx0 + cell - lcy * ncx, gcy = R.ccy0 + lcy;
             const uint32_t key = sel[e];
-            b.slots[L.slot_base + (gcy * cells_x + gcx) * k + j] = key;
+            b.slots[R.slot_base + (gcy * R.cells_x + gcx) * k + j] = key;
             if (key) {
                 const int inidx = 0xFFFF - (int)(key & 0xFFFFu);
                 const int x = gcx * c + inidx % c, y = gcy * c + inidx / c;
-                if (x >= W || y >= Hh) { atomicOr(b.err, kErrDecode); continue; }
-                const int X = __ldg(L.projx + x), Y = __ldg(L.projy + y);
-                atomicAdd(I.map + (size_t)Y * I.W0 + X, (1u << 16) + (key >> 16));
+                if (x >= R.W || y >= R.H) { atomicOr(b.err, kErrDecode); continue; }
+                const int X = prj[R.prj_off_x + x - R.x0], Y = prj[kPrjBytes / 2 + R.prj_off_y + y - R.y0];
+                atomicAdd(R.map + (size_t)Y * R.W0 + X, (1u << 16) + (key >> 16));
             }
         }
-        __syncthreads();  // every reader of this buffer, the planes and this set is done
+        __syncthreads();  // every reader of this box, its projections, the planes and this set is done
     }
 }
 
