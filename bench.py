@@ -69,9 +69,10 @@ WORKLOAD_DESC = {
 }
 
 # Stage -> kernel name, for the roofline and the ncu summaries.
-KERNELS = {"pyramid": "k_pyramid", "detect": "k_fast_cull", "pfa_nms": "k_pfa_nms",
+KERNELS = {"pyramid": "k_pyramid", "detect": "k_fast_bits", "pfa_nms": "k_pfa_nms",
            "pfa_final": "k_pfa_finalize", "orb": "k_orient_desc", "match": "k_match"}
-KERNEL_SOURCES = {"k_pyramid": "k_detect.cu", "k_fast_cull": "k_detect.cu", "k_pfa_nms": "k_pyca.cu",
+KERNEL_SOURCES = {"k_pyramid": "k_detect.cu", "k_fast_cull": "k_detect.cu", "k_fast_bits": "k_detect.cu",
+                  "k_pfa_nms": "k_pyca.cu",
                   "k_pfa_finalize": "k_pyca.cu", "k_orient_desc": "k_orb_match.cu", "k_match": "k_orb_match.cu",
                   "k_skipnet": "k_skipnet.cu"}
 LAUNCHES_PER_CALL = 6  # pyramid, detect, PFA NMS, PFA final, ORB, match (exact path)
@@ -120,6 +121,12 @@ def level_pixels(W0, H0, levels, scale):
     from paper_2410_04090_gb300 import jslam
     w, h, _ = jslam.level_geometry(W0, H0, levels, scale, 32)
     return [int(a) * int(b) for a, b in zip(w, h)]
+
+
+def level_pixels_batch(pairs, params):
+    """Pixels of every level of every image of the batch."""
+    return sum(2 * sum(level_pixels(pr.left.shape[1], pr.left.shape[0], p["levels"], p["scale"]))
+               for pr, p in zip(pairs, params))
 
 
 def algorithmic_bytes(stage, pairs, params, kp_counts):
@@ -742,22 +749,28 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
         alg = algorithmic_bytes(dom, pairs, params, counts)
         ach = alg / (stage_ms[dom] / 1e3) / 1e9
         prof = profile_summary(KERNELS[dom], args.workload)
-        roof = {"bound": "hbm", "kernel": KERNELS[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth",
-                "algorithmic_bytes_per_launch": alg,
-                "traffic": profile_number(prof, "dram_bytes_per_launch_full_workload"),
-                "stage_ms_per_launch": stage_ms,
-                "stage_timing": "CUDA events on the context stream between the stages of the batched mode's timed steps"}
-        # the same launch against the integer issue rate (instructions from ncu)
+        hbm = {"bound": "hbm", "kernel": KERNELS[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
+               "frac": ach / peak, "peak_kind": f"{peak_kind} HBM copy bandwidth",
+               "algorithmic_bytes_per_launch": alg,
+               "traffic": profile_number(prof, "dram_bytes_per_launch_full_workload")}
+        roof = hbm
+        # the kernels of the path are integer-issue bound: with the launch's
+        # executed instructions from the committed ncu summary, the roofline
+        # is the issue rate, and the HBM view rides along
         warp_inst = profile_number(prof, "inst_executed_warp_per_launch")
         if warp_inst:
             apeak, sms, mhz = alu_peak(dev_index)
             lane_ops = warp_inst * 32
-            pixels = algorithmic_bytes("detect", pairs, params, counts)  # level pixels tested (1 byte each)
-            roof["alu"] = {"achieved": lane_ops / (stage_ms[dom] / 1e3), "peak": apeak, "unit": "lane-op/s",
-                           "frac": lane_ops / (stage_ms[dom] / 1e3) / apeak,
-                           "peak_kind": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz",
-                           "inst_per_launch": lane_ops, "ops_per_pixel": lane_ops / pixels}
+            pixels = level_pixels_batch(pairs, params)
+            rate = lane_ops / (stage_ms[dom] / 1e3)
+            roof = {"bound": "alu", "kernel": KERNELS[dom], "achieved": rate, "peak": apeak, "unit": "lane-op/s",
+                    "frac": rate / apeak, "peak_kind": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz (integer issue)",
+                    "traffic": hbm["traffic"], "inst_per_launch": lane_ops, "ops_per_pixel": lane_ops / pixels,
+                    "instructions_from": f"profiles/{KERNELS[dom]}_{args.workload}.txt",
+                    "hbm": {k: hbm[k] for k in ("achieved", "peak", "unit", "frac", "peak_kind",
+                                                "algorithmic_bytes_per_launch")}}
+        roof["stage_ms_per_launch"] = stage_ms
+        roof["stage_timing"] = "CUDA events on the context stream between the stages of the batched mode's timed steps"
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args, pairs, params, lo)
     launches = {"batched": LAUNCHES_PER_CALL, "graph": LAUNCHES_PER_CALL, "plain": LAUNCHES_PER_CALL * n,
                 "learned_skip": LAUNCHES_PER_CALL + 2, "streams2": 2 * LAUNCHES_PER_CALL,
