@@ -13,6 +13,11 @@
 //             the top-k corners of each cell (Sec. II-C-1, Feature Culling)
 //             and adds each survivor to the s0 score map (Sec. II-C-2, PFA
 //             steps 1-2: K_l and K_r accumulate in one packed word).
+// k_fast_bits the same results for run bounds [9, 13] (the default): the tile
+//             is transposed into bit-planes and each thread tests 32 pixels
+//             of a row at once with bitwise arithmetic (carry-chain compares,
+//             run windows), scoring its corners in place; tiles come with
+//             host-made records staged by bulk copies.
 #include <algorithm>
 
 #include <cuda.h>

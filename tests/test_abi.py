@@ -84,6 +84,53 @@ def test_cardinal_pretest_is_necessary(oracle):
     assert not passes[runs == 7].all()
 
 
+def test_bitsliced_run_window_identity(oracle):
+    """The bit-sliced detection kernel decides Eq. 3 for run bounds [9, 13]
+    by windows of flags: A3_q = F_q F_q+1 F_q+2, a run of 9 at q is
+    A3_q A3_q+3 A3_q+6, a run of 14 is that and A3_q+9 A3_q+11, and the
+    pixel is a corner when some run of 9 exists and no run of 14 does.  Over
+    all 2^16 ring masks this equals 9 <= longest circular run <= 13."""
+    m = np.arange(1 << 16)
+    F = [(m >> q) & 1 for q in range(16)]
+    A3 = [F[q] & F[(q + 1) % 16] & F[(q + 2) % 16] for q in range(16)]
+    r9 = np.zeros_like(m)
+    r14 = np.zeros_like(m)
+    for q in range(16):
+        a9 = A3[q] & A3[(q + 3) % 16] & A3[(q + 6) % 16]
+        r9 |= a9
+        r14 |= a9 & A3[(q + 9) % 16] & A3[(q + 11) % 16]
+    got = (r9 & (1 - r14)).astype(bool)
+    want = np.array([9 <= oracle.longest_run(int(v)) <= 13 for v in m])
+    assert np.array_equal(got, want)
+
+
+def test_bitplane_transpose_identity():
+    """The detection kernel's bit-plane transpose (three delta swaps per 8x8
+    bit block, then byte permutes gathering byte i of the four blocks into
+    word i) gives word i, bit j = bit i of byte j, for random 32-byte chunks
+    (the same word operations in numpy)."""
+    rng = np.random.default_rng(7)
+    by = rng.integers(0, 256, (4096, 32), dtype=np.uint64)
+    w = [(by[:, 4 * k] | by[:, 4 * k + 1] << 8 | by[:, 4 * k + 2] << 16 | by[:, 4 * k + 3] << 24) for k in range(8)]
+    M = np.uint64(0xFFFFFFFF)
+    for blk in range(4):
+        lo, hi = w[2 * blk], w[2 * blk + 1]
+        for sh, mask in ((7, 0x00AA00AA), (14, 0x0000CCCC)):
+            t = (lo ^ (lo >> np.uint64(sh))) & np.uint64(mask); lo = lo ^ t ^ ((t << np.uint64(sh)) & M)
+            t = (hi ^ (hi >> np.uint64(sh))) & np.uint64(mask); hi = hi ^ t ^ ((t << np.uint64(sh)) & M)
+        t = (lo ^ ((hi << np.uint64(4)) & M)) & np.uint64(0xF0F0F0F0)
+        w[2 * blk], w[2 * blk + 1] = lo ^ t, hi ^ (t >> np.uint64(4))
+    byte = lambda x, i: (x >> np.uint64(8 * i)) & np.uint64(0xFF)
+    for i in range(8):
+        half, bi = divmod(i, 4)
+        got = byte(w[half], bi) | byte(w[2 + half], bi) << np.uint64(8) | \
+            byte(w[4 + half], bi) << np.uint64(16) | byte(w[6 + half], bi) << np.uint64(24)
+        want = np.zeros(len(by), np.uint64)
+        for j in range(32):
+            want |= ((by[:, j] >> np.uint64(i)) & np.uint64(1)) << np.uint64(j)
+        assert np.array_equal(got, want), i
+
+
 def test_sector_float_margin_agrees_with_double(jslam):
     """The orientation kernel decides each sector boundary in float when
     |m01 cos - m10 sin| exceeds (|m01| + |m10|) 2^-20 and in IEEE double
