@@ -366,15 +366,17 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     const size_t o_pyr = reserve(sizeof(int32_t) * (n_levels + 1));
     const size_t o_fast = reserve(sizeof(int32_t) * (n_levels + 1));
     const size_t o_seg = reserve(sizeof(int32_t) * (n_segs + 1));
-    size_t n_fast_tiles = 0;
+    size_t n_fast_tiles = 0, n_pyr_tiles = 0;
     for (int p = 0; p < n; ++p)
         for (int l = 0; l < geo[p].levels; ++l) {
+            n_pyr_tiles += 2 * (size_t)(((geo[p].W[l] + kPyrTW - 1) / kPyrTW) * ((geo[p].H[l] + kPyrTH - 1) / kPyrTH));
             int bx, by;
             fast_block(geo[p].c[l], k, ctx->tune.tile_w_px, ctx->tune.tile_h_px, &bx, &by);
             const int cx = (geo[p].W[l] + geo[p].c[l] - 1) / geo[p].c[l], cy = (geo[p].H[l] + geo[p].c[l] - 1) / geo[p].c[l];
             n_fast_tiles += 2 * (size_t)(((cx + bx - 1) / bx) * ((cy + by - 1) / by));
         }
     const size_t o_ftl = reserve(sizeof(int32_t) * (n_fast_tiles + 1));
+    const size_t o_ptl = reserve(sizeof(int32_t) * (n_pyr_tiles + 1));
     const size_t o_trec = reserve(sizeof(TileRec) * (n_fast_tiles + 1));
     const size_t o_lstart = reserve(sizeof(int32_t) * (kMaxLevels + 1) * n_img);
     const size_t o_tmaps = reserve(sizeof(CUtensorMap) * (size_t)n_levels);
@@ -390,6 +392,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     auto fast_base = reinterpret_cast<int32_t *>(host.data() + o_fast);
     auto seg_level = reinterpret_cast<int32_t *>(host.data() + o_seg);
     auto ftile_level = reinterpret_cast<int32_t *>(host.data() + o_ftl);
+    auto ptile_level = reinterpret_cast<int32_t *>(host.data() + o_ptl);
     size_t t_off = o_tables, lvl_off = 0, map_off = 0, stage_off = 0;
     int li = 0, slot = 0, seg = 0, pyr = 0, fast = 0;
     ctx->staging_off.assign(n_img, 0);
@@ -504,7 +507,9 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 for (int r = 0; r < L.cells_y; ++r) seg_level[seg + r] = li;
                 seg += L.cells_y;
                 pyr_base[li] = pyr;
-                pyr += ((L.W + kPyrTW - 1) / kPyrTW) * ((L.H + kPyrTH - 1) / kPyrTH);
+                const int ptiles = ((L.W + kPyrTW - 1) / kPyrTW) * ((L.H + kPyrTH - 1) / kPyrTH);
+                for (int q = 0; q < ptiles; ++q) ptile_level[pyr + q] = li;
+                pyr += ptiles;
                 fast_base[li] = fast;
                 const int ftiles = ((L.cells_x + L.bx - 1) / L.bx) * ((L.cells_y + L.by - 1) / L.by);
                 for (int q = 0; q < ftiles; ++q) ftile_level[fast + q] = li;
@@ -574,6 +579,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.levels = reinterpret_cast<const LevelDesc *>(dplan + o_levels);
     b.pairs = reinterpret_cast<const PairDesc *>(dplan + o_pairs);
     b.pyr_tile_base = reinterpret_cast<const int32_t *>(dplan + o_pyr);
+    b.pyr_tile_level = reinterpret_cast<const int32_t *>(dplan + o_ptl);
     b.fast_tile_base = reinterpret_cast<const int32_t *>(dplan + o_fast);
     b.seg_level = reinterpret_cast<const int32_t *>(dplan + o_seg);
     b.fast_tile_level = reinterpret_cast<const int32_t *>(dplan + o_ftl);

@@ -154,6 +154,7 @@ struct Batch {
     const LevelDesc *levels;
     const PairDesc *pairs;
     const int32_t *pyr_tile_base;   // n_levels + 1
+    const int32_t *pyr_tile_level;  // level index of each pyramid tile
     const int32_t *fast_tile_base;  // n_levels + 1
     const int32_t *fast_tile_level; // level index of each detection tile
     const int32_t *seg_level;       // level index of each segment

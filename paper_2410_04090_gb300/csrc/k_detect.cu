@@ -33,17 +33,6 @@ cudaError_t set_blur_weights(const int32_t w[7])
     return cudaMemcpyToSymbol(c_blur_w, w, sizeof(int32_t) * 7);
 }
 
-// Largest i in [0, n) with base[i] <= v (base non-decreasing, base[0] = 0).
-__device__ __forceinline__ int find_bucket(const int32_t *base, int n, int v)
-{
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (__ldg(base + mid) <= v) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // ---------------------------------------------------------------- pyramid
 //
 // Per 128x32 output tile: the raw level over the tile plus a halo (3 rows, 4
@@ -78,8 +67,8 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
     __shared__ int s_ya[kPyrRows];
     __shared__ int nsrc;
 
-    const int li = find_bucket(b.pyr_tile_base, b.n_levels, blockIdx.x);
-    const LevelDesc L = b.levels[li];
+    const int li = __ldg(b.pyr_tile_level + blockIdx.x);
+    const LevelDesc &L = b.levels[li];
     const ImageDesc &I = b.images[L.image];
     const int t = blockIdx.x - b.pyr_tile_base[li];
     const int tiles_x = (L.W + kPyrTW - 1) / kPyrTW;
