@@ -2,11 +2,12 @@
 // streamlined multiscale detection and extraction; middle-end stereo
 // matching by descriptor-distance minimisation).
 //
-// k_orient_desc  one warp per keypoint of any image and level.  Lanes 0..30
-//                own one column of the radius-15 disk and load all its rows
-//                at once to accumulate the intensity moments m10, m01 on the
-//                raw level; lanes 0..26 stage the 27 x 27 blurred patch the
-//                BRIEF pattern reaches in shared memory; lanes 0..29 each test
+// k_orient_desc  one warp per keypoint of any image and level.  The lanes
+//                read the radius-15 disk of the raw level as aligned words
+//                (9 per row) and accumulate the intensity moments m10, m01
+//                with byte dot products over the bytes inside the disk; they
+//                stage the 27 x 27 blurred patch the BRIEF pattern reaches in
+//                shared memory the same way (8 words per row); lanes 0..29 each test
 //                one sector boundary (float with an error margin, IEEE double
 //                with explicit rounding inside it, so the sector equals the
 //                one the host-side definition gives); the 256 BRIEF
@@ -23,11 +24,14 @@ namespace jslam {
 
 constexpr int kPatR = 13;                 // rotated BRIEF offsets lie in [-13, 13]
 constexpr int kPatW = 2 * kPatR + 1;      // 27
-constexpr int kPatPitch = kPatW + 1;
+constexpr int kPatPitch = 32;             // patch rows staged as 8 aligned words
+constexpr int kDiskWords = 9;             // aligned words covering the 31 disk columns of a row
+// largest |dx| with dx^2 + dy^2 <= kDiskR^2, by |dy|
+__constant__ int8_t c_disk_umax[kDiskR + 1] = { 15, 14, 14, 14, 14, 14, 13, 13, 12, 12, 11, 10, 9, 7, 5, 0 };
 
 __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
 {
-    __shared__ uint8_t s_patch[8][kPatW * kPatPitch];
+    __shared__ __align__(16) uint8_t s_patch[8][kPatW * kPatPitch];
     const int img = blockIdx.y;
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -43,33 +47,53 @@ __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
 
     // The keypoint is at least `border` (>= 16) from every edge, so the
     // 31 x 31 square of the moment disk and the 27 x 27 patch of the BRIEF
-    // pattern are inside the level: every row is loaded at once (no
-    // dependent chain), lanes on consecutive columns (one or two sectors per
-    // row), and the disk is applied as a mask.
-    if (lane < kPatW) {
-        const uint8_t *src = L.blur + (size_t)(y - kPatR) * bpitch + (x - kPatR + lane);
-        uint32_t v[kPatW];
+    // pattern are inside the level.  Both are read as aligned 32-bit words
+    // (rows start on 128-byte boundaries; a row's last word may reach 3
+    // bytes past the level's width, into the pitch or the buffer's slack),
+    // every load independent of the others.
+    // Patch: 27 rows x 8 words from word column (x - 13) / 4 of the blurred
+    // level, staged with a pitch of 32 bytes.
+    const int pw0 = (x - kPatR) >> 2;
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(L.blur + (size_t)(y - kPatR) * bpitch) + pw0;
+        uint32_t *dst = reinterpret_cast<uint32_t *>(patch);
 #pragma unroll
-        for (int r = 0; r < kPatW; ++r) v[r] = __ldg(src + (size_t)r * bpitch);
-#pragma unroll
-        for (int r = 0; r < kPatW; ++r) patch[r * kPatPitch + lane] = (uint8_t)v[r];
-    }
-    int m10 = 0, m01 = 0;
-    if (lane < 2 * kDiskR + 1) {
-        const int dx = lane - kDiskR;
-        const uint8_t *col = raw + (size_t)(y - kDiskR) * pitch + (x + dx);
-        int v[2 * kDiskR + 1];
-#pragma unroll
-        for (int r = 0; r <= 2 * kDiskR; ++r) v[r] = __ldg(col + (size_t)r * pitch);
-        int s = 0;
-#pragma unroll
-        for (int r = 0; r <= 2 * kDiskR; ++r) {
-            const int dy = r - kDiskR;
-            const int w = dx * dx + dy * dy <= kDiskR * kDiskR ? v[r] : 0;
-            s += w;
-            m01 += dy * w;
+        for (int k = 0; k < (kPatW * 8 + 31) / 32; ++k) {
+            const int it = k * 32 + lane;
+            if (it < kPatW * 8) {
+                const int r = it >> 3, w = it & 7;
+                dst[it] = __ldg(src + (size_t)r * (bpitch >> 2) + w);
+            }
         }
-        m10 = dx * s;
+    }
+    // Disk moments: 31 rows x 9 words from word column (x - 15) / 4 of the
+    // raw level.  Per word, the bytes inside the disk (|dx| <= umax(|dy|))
+    // are kept and two byte dot products give the row sum and the sum of
+    // (dx + 18) I (weights 3..36, unsigned); m10 = that - 18 sum I.
+    int m10 = 0, m01 = 0;
+    {
+        const int dw0 = (x - kDiskR) >> 2;
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(raw + (size_t)(y - kDiskR) * pitch) + dw0;
+        int s = 0, sw = 0;
+#pragma unroll
+        for (int k = 0; k < ((2 * kDiskR + 1) * kDiskWords + 31) / 32; ++k) {
+            const int it = k * 32 + lane;
+            if (it < (2 * kDiskR + 1) * kDiskWords) {
+                const int r = it / kDiskWords, w = it - r * kDiskWords;
+                const uint32_t v = __ldg(src + (size_t)r * (pitch >> 2) + w);
+                const int dy = r - kDiskR;
+                const int um = c_disk_umax[abs(dy)];
+                const int cx0 = 4 * (dw0 + w) - x;  // dx of the word's byte 0
+                const int lo = max(-um - cx0, 0), hi = min(um - cx0, 3);
+                const uint32_t mask = hi < lo ? 0u : (0xFFFFFFFFu >> (24 - 8 * (hi - lo))) << (8 * lo);
+                const uint32_t vm = v & mask;
+                const int rs = (int)__dp4a(vm, 0x01010101u, 0u);
+                s += rs;
+                m01 += dy * rs;
+                sw += (int)__dp4a(vm, (uint32_t)(cx0 + 18) * 0x01010101u + 0x03020100u, 0u);
+            }
+        }
+        m10 = sw - 18 * s;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -104,7 +128,7 @@ __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
 
     __syncwarp();  // the patch is complete
     const char4 *pat = reinterpret_cast<const char4 *>(b.pattern) + (size_t)bin * kPairs;
-    const uint8_t *centre = patch + kPatR * kPatPitch + kPatR;
+    const uint8_t *centre = patch + kPatR * kPatPitch + (x - kPatR - 4 * pw0) + kPatR;
     uint32_t myword = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
