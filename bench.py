@@ -660,12 +660,26 @@ def main():
                           "per-level MLPT/TEWA culling kernels; fused: FAST + BR + culling + PFA scatter in one "
                           "persistent kernel, no CRF-matrix"}
 
+    # repeatability of Bounded Rectification against plain FAST on rotated
+    # labeled scenes (the corner sets from the library's CRF-matrix)
+    br_rep = None
+    if not args.only_batched and rank == 0:
+        from paper_2410_04090_gb300 import repeatability
+        r = repeatability.study(device=dev.index)
+        br_rep = {"angles_deg": r["angles"], "match_radius_px": r["radius_px"], "size": r["size"],
+                  "eps": r["eps"], "labeled_corners_per_scene": r["corners_per_scene"],
+                  "crf_ms_per_batch_of_angles": r["crf_ms"]}
+        for set_name in repeatability.SCENES:
+            br_rep[set_name] = {name: {"p_max": d["p_max"], "mean_f1": d["mean_f1"],
+                                       "f1": [round(v, 4) for v in d["f1"]]}
+                                for name, d in r[set_name].items()}
+
     e2e = None
     if not args.only_batched:
         e2e = run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, stream)
     if rank == 0:
         emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks,
-             tuning, skip_quality, dev.index, refine, track, fc_abl)
+             tuning, skip_quality, dev.index, refine, track, fc_abl, br_rep)
     fe.close()
     for extra in [graph_fe, skip_fe] + extra_fes:
         if extra:
@@ -738,7 +752,7 @@ def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, 
 
 
 def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks, tuning,
-         skip_quality, dev_index, refine=None, track=None, fc_abl=None):
+         skip_quality, dev_index, refine=None, track=None, fc_abl=None, br_rep=None):
     import numpy as np
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
@@ -783,7 +797,7 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
                        "pairs_per_step": n, "mode": args.mode, "detect_tile_px": list(tuning),
                        "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
             "modes": mode_values, "learned_skip": skip_quality, "refine": refine, "track": track,
-            "fc_ablation": fc_abl,
+            "fc_ablation": fc_abl, "br_repeatability": br_rep,
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks.summary(), "gpu_launches": launches[args.mode] * args.steps,
             "keypoints_per_image_mean": float(np.mean(counts))}

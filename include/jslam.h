@@ -187,6 +187,18 @@ jslam_status jslam_fc_ablation_view(jslam_ctx *ctx, int32_t pair, int32_t side, 
                                     const uint32_t **ablation_keys, const uint32_t **fused_keys,
                                     int32_t *cells_x, int32_t *cells_y);
 
+/* Device view of one level's CRF-matrix from the last jslam_fc_ablation()
+ * (Sec. II-C-1: the corner response of every pixel before culling): Eq. 1-3
+ * at the image's primary threshold with the context's P_min, P_max, the
+ * SAD response of every corner and 0 for every other pixel and inside the
+ * border; height x width uint16, row-major, no padding, ctx-owned and valid
+ * until the next extraction or ablation.  The repeatability study of
+ * Bounded Rectification reads its corner sets here.  JSLAM_ERR_STATE before
+ * an ablation; JSLAM_ERR_ARG for a pair, side or level outside the last
+ * batch or a null output. */
+jslam_status jslam_crf_view(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t level, const uint16_t **crf,
+                            int32_t *width, int32_t *height);
+
 /* Milliseconds of the ablation's CRF-matrix kernel and of its culling
  * kernels (after jslam_sync). */
 jslam_status jslam_fc_ablation_times(jslam_ctx *ctx, float *crf_ms, float *fc_ms);

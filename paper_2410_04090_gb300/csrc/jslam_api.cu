@@ -973,6 +973,26 @@ jslam_status jslam_fc_ablation_view(jslam_ctx *ctx, int32_t pair, int32_t side, 
     return JSLAM_OK;
 }
 
+jslam_status jslam_crf_view(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t level, const uint16_t **crf,
+                            int32_t *width, int32_t *height)
+{
+    if (!ctx || !crf || !width || !height) return JSLAM_ERR_ARG;
+    if (!ctx->have_ablation) return JSLAM_ERR_STATE;
+    if (pair < 0 || pair >= (int)ctx->layouts.size() || side < 0 || side > 1) return JSLAM_ERR_ARG;
+    const int img = 2 * pair + side;
+    int base = -1, nl = 0;
+    for (size_t i = 0; i < ctx->h_levels.size(); ++i)
+        if (ctx->h_levels[i].image == img) { if (base < 0) base = (int)i; ++nl; }
+    if (level < 0 || level >= nl) return JSLAM_ERR_ARG;
+    const LevelDesc &L = ctx->h_levels[base + level];
+    const size_t off_bytes = align_up(ctx->h_levels.size() * sizeof(uint64_t), 256);
+    const size_t key_bytes = align_up(ctx->slot_count * sizeof(uint32_t), 256);
+    *crf = ctx->abl.as<uint16_t>(off_bytes + key_bytes) + ctx->abl_off[base + level];
+    *width = L.W;
+    *height = L.H;
+    return JSLAM_OK;
+}
+
 jslam_status jslam_fc_ablation_times(jslam_ctx *ctx, float *crf_ms, float *fc_ms)
 {
     if (!ctx || !crf_ms || !fc_ms) return JSLAM_ERR_ARG;

@@ -244,3 +244,102 @@ def random_image(height: int, width: int, seed: int, kind: str = "polygons") -> 
     rng = _rng(seed)
     t = _texture(rng, height, width, 2000.0)
     return _finish(t, rng, 2.0)
+
+
+@dataclass
+class CornerScene:
+    image: np.ndarray     # uint8 [H, W]
+    corners: np.ndarray   # float64 [N, 2]: (x, y) of every polygon vertex; pixel (i, j) covers [i, i+1) x [j, j+1)
+
+
+def corner_polygons(width: int, height: int, seed: int, polygons: int = 14, rmin: float = 10.0,
+                    rmax: float = 24.0, margin: float = 24.0):
+    """Labeled shapes for the repeatability study of Bounded Rectification:
+    convex polygons inscribed in circles (3-6 vertices, every interior angle
+    in [30, 150] degrees), pairwise 6 px apart, inside the disc about the
+    image centre that keeps them `margin` px from every edge under any
+    rotation; background and fills at least 40 grey levels apart.
+    Returns (background, [(vertices [nv, 2], fill, (cx, cy, r)), ...])."""
+    rng = _rng(seed)
+    cx, cy = width / 2.0, height / 2.0
+    reach = min(width, height) / 2.0 - rmax - margin
+    bg = float(rng.integers(80, 177))
+    shapes = []
+    tries = 0
+    while len(shapes) < polygons and tries < 20000:
+        tries += 1
+        r = rng.uniform(rmin, rmax)
+        rho, th = reach * np.sqrt(rng.uniform()), rng.uniform(0, 2 * np.pi)
+        px, py = cx + rho * np.cos(th), cy + rho * np.sin(th)
+        if any(np.hypot(px - qx, py - qy) < r + qr + 6.0 for _, _, (qx, qy, qr) in shapes):
+            continue
+        nv = int(rng.integers(3, 7))
+        phi = np.sort(rng.uniform(0, 2 * np.pi, nv))
+        gaps = np.diff(np.concatenate([phi, phi[:1] + 2 * np.pi]))
+        # inscribed polygon: the interior angle at vertex i is pi - (gap before + gap after) / 2
+        interior = np.pi - (gaps + np.roll(gaps, 1)) / 2.0
+        if interior.min() < np.radians(30) or interior.max() > np.radians(150):
+            continue
+        fill = float(rng.integers(0, 256))
+        if abs(fill - bg) < 40:
+            continue
+        verts = np.stack([px + r * np.cos(phi), py + r * np.sin(phi)], axis=1)
+        shapes.append((verts, fill, (px, py, r)))
+    return bg, shapes
+
+
+def corner_scene(width: int, height: int, angle_deg: float, seed: int, polygons: int = 14,
+                 supersample: int = 4, sigma: float = 2.0, dots: int = 0) -> CornerScene:
+    """The shapes of corner_polygons(seed) rotated by angle_deg about the image
+    centre (counter-clockwise on screen, y down), rendered with area
+    coverage from supersample^2 samples per pixel, plus Gaussian noise of
+    sigma (seeded by the seed and the angle).  `dots` unlabeled discs of
+    radius 1-2 px (contrast >= 40, 6 px clear of the polygons' circles,
+    rotating with the scene) stand in for the specks and blobs of real
+    images, which are not corners."""
+    bg, shapes = corner_polygons(width, height, seed, polygons)
+    cx, cy = width / 2.0, height / 2.0
+    items = [(v, f, True) for v, f, _ in shapes]
+    if dots:
+        drng = _rng(seed * 7919 + 17)
+        reach = min(width, height) / 2.0 - 30.0
+        placed = 0
+        while placed < dots:
+            rho, th = reach * np.sqrt(drng.uniform()), drng.uniform(0, 2 * np.pi)
+            px, py = cx + rho * np.cos(th), cy + rho * np.sin(th)
+            rd = drng.uniform(1.0, 2.0)
+            if any(np.hypot(px - qx, py - qy) < qr + rd + 6.0 for _, _, (qx, qy, qr) in shapes):
+                continue
+            fill = float(drng.integers(0, 256))
+            if abs(fill - bg) < 40:
+                continue
+            k = np.arange(16) * (2 * np.pi / 16)
+            items.append((np.stack([px + rd * np.cos(k), py + rd * np.sin(k)], axis=1), fill, False))
+            placed += 1
+    a = np.radians(angle_deg)
+    ca, sa = np.cos(a), np.sin(a)
+    img = np.full((height, width), bg)
+    corners = []
+    ss = supersample
+    for verts, fill, labeled in items:
+        dx, dy = verts[:, 0] - cx, verts[:, 1] - cy
+        v = np.stack([cx + ca * dx + sa * dy, cy - sa * dx + ca * dy], axis=1)
+        if labeled:
+            corners.append(v)
+        x0, x1 = int(np.floor(v[:, 0].min())), int(np.ceil(v[:, 0].max())) + 1
+        y0, y1 = int(np.floor(v[:, 1].min())), int(np.ceil(v[:, 1].max())) + 1
+        sx = x0 + (np.arange((x1 - x0) * ss) + 0.5) / ss
+        sy = y0 + (np.arange((y1 - y0) * ss) + 0.5) / ss
+        px, py = np.meshgrid(sx, sy)
+        inside = np.ones(px.shape, bool)
+        nv = len(v)
+        area2 = sum(v[i, 0] * v[(i + 1) % nv, 1] - v[(i + 1) % nv, 0] * v[i, 1] for i in range(nv))
+        for i in range(nv):  # convex: inside every edge's half-plane (orientation from the signed area)
+            ax, ay = v[i]
+            bx, by = v[(i + 1) % nv]
+            cross = (bx - ax) * (py - ay) - (by - ay) * (px - ax)
+            inside &= cross * np.sign(area2) >= 0
+        cov = inside.reshape(y1 - y0, ss, x1 - x0, ss).mean(axis=(1, 3))
+        img[y0:y1, x0:x1] = img[y0:y1, x0:x1] * (1 - cov) + fill * cov
+    rng = _rng(seed * 1000003 + int(round((angle_deg % 360.0) * 1000)))
+    return CornerScene(_finish(img, rng, sigma), np.concatenate(corners) if corners else np.zeros((0, 2)))
