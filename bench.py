@@ -785,6 +785,18 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
                                                 "algorithmic_bytes_per_launch")}}
         roof["stage_ms_per_launch"] = stage_ms
         roof["stage_timing"] = "CUDA events on the context stream between the stages of the batched mode's timed steps"
+    # the whole path against HBM: per image, L0 read once, raw levels n >= 1
+    # and blurred levels written once, 48 bytes per keypoint out (keypoint
+    # record + descriptor), over the headline throughput
+    path_bytes = 0
+    for i, (pr, p) in enumerate(zip(pairs, params)):
+        px = level_pixels(pr.left.shape[1], pr.left.shape[0], p["levels"], p["scale"])
+        A = sum(px)
+        path_bytes += sum(px[0] + (A - px[0]) + A + 48 * counts[2 * i + s] for s in (0, 1))
+    per_pair = path_bytes / max(n, 1)
+    path_hbm = {"algorithmic_bytes_per_pair": per_pair, "achieved": per_pair * value / 1e9, "peak": peak,
+                "unit": "GB/s", "frac": per_pair * value / 1e9 / peak,
+                "definition": "A0 (1 + (S_L - 1) + S_L) + 48 N_kp per image, at the headline pairs/s"}
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args, pairs, params, lo)
     launches = {"batched": LAUNCHES_PER_CALL, "graph": LAUNCHES_PER_CALL, "plain": LAUNCHES_PER_CALL * n,
                 "learned_skip": LAUNCHES_PER_CALL + 2, "streams2": 2 * LAUNCHES_PER_CALL,
@@ -798,7 +810,7 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
                        "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
             "modes": mode_values, "learned_skip": skip_quality, "refine": refine, "track": track,
             "fc_ablation": fc_abl, "br_repeatability": br_rep,
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roof, "path_hbm": path_hbm, "cpu_baseline": cpu, "e2e": e2e,
             "clocks": clocks.summary(), "gpu_launches": launches[args.mode] * args.steps,
             "keypoints_per_image_mean": float(np.mean(counts))}
     print(json.dumps(line), flush=True)
