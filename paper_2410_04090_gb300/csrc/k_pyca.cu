@@ -126,7 +126,7 @@ __device__ __forceinline__ int block_excl_scan(int v, int *ws, int *total)
     return pre + x - v;
 }
 
-__global__ void __launch_bounds__(kFinThreads) k_pfa_finalize(Batch b)
+__global__ void __launch_bounds__(kFinThreads, 2) k_pfa_finalize(Batch b)
 {
     __shared__ int ws[32];
     __shared__ int hist[256];
