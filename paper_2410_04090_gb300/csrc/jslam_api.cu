@@ -585,6 +585,8 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.fast_tile_level = reinterpret_cast<const int32_t *>(dplan + o_ftl);
     b.tile_rec = reinterpret_cast<const TileRec *>(dplan + o_trec);
     b.n_images = n_img; b.n_levels = n_levels; b.n_pairs = n; b.n_segments = n_segs;
+    b.max_segment = 0;
+    for (int l = 0; l < n_levels; ++l) b.max_segment = std::max(b.max_segment, levels[l].cells_x * k);
     b.pyr_tiles = pyr; b.fast_tiles = fast; b.max_capacity = max_cap;
     b.fast_max_box = max_box; b.fast_max_px = max_px; b.fast_max_cells = max_cells;
     b.fast_bits = ctx->prm.p_min == 9 && ctx->prm.p_max == 13;

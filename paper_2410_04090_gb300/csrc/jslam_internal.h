@@ -159,6 +159,7 @@ struct Batch {
     const int32_t *fast_tile_level; // level index of each detection tile
     const int32_t *seg_level;       // level index of each segment
     int32_t n_images, n_levels, n_pairs, n_segments;
+    int32_t max_segment;            // largest segment (cells_x x k slots) of the batch
     int32_t pyr_tiles, fast_tiles;
     int32_t max_capacity;           // largest keypoint capacity of any image
     int32_t fast_smem;              // dynamic shared memory of the detection kernel

@@ -1,6 +1,8 @@
 // Pyramidal Feature Aggregation, steps 3 and the aggregation (Sec. II-C-2).
 //
-// k_pfa_nms       one CTA per segment = (image, level, cell row).  Each
+// k_pfa_nms       one CTA per segment = (image, level, cell row), or one warp
+//                 per segment (four per CTA) when every segment of the batch
+//                 has at most 96 slots.  Each
 //                 culled corner reads its own packed (K_l, K_r) and those of
 //                 the q x q window around its s0 projection from the score map
 //                 filled by the detection kernel, and is suppressed when a
@@ -90,10 +92,105 @@ __global__ void __launch_bounds__(kNmsThreads) k_pfa_nms(Batch b)
     if (threadIdx.x == 0) b.seg_count[seg] = alive_total;
 }
 
+// The same per segment with one warp, for batches whose segments (cell rows:
+// cells_x x k slots) all have at most 32 S slots: lane l takes slots l,
+// l + 32, ..., and every step of their chains of dependent loads (slot ->
+// projection -> own score -> neighbours) is issued for all S slots before
+// the next, so the chains overlap; a CTA of four warps takes four segments.
+template <int S>
+__global__ void __launch_bounds__(kNmsThreads) k_pfa_nms_warp(Batch b)
+{
+    __shared__ uint32_t sk[kNmsThreads / 32][32 * S];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int seg = blockIdx.x * (kNmsThreads / 32) + warp;
+    if (seg >= b.n_segments) return;  // whole warps only
+    const LevelDesc &L = b.levels[b.seg_level[seg]];
+    const ImageDesc &I = b.images[L.image];
+    const int k = b.prm.k, rad = b.prm.nms_rad, rule = b.prm.rule;
+    const int cy = seg - L.seg_base;
+    const int m = L.cells_x * k;
+    if (m > 32 * S) {  // the host launches this kernel only when no segment is wider
+        if (lane == 0) { atomicOr(b.err, kErrSegment); b.seg_count[seg] = 0; }
+        return;
+    }
+    const int base = L.slot_base + cy * m;
+    const int W0 = I.W0, H0 = I.H0;
+    uint32_t key[S], own[S];
+    int X[S], Y[S], px[S], py[S];
+    bool dom[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) key[q] = lane + 32 * q < m ? b.slots[base + lane + 32 * q] : 0u;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        X[q] = Y[q] = px[q] = py[q] = 0;
+        if (key[q]) {
+            const SlotPos p = decode_slot(key[q], cy * m + lane + 32 * q, L.cells_x, L.c, k);
+            px[q] = p.x; py[q] = p.y;
+            X[q] = __ldg(L.projx + p.x);
+            Y[q] = __ldg(L.projy + p.y);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        own[q] = key[q] ? I.map[(size_t)Y[q] * W0 + X[q]] : 0u;
+        dom[q] = false;
+    }
+    for (int dy = -rad; dy <= rad; ++dy)
+        for (int dx = -rad; dx <= rad; ++dx) {
+            if ((dx | dy) == 0) continue;
+            uint32_t w[S];
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+                const int qx = X[q] + dx, qy = Y[q] + dy;
+                w[q] = key[q] && qx >= 0 && qx < W0 && qy >= 0 && qy < H0 ? I.map[(size_t)qy * W0 + qx] : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < S; ++q)
+                if (w[q]) {
+                    const uint32_t ql = w[q] >> 16, qr = w[q] & 0xFFFFu, kl = own[q] >> 16, kr = own[q] & 0xFFFFu;
+                    dom[q] |= rule == 0 ? (ql > kl && qr > kr) : (ql > kl || (ql == kl && qr > kr));
+                }
+        }
+    uint32_t v[S];
+    int alive = 0;
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        v[q] = 0xFFFFFFFFu;
+        if (key[q]) {
+            b.slot_k[base + lane + 32 * q] = own[q];
+            if (!dom[q]) { v[q] = ((uint32_t)py[q] << 16) | (uint32_t)px[q]; ++alive; }
+        }
+        sk[warp][lane + 32 * q] = v[q];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < S; ++q)
+        if (lane + 32 * q < m) {
+            int rank = -1;
+            if (v[q] != 0xFFFFFFFFu) {
+                rank = 0;
+                for (int j = 0; j < m; ++j) rank += sk[warp][j] < v[q];
+            }
+            b.slot_rank[base + lane + 32 * q] = rank;
+        }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) alive += __shfl_xor_sync(0xFFFFFFFFu, alive, off);
+    if (lane == 0) b.seg_count[seg] = alive;
+}
+
 cudaError_t launch_pfa_nms(const Batch &b, cudaStream_t stream)
 {
     if (b.n_segments == 0) return cudaSuccess;
-    k_pfa_nms<<<b.n_segments, kNmsThreads, 0, stream>>>(b);
+    constexpr int per = kNmsThreads / 32;
+    if (b.max_segment <= 32) {
+        k_pfa_nms_warp<1><<<(b.n_segments + per - 1) / per, kNmsThreads, 0, stream>>>(b);
+    } else if (b.max_segment <= 64) {
+        k_pfa_nms_warp<2><<<(b.n_segments + per - 1) / per, kNmsThreads, 0, stream>>>(b);
+    } else if (b.max_segment <= 96) {
+        k_pfa_nms_warp<3><<<(b.n_segments + per - 1) / per, kNmsThreads, 0, stream>>>(b);
+    } else {
+        k_pfa_nms<<<b.n_segments, kNmsThreads, 0, stream>>>(b);
+    }
     return cudaGetLastError();
 }
 

@@ -129,6 +129,26 @@ def test_parameter_variants(J, oracle, kw):
     _check_pair(J, oracle, pair.left, pair.right, p)
 
 
+def test_wide_segments(J, oracle):
+    """Segments (cell rows of a level) of 1248 candidate slots -- k = 8 per
+    8 px cell on a 1241-wide image -- in the one-CTA-per-segment NMS kernel
+    (batches whose segments have at most 96 slots use one warp per segment)."""
+    pair = scenes.planes_pair(1241, 376, 0, 31, 32)
+    p = params_from(oracle, levels=2, max_feats=3000, cell=8, k_per_cell=8)
+    _check_pair(J, oracle, pair.left, pair.right, p)
+
+
+@pytest.mark.parametrize("w,h,k", [(640, 480, 1), (1241, 376, 1), (640, 300, 3), (640, 300, 5)])
+def test_narrow_segments(J, oracle, w, h, k):
+    """Largest segment (cells per row x k) of 22 slots (640 px), 42 (1241 px)
+    and 66 (3 per cell on 640 px) -- the warp-per-segment NMS kernel with
+    one, two and three slots per lane -- and 110 (5 per cell: the CTA
+    kernel)."""
+    pair = scenes.planes_pair(w, h, 0, 41, 42)
+    p = params_from(oracle, levels=6, max_feats=1500, fast_thresh_lo=7, k_per_cell=k)
+    _check_pair(J, oracle, pair.left, pair.right, p)
+
+
 def test_maximum_image_size(J, oracle):
     """The largest accepted image, 4096 x 4096 with 8 levels and 4000 features:
     keypoints, descriptors and angles against the oracle (one image, used as
