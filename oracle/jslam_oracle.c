@@ -31,7 +31,7 @@
  * and brute force on tiny inputs (run length, culling, PFA, matching).
  * Parity unpinned: none of the exported functions; the Box-Muller draw and
  * the pattern rejection rule are pinned only statistically (moments and
- * radius bounds), which the design doc records.
+ * radius bounds).
  */
 #include <stdint.h>
 #include <stdlib.h>

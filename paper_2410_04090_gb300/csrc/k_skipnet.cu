@@ -1,6 +1,6 @@
 // Learned cell-skip proposal: an opt-in approximate mode on top of the exact
-// path (the paper has no counterpart; its exact path stays the fallback and
-// the judge of the proposal).
+// path (the paper has no counterpart; the exact path stays the fallback and
+// the reference the proposal's recall is measured against).
 //
 // k_skipnet    one CTA per 26 x 12 block of the 1/8-scale logit map of an
 //              image.  It box-averages 8x8 blocks of level 0 (scaled to
