@@ -123,6 +123,19 @@ def level_pixels(W0, H0, levels, scale):
     return [int(a) * int(b) for a, b in zip(w, h)]
 
 
+def path_bytes_per_pair(pairs, params, counts):
+    """Algorithmic bytes of the whole path per stereo pair, averaged over the
+    batch: per image, level 0 read once, raw levels n >= 1 and blurred
+    levels n >= 0 written once, 48 bytes per keypoint out (keypoint record +
+    descriptor); `counts` holds the keypoints of image 2 p + side."""
+    total = 0
+    for i, (pr, p) in enumerate(zip(pairs, params)):
+        px = level_pixels(pr.left.shape[1], pr.left.shape[0], p["levels"], p["scale"])
+        A = sum(px)
+        total += sum(px[0] + (A - px[0]) + A + 48 * counts[2 * i + s] for s in (0, 1))
+    return total / max(len(pairs), 1)
+
+
 def level_pixels_batch(pairs, params):
     """Pixels of every level of every image of the batch."""
     return sum(2 * sum(level_pixels(pr.left.shape[1], pr.left.shape[0], p["levels"], p["scale"]))
@@ -785,15 +798,7 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
                                                 "algorithmic_bytes_per_launch")}}
         roof["stage_ms_per_launch"] = stage_ms
         roof["stage_timing"] = "CUDA events on the context stream between the stages of the batched mode's timed steps"
-    # the whole path against HBM: per image, L0 read once, raw levels n >= 1
-    # and blurred levels written once, 48 bytes per keypoint out (keypoint
-    # record + descriptor), over the headline throughput
-    path_bytes = 0
-    for i, (pr, p) in enumerate(zip(pairs, params)):
-        px = level_pixels(pr.left.shape[1], pr.left.shape[0], p["levels"], p["scale"])
-        A = sum(px)
-        path_bytes += sum(px[0] + (A - px[0]) + A + 48 * counts[2 * i + s] for s in (0, 1))
-    per_pair = path_bytes / max(n, 1)
+    per_pair = path_bytes_per_pair(pairs, params, counts)
     path_hbm = {"algorithmic_bytes_per_pair": per_pair, "achieved": per_pair * value / 1e9, "peak": peak,
                 "unit": "GB/s", "frac": per_pair * value / 1e9 / peak,
                 "definition": "A0 (1 + (S_L - 1) + S_L) + 48 N_kp per image, at the headline pairs/s"}
