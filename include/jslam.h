@@ -187,6 +187,15 @@ jslam_status jslam_fc_ablation_view(jslam_ctx *ctx, int32_t pair, int32_t side, 
                                     const uint32_t **ablation_keys, const uint32_t **fused_keys,
                                     int32_t *cells_x, int32_t *cells_y);
 
+/* Failure-detection self-test (no counterpart in the paper): enqueues one
+ * kernel whose bounded wait -- on an mbarrier that nothing arrives on, the
+ * wait the detection kernels use for their tile loads -- runs out after
+ * about a second and sets the context's timeout flag.  The next jslam_sync()
+ * returns JSLAM_ERR_TIMEOUT, and the context keeps that status (create a new
+ * one to continue); the device itself stays usable.  JSLAM_ERR_ARG for a
+ * null context; the context's own status if it already failed. */
+jslam_status jslam_selftest_wait(jslam_ctx *ctx);
+
 /* Device view of one level's CRF-matrix from the last jslam_fc_ablation()
  * (Sec. II-C-1: the corner response of every pixel before culling): Eq. 1-3
  * at the image's primary threshold with the context's P_min, P_max, the

@@ -975,6 +975,18 @@ jslam_status jslam_fc_ablation_view(jslam_ctx *ctx, int32_t pair, int32_t side, 
     return JSLAM_OK;
 }
 
+jslam_status jslam_selftest_wait(jslam_ctx *ctx)
+{
+    if (!ctx) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    uint32_t *err = reinterpret_cast<uint32_t *>(ctx->counts.as<int32_t>() + 2 * (size_t)ctx->cfg.max_pairs);
+    cudaError_t e = launch_wait_selftest(err, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, e);
+    return enqueue_counts(ctx);
+}
+
 jslam_status jslam_crf_view(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t level, const uint16_t **crf,
                             int32_t *width, int32_t *height)
 {

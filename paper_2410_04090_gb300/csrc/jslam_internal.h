@@ -186,6 +186,7 @@ struct Batch {
 // Kernel launchers (one per stage), all on `stream`.
 cudaError_t launch_pyramid(const Batch &b, cudaStream_t stream);
 cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream);
+cudaError_t launch_wait_selftest(uint32_t *err, cudaStream_t stream);
 cudaError_t launch_pfa_nms(const Batch &b, cudaStream_t stream);
 cudaError_t launch_pfa_finalize(const Batch &b, cudaStream_t stream);
 cudaError_t launch_orient_desc(const Batch &b, cudaStream_t stream);

@@ -394,6 +394,26 @@ __device__ __forceinline__ bool wait_tile(uint64_t *bar, uint32_t parity)
     }
 }
 
+// Failure-detection self-test: a tile wait on an mbarrier that nothing
+// arrives on runs out after its limit, sets kErrTimeout and returns, as the
+// detection kernels do when a tile load does not complete.
+__global__ void k_wait_selftest(uint32_t *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (!wait_tile(&bar, 0u) && threadIdx.x == 0) atomicOr(err, kErrTimeout);
+}
+
+cudaError_t launch_wait_selftest(uint32_t *err, cudaStream_t stream)
+{
+    k_wait_selftest<<<1, 32, 0, stream>>>(err);
+    return cudaGetLastError();
+}
+
 // Corner bits (bit j: pixel 4g + j) of a group of 4 pixels; `base` points at
 // the word left of the group's centre word in the first of its 7 tile rows.
 __device__ __forceinline__ uint32_t group_corners(const uint32_t *base, int wpr, uint32_t e0, uint32_t e1,

@@ -99,7 +99,7 @@ SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extra
            "jslam_autotune", "jslam_graph_capture", "jslam_graph_launch", "jslam_set_skip_model",
            "jslam_get_skip_view", "jslam_result_range", "jslam_download_range", "jslam_refine_matches",
            "jslam_get_refined", "jslam_result_refined_view", "jslam_track", "jslam_fc_ablation",
-           "jslam_fc_ablation_view", "jslam_fc_ablation_times", "jslam_crf_view")
+           "jslam_fc_ablation_view", "jslam_fc_ablation_times", "jslam_crf_view", "jslam_selftest_wait")
 STAGES = ("pyramid", "skip", "detect", "pfa_nms", "pfa_final", "orb", "match", "refine")
 
 _lib = None
@@ -144,6 +144,8 @@ def lib():
         L.jslam_crf_view.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p),
                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.jslam_crf_view.restype = st
+        L.jslam_selftest_wait.argtypes = [C.c_void_p]
+        L.jslam_selftest_wait.restype = st
         L.jslam_refine_matches.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_float]
         L.jslam_refine_matches.restype = st
         L.jslam_get_refined.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Refined)]
@@ -422,6 +424,11 @@ class Frontend:
         w, h = C.c_int32(), C.c_int32()
         _check(lib().jslam_crf_view(self._h, pair, side, level, C.byref(p), C.byref(w), C.byref(h)), "jslam_crf_view")
         return _device_view(p.value, (h.value, w.value), np.uint16, self.device)
+
+    def selftest_wait(self):
+        """Enqueue the failure-detection self-test: the next sync() raises with
+        JSLAM_ERR_TIMEOUT after about a second."""
+        _check(lib().jslam_selftest_wait(self._h), "jslam_selftest_wait")
 
     def fc_ablation_times(self):
         a, b = C.c_float(), C.c_float()
