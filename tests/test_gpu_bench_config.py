@@ -1,8 +1,9 @@
-"""Parity in the launch configuration the benchmark times: the 100-pair
-KITTI-shaped batch split over four contexts on four streams, each part
-replayed as a captured CUDA graph, 128x128 detection tiles.  Four sampled
-pairs (one per context) are compared with the oracle bit for bit; all 100
-pairs are checked against properties that hold at any size."""
+"""Parity in the launch configuration the benchmark times: a 100-pair batch
+(KITTI-shaped, EuRoC-shaped, 1920x1080) split over four contexts on four
+streams, each part replayed as a captured CUDA graph, 128x128 detection
+tiles.  Four sampled pairs (one per context) are compared with the oracle
+bit for bit; all 100 pairs are checked against properties that hold at any
+size."""
 import numpy as np
 import pytest
 
@@ -11,7 +12,6 @@ from parity_util import compare_keypoints, compare_matches, params_from
 
 pytestmark = pytest.mark.gpu
 
-WL = "kitti_1241x376_L8"
 N = 100
 PARTS = 4
 SAMPLES = (0, 37, 62, 99)
@@ -25,9 +25,10 @@ def J():
     return jslam
 
 
-@pytest.fixture(scope="module")
-def run(J):
+@pytest.fixture(scope="module", params=["kitti_1241x376_L8", "euroc_752x480_L8", "fhd_1920x1080_L8"])
+def run(J, request):
     import torch
+    WL = request.param
     w = scenes.WORKLOADS[WL]
     frames = [scenes.workload_pair(WL, f) for f in range(N)]
     dev = torch.device("cuda", 0)
