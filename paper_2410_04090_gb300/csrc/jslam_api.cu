@@ -168,6 +168,7 @@ struct jslam_ctx {
     // constant tables
     GrowBuf consts;  // pattern | cos | sin | corner table
     int8_t *d_pattern = nullptr;
+    uint32_t *d_pattern_off = nullptr;
     double *d_cos = nullptr, *d_sin = nullptr;
     float *d_cosf = nullptr, *d_sinf = nullptr;
     uint32_t *d_lut = nullptr;
@@ -603,6 +604,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.seg_count = reinterpret_cast<int32_t *>(sw + 4 * slot_words);
     b.seg_off = reinterpret_cast<int32_t *>(sw + 4 * slot_words + seg_words);
     b.pattern = ctx->d_pattern;
+    b.pattern_off = ctx->d_pattern_off;
     b.bin_cos = ctx->d_cos;
     b.bin_sin = ctx->d_sin;
     b.bin_cosf = ctx->d_cosf;
@@ -710,7 +712,8 @@ jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
     const size_t pat_bytes = (size_t)kBins * kPairs * 4;
     const size_t lut_off = pat_bytes + 2 * kBins * sizeof(double);
     const size_t f_off = lut_off + kLutWords * sizeof(uint32_t);
-    const size_t const_bytes = f_off + 2 * kBins * sizeof(float);
+    const size_t po_off = f_off + 2 * kBins * sizeof(float);
+    const size_t const_bytes = po_off + (size_t)kBins * kPairs * sizeof(uint32_t);
     if (e == cudaSuccess) e = ctx->consts.ensure(const_bytes + 512, false, nullptr);
     if (e == cudaSuccess) {
         std::vector<char> h(const_bytes, 0);
@@ -720,6 +723,14 @@ jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
         corner_table(c.p_min, c.p_max, reinterpret_cast<uint32_t *>(h.data() + lut_off));
         float *cf = reinterpret_cast<float *>(h.data() + f_off);
         for (int i = 0; i < 2 * kBins; ++i) cf[i] = static_cast<float>(cs[i]);
+        // the same pattern as offsets into the staged patch (row pitch kPatPitch)
+        const int8_t *pt = reinterpret_cast<const int8_t *>(h.data());
+        uint32_t *po = reinterpret_cast<uint32_t *>(h.data() + po_off);
+        for (int i = 0; i < kBins * kPairs; ++i) {
+            const int op = pt[4 * i + 1] * kPatPitch + pt[4 * i + 0];
+            const int oq = pt[4 * i + 3] * kPatPitch + pt[4 * i + 2];
+            po[i] = (uint32_t)(uint16_t)(int16_t)op | ((uint32_t)(uint16_t)(int16_t)oq << 16);
+        }
         e = cudaMemcpy(ctx->consts.ptr, h.data(), h.size(), cudaMemcpyHostToDevice);
         ctx->d_pattern = ctx->consts.as<int8_t>();
         ctx->d_cos = ctx->consts.as<double>(pat_bytes);
@@ -727,6 +738,7 @@ jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
         ctx->d_lut = ctx->consts.as<uint32_t>(lut_off);
         ctx->d_cosf = ctx->consts.as<float>(f_off);
         ctx->d_sinf = ctx->d_cosf + kBins;
+        ctx->d_pattern_off = ctx->consts.as<uint32_t>(po_off);
     }
     if (e == cudaSuccess) e = ctx->counts.ensure(sizeof(int32_t) * (2 * (size_t)c.max_pairs + 8), true, nullptr);
     if (e == cudaSuccess) {

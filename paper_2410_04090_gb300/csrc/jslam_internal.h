@@ -21,6 +21,8 @@ constexpr int kMaxLevels = 8;
 constexpr int kBins = 30;        // orientation sectors of 12 degrees
 constexpr int kPairs = 256;      // BRIEF point pairs
 constexpr int kDiskR = 15;       // intensity-centroid disk radius
+constexpr int kPatR = 13;        // rotated BRIEF offsets lie in [-13, 13]
+constexpr int kPatPitch = 32;    // row pitch of the staged 27 x 27 BRIEF patch (8 aligned words)
 constexpr int kMaxSegment = 4096;  // candidate slots per (level, cell row)
 constexpr int kMaxImages = 256;    // images per batch (two per stereo pair)
 
@@ -175,6 +177,7 @@ struct Batch {
     int32_t *seg_off;               // exclusive prefix of seg_count per image
     int32_t *canon;                 // slot of each canonical position
     const int8_t *pattern;          // kBins x kPairs x 4
+    const uint32_t *pattern_off;    // kBins x kPairs: int16 patch offsets of p | of q << 16 (pitch kPatPitch)
     const double *bin_cos, *bin_sin;
     const float *bin_cosf, *bin_sinf;  // the same tables rounded to float (fast sector test)
     uint32_t *err;

@@ -22,9 +22,7 @@
 
 namespace jslam {
 
-constexpr int kPatR = 13;                 // rotated BRIEF offsets lie in [-13, 13]
 constexpr int kPatW = 2 * kPatR + 1;      // 27
-constexpr int kPatPitch = 32;             // patch rows staged as 8 aligned words
 constexpr int kDiskWords = 9;             // aligned words covering the 31 disk columns of a row
 // largest |dx| with dx^2 + dy^2 <= kDiskR^2, by |dy|
 __constant__ int8_t c_disk_umax[kDiskR + 1] = { 15, 14, 14, 14, 14, 14, 13, 13, 12, 12, 11, 10, 9, 7, 5, 0 };
@@ -67,30 +65,34 @@ __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
         }
     }
     // Disk moments: 31 rows x 9 words from word column (x - 15) / 4 of the
-    // raw level.  Per word, the bytes inside the disk (|dx| <= umax(|dy|))
-    // are kept and two byte dot products give the row sum and the sum of
-    // (dx + 18) I (weights 3..36, unsigned); m10 = that - 18 sum I.
+    // raw level.  Lane l < 27 keeps word column l mod 9 and takes rows
+    // l / 9, l / 9 + 3, ...; per word, the bytes inside the disk
+    // (|dx| <= umax(|dy|)) are kept and two byte dot products give the row
+    // sum and the sum of (dx + 18) I (weights 3..36, unsigned, fixed per
+    // lane); m10 = that - 18 sum I.
     int m10 = 0, m01 = 0;
-    {
+    if (lane < 3 * kDiskWords) {
         const int dw0 = (x - kDiskR) >> 2;
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(raw + (size_t)(y - kDiskR) * pitch) + dw0;
+        const int w = lane % kDiskWords, r0 = lane / kDiskWords;
+        const int cx0 = 4 * (dw0 + w) - x;  // dx of the word's byte 0
+        const uint32_t wdx = (uint32_t)(cx0 + 18) * 0x01010101u + 0x03020100u;
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(raw + (size_t)(y - kDiskR + r0) * pitch) + dw0 + w;
+        const size_t step = (size_t)3 * (pitch >> 2);
         int s = 0, sw = 0;
 #pragma unroll
-        for (int k = 0; k < ((2 * kDiskR + 1) * kDiskWords + 31) / 32; ++k) {
-            const int it = k * 32 + lane;
-            if (it < (2 * kDiskR + 1) * kDiskWords) {
-                const int r = it / kDiskWords, w = it - r * kDiskWords;
-                const uint32_t v = __ldg(src + (size_t)r * (pitch >> 2) + w);
+        for (int k = 0; k < (2 * kDiskR + 1 + 2) / 3; ++k) {
+            const int r = r0 + 3 * k;
+            if (r <= 2 * kDiskR) {
+                const uint32_t v = __ldg(src + k * step);
                 const int dy = r - kDiskR;
                 const int um = c_disk_umax[abs(dy)];
-                const int cx0 = 4 * (dw0 + w) - x;  // dx of the word's byte 0
                 const int lo = max(-um - cx0, 0), hi = min(um - cx0, 3);
                 const uint32_t mask = hi < lo ? 0u : (0xFFFFFFFFu >> (24 - 8 * (hi - lo))) << (8 * lo);
                 const uint32_t vm = v & mask;
                 const int rs = (int)__dp4a(vm, 0x01010101u, 0u);
                 s += rs;
                 m01 += dy * rs;
-                sw += (int)__dp4a(vm, (uint32_t)(cx0 + 18) * 0x01010101u + 0x03020100u, 0u);
+                sw += (int)__dp4a(vm, wdx, 0u);
             }
         }
         m10 = sw - 18 * s;
@@ -127,14 +129,14 @@ __global__ void __launch_bounds__(256) k_orient_desc(Batch b)
     const int bin = (zero || T == 0) ? 0 : __ffs(T) - 1;
 
     __syncwarp();  // the patch is complete
-    const char4 *pat = reinterpret_cast<const char4 *>(b.pattern) + (size_t)bin * kPairs;
+    const uint32_t *pat = b.pattern_off + (size_t)bin * kPairs;
     const uint8_t *centre = patch + kPatR * kPatPitch + (x - kPatR - 4 * pw0) + kPatR;
     uint32_t myword = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) {
-        const char4 pq = __ldg(pat + w * 32 + lane);
-        const int a = centre[pq.y * kPatPitch + pq.x];
-        const int c = centre[pq.w * kPatPitch + pq.z];
+        const uint32_t o = __ldg(pat + w * 32 + lane);  // offsets of p and q in the staged patch
+        const int a = centre[(int16_t)(o & 0xFFFFu)];
+        const int c = centre[(int16_t)(o >> 16)];
         const uint32_t word = __ballot_sync(0xFFFFFFFFu, a < c);
         if (lane == w) myword = word;
     }
