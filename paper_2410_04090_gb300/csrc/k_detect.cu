@@ -732,7 +732,16 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
 
         if (L.tmap) {
             if (!wait_tile(&bars[cur], cur ? phase1 : phase0)) {
-                if (threadIdx.x == 0) atomicOr(b.err, kErrTimeout);
+                if (threadIdx.x == 0) {
+                    atomicOr(b.err, kErrTimeout);
+                    // wait once more, with the same limit, for this tile's box
+                    // and the next one's, so that no copy lands in the shared
+                    // memory of a CTA that has ended
+                    wait_tile(&bars[cur], cur ? phase1 : phase0);
+                    const int tn = t + (int)gridDim.x;
+                    if (tn < b.fast_tiles && b.levels[tile_geom(b, tn).li].tmap)
+                        wait_tile(&bars[cur ^ 1], cur ? phase0 : phase1);
+                }
                 return;
             }
             if (cur) phase1 ^= 1u; else phase0 ^= 1u;
@@ -965,6 +974,26 @@ __device__ __forceinline__ void issue_rec_tile(const TileRec &R, uint8_t *buf, u
                  "r"((uint32_t)R.prj_bytes_y), "r"(smem_u32(bar)) : "memory");
 }
 
+// Thread 0 of k_fast_bits after the wait for tile t's box ran out: wait once
+// more, with the same limit, for every copy it still has in flight (this
+// box; then either the next tile's box and the record after it, or the next
+// record if its wait ran out too), so that no copy lands in the shared
+// memory of a CTA that has ended.  rph bit s is the parity of the next
+// completion of record barrier 2 + s, phases bit p that of box barrier p.
+__device__ __forceinline__ void drain_bits(const Batch &b, uint64_t *bars, int t, int grid, int cur, int s3,
+                                        uint32_t phases, uint32_t rph, int aborted)
+{
+    wait_tile(&bars[cur], (phases >> cur) & 1u);
+    if (t + grid >= b.fast_tiles) return;
+    const int sn = s3 == 2 ? 0 : s3 + 1, sa = s3 == 0 ? 2 : s3 - 1;
+    if (aborted) {
+        wait_tile(&bars[2 + sn], (rph >> sn) & 1u);
+        return;
+    }
+    wait_tile(&bars[cur ^ 1], (phases >> (cur ^ 1)) & 1u);
+    if (t + 2 * grid < b.fast_tiles) wait_tile(&bars[2 + sa], (rph >> sa) & 1u);
+}
+
 // Bit-sliced ring test (P_min = 9, P_max = 13), the same results as
 // k_fast_cull.  Tiles come with host-made records: thread 0 fetches the
 // record of the tile after next and, once the next tile's record is in,
@@ -1014,7 +1043,14 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
             fetch_rec(b, t0, &recs[0], &bars[2]);
             if (t0 + grid < b.fast_tiles) fetch_rec(b, t0 + grid, &recs[1], &bars[3]);
             if (wait_tile(&bars[2], 0u)) issue_rec_tile(recs[0], buf0, s_prj[0], &bars[0]);
-            else { atomicOr(b.err, kErrTimeout); s_abort = 1; }
+            else {
+                // give up, after waiting once more (same limit) for both
+                // record copies, so that none lands after the CTA has ended
+                atomicOr(b.err, kErrTimeout);
+                s_abort = 1;
+                wait_tile(&bars[2], 0u);
+                if (t0 + grid < b.fast_tiles) wait_tile(&bars[3], 0u);
+            }
         }
         s_rph = 1u;
     }
@@ -1033,16 +1069,18 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
             // the next tile's record was fetched one tile ago; the slot of the
             // tile after it, the other box and its projections were last read
             // before the barrier that ended the previous tile
+            // (after a record wait runs out nothing more is issued; the CTA
+            // stops at the abort check after the tile's bit-plane barrier)
             if (t + grid < b.fast_tiles) {
                 const int sn = s3 == 2 ? 0 : s3 + 1;
-                if (wait_tile(&bars[2 + sn], (s_rph >> sn) & 1u))
+                if (wait_tile(&bars[2 + sn], (s_rph >> sn) & 1u)) {
                     issue_rec_tile(recs[sn], cur ? buf0 : buf1, s_prj[cur ^ 1], &bars[cur ^ 1]);
-                else { atomicOr(b.err, kErrTimeout); s_abort = 1; }
-                s_rph ^= 1u << sn;
-                if (t + 2 * grid < b.fast_tiles) {
-                    const int sa = s3 == 0 ? 2 : s3 - 1;
-                    fetch_rec(b, t + 2 * grid, &recs[sa], &bars[2 + sa]);
-                }
+                    s_rph ^= 1u << sn;
+                    if (t + 2 * grid < b.fast_tiles) {
+                        const int sa = s3 == 0 ? 2 : s3 - 1;
+                        fetch_rec(b, t + 2 * grid, &recs[sa], &bars[2 + sa]);
+                    }
+                } else { atomicOr(b.err, kErrTimeout); s_abort = 1; }
             }
             cnt[cur ^ 1][0] = cnt[cur ^ 1][1] = cnt[cur ^ 1][2] = cnt[cur ^ 1][3] = 0;
         }
@@ -1050,7 +1088,10 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
         // the box and the projections (every tile waits: the projections
         // come on the same barrier whether or not the box does)
         if (!wait_tile(&bars[cur], (phases >> cur) & 1u)) {
-            if (threadIdx.x == 0) atomicOr(b.err, kErrTimeout);
+            if (threadIdx.x == 0) {
+                atomicOr(b.err, kErrTimeout);
+                drain_bits(b, bars, t, grid, cur, s3, phases, s_rph, s_abort);
+            }
             return;
         }
         phases ^= 1u << cur;
@@ -1121,7 +1162,13 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
         }
         }
         __syncthreads();
-        if (s_abort) return;  // thread 0 could not start the next tile
+        if (s_abort) {  // thread 0 could not start the next tile
+            if (threadIdx.x == 0) {
+                const int sn = s3 == 2 ? 0 : s3 + 1;
+                wait_tile(&bars[2 + sn], (s_rph >> sn) & 1u);  // the record copy that did not complete
+            }
+            return;
+        }
         const bool some_skipped = C[1] > 0;
 
         {
