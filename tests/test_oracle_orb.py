@@ -75,6 +75,18 @@ def test_orientation_of_ramp(oracle, deg):
         assert b == want
 
 
+def test_sector_boundaries_are_half_open(oracle):
+    """Sector b covers [phi_b, phi_b+1): a centroid exactly on a boundary is in
+    the sector that starts there.  Ramps along the axes give m01 = 0 (or
+    m10 = 0) exactly, by symmetry: 0 deg is on phi_0 and 180 deg on phi_15,
+    while 90 and 270 deg lie inside sectors 7 and 22."""
+    for deg, want in ((0, 0), (180, 15), (90, 7), (270, 22)):
+        img, c = _ramp(math.radians(deg))
+        m10, m01, theta, b = oracle.orient(img, c, c)
+        assert (m01 == 0 and m10 != 0) if deg in (0, 180) else (m10 == 0 and m01 != 0)
+        assert b == want, (deg, b)
+
+
 def test_orientation_moments_brute_force(oracle):
     rng = np.random.default_rng(3)
     img = rng.integers(0, 256, (41, 41)).astype(np.uint8)

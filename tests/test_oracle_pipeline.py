@@ -46,11 +46,47 @@ def test_cap_keeps_highest_priority(oracle):
         assert np.array_equal(capped["desc"], full["desc"][want])
 
 
-def test_fallback_threshold_adds_keypoints_in_empty_cells(oracle):
-    pair = scenes.workload_pair("euroc_752x480_L8", 0)
-    a = oracle.extract_image(pair.left, _params(oracle, levels=2, max_feats=100000))
-    b = oracle.extract_image(pair.left, _params(oracle, levels=2, max_feats=100000, fast_thresh_lo=7))
-    assert b["count"] >= a["count"]
+def test_fallback_threshold_fills_cells_without_a_primary_corner(oracle):
+    """One level (PFA never suppresses there): per 32x32 cell, the strongest
+    corner at eps = 20 (response, then y, then x), or, in a cell without one,
+    the strongest corner at eps_lo = 7 -- built here by brute force from the
+    CRF-matrices at both thresholds (Eq. 1-3, pinned on their own)."""
+    img = scenes.workload_pair("euroc_752x480_L8", 0).left
+    H, W = img.shape
+    kp = oracle.extract_image(img, _params(oracle, levels=1, max_feats=100000, fast_thresh_lo=7))
+    hi, resp = oracle.fast(img, 20, 9, 13, 19)
+    lo, _ = oracle.fast(img, 7, 9, 13, 19)
+    want, from_lo = [], 0
+    for cy in range(0, H, 32):
+        for cx in range(0, W, 32):
+            for flags, is_lo in ((hi, 0), (lo, 1)):
+                ys, xs = np.nonzero(flags[cy:cy + 32, cx:cx + 32])
+                if len(ys):
+                    y, x = min(((cy + a, cx + b) for a, b in zip(ys, xs)), key=lambda t: (-int(resp[t]), t[0], t[1]))
+                    want.append((y, x, int(resp[y, x])))
+                    from_lo += is_lo
+                    break
+    got = sorted(zip(kp["y"].astype(int), kp["x"].astype(int), kp["response"].astype(int)))
+    assert got == sorted(want)
+    assert from_lo > 20  # the scene's flat regions leave cells to the fallback threshold
+
+
+def test_orientation_uses_the_raw_level(oracle):
+    """Level-0 keypoints: the intensity-centroid moments over the radius-15
+    disk of the input image itself (the raw level, not the blurred one), by
+    brute force here, and theta = atan2(m01, m10)."""
+    img = scenes.random_image(200, 260, seed=4)
+    kp = oracle.extract_image(img, _params(oracle, levels=3, max_feats=10000))
+    dy, dx = np.mgrid[-15:16, -15:16]
+    disk = dx * dx + dy * dy <= 225
+    lv0 = np.nonzero(kp["level"] == 0)[0]
+    assert len(lv0) > 20
+    for i in lv0:
+        x, y = int(kp["x"][i]), int(kp["y"][i])
+        patch = img[y - 15:y + 16, x - 15:x + 16].astype(np.int64) * disk
+        m10, m01 = int((dx * patch).sum()), int((dy * patch).sum())
+        assert (kp["m10"][i], kp["m01"][i]) == (m10, m01)
+        assert abs(float(kp["angle"][i]) - np.arctan2(m01, m10)) < 1e-6
 
 
 def test_pfa_reduces_keypoints_across_levels(oracle):

@@ -54,6 +54,45 @@ def test_bilinear_against_scipy(oracle):
         assert np.max(np.abs(lvl - ref)) <= 1.5
 
 
+def _q8_bound(img, n, Wn, Hn, scale=1.2):
+    """Per output pixel: 1/2 (rounding to nearest) + (dx + dy) / 512, where dx
+    and dy are the largest horizontal and vertical differences of the 2x2
+    source cell holding the exact position: Q8 weights are each within 1/512
+    of the exact fractions, and the bilinear interpolant changes by at most
+    dx (dy) per unit of its horizontal (vertical) argument in that cell."""
+    H0, W0 = img.shape
+    s = float(np.float64(np.float32(scale)) ** n)
+    u = np.clip((np.arange(Wn) + 0.5) * s - 0.5, 0, W0 - 1)
+    v = np.clip((np.arange(Hn) + 0.5) * s - 0.5, 0, H0 - 1)
+    xa = np.floor(u).astype(int); xb = np.minimum(xa + 1, W0 - 1)
+    ya = np.floor(v).astype(int); yb = np.minimum(ya + 1, H0 - 1)
+    I = img.astype(np.int64)
+    p00, p01 = I[np.ix_(ya, xa)], I[np.ix_(ya, xb)]
+    p10, p11 = I[np.ix_(yb, xa)], I[np.ix_(yb, xb)]
+    dx = np.maximum(np.abs(p01 - p00), np.abs(p11 - p10))
+    dy = np.maximum(np.abs(p10 - p00), np.abs(p11 - p01))
+    return 0.5 + (dx + dy) / 512.0 + 1e-9
+
+
+def test_bilinear_within_the_q8_error_bound(oracle):
+    """The level equals the exact bilinear value (scipy) to within the bound
+    that Q8 weights rounded to nearest and a final rounding to nearest allow.
+    A smooth image makes the bound close to 1/2 (rounding down instead would
+    break it); vertical step edges of 0 and 255 make it close to 1 (weights
+    truncated instead of rounded would break it)."""
+    y, x = np.mgrid[0:157, 0:211]
+    smooth = np.round(128 + 60 * np.sin(x / 9.0) * np.cos(y / 11.0)).astype(np.uint8)
+    rng = np.random.default_rng(5)
+    cols = np.cumsum(rng.integers(1, 6, 211)) % 2  # 0/255 columns in random runs
+    steps = np.repeat((cols * 255).astype(np.uint8)[None, :], 157, axis=0)
+    for img in (smooth, steps):
+        for n in range(1, 8):
+            lvl = oracle.pyramid_level(img, 1.2, n)
+            ref = _reference_bilinear(img, n, lvl.shape[1], lvl.shape[0])
+            bound = _q8_bound(img, n, lvl.shape[1], lvl.shape[0])
+            assert np.all(np.abs(lvl - ref) <= bound), (n, float(np.max(np.abs(lvl - ref) - bound)))
+
+
 def test_pyramid_preserves_mirror_symmetry(oracle):
     """Pixel-centre alignment maps the image centre onto the level centre:
     a left-right mirror-symmetric image stays mirror symmetric (to rounding)."""

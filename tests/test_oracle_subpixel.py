@@ -110,3 +110,78 @@ def test_brightness_offset_is_cancelled(oracle):
     ok = r["disparity"] >= 0
     assert ok.sum() > 30
     assert (r["sad"][ok] == 0).all()
+
+
+def _kps(x, y, level, X=None):
+    n = len(x)
+    X = x if X is None else X
+    z8 = lambda: np.zeros(n, np.uint8)
+    return {"count": n, "x": np.array(x, np.uint16), "y": np.array(y, np.uint16), "X": np.array(X, np.uint16),
+            "Y": np.array(y, np.uint16), "level": np.array(level, np.uint8), "response": np.zeros(n, np.uint16),
+            "k_levels": np.ones(n, np.uint8), "k_resp": np.zeros(n, np.uint32), "angle": np.zeros(n, np.float32),
+            "angle_bin": z8(), "desc": np.zeros((n, 8), np.uint32)}
+
+
+def _params(oracle, **kw):
+    p = oracle.FrontendParams()
+    p.levels, p.max_disp = 1, 64
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def test_first_minimum_of_tied_sads(oracle):
+    """A texture periodic in x with period 4 and identical left and right
+    images: SAD(t) vanishes at t = -4, 0 and 4 around xr0 = x.  The first
+    minimum, t* = -4, gives the disparity 4 - delta (|delta| <= 1); the last
+    one would give a negative disparity, which is rejected."""
+    rng = np.random.default_rng(8)
+    tile = rng.integers(20, 236, (40, 4))
+    img = np.tile(tile, (1, 15)).astype(np.uint8)             # 40 x 60
+    kl = _kps([30], [20], [0])
+    r = oracle.subpixel(img, img, kl, _kps([30], [20], [0]), np.array([0]), _params(oracle), 5, 5)
+    assert r["sad"][0] == 0
+    assert 3.0 <= r["disparity"][0] <= 5.0
+
+
+def test_outlier_bound_is_inclusive_at_21_tenths_of_the_median(oracle):
+    """Right image = left shifted by 3 columns, then k pixels of the window of
+    keypoint i (never its centre) raised by 1, so that SAD(t*) = k exactly:
+    k = 10, 10, 10, 21, 22.  The median of the kept SADs is 10; a match is an
+    outlier when 10 SAD > 21 median: 21 stays, 22 goes."""
+    rng = np.random.default_rng(9)
+    H, W, d = 40, 150, 3
+    base = rng.integers(20, 230, (H, W + d))
+    left, right = base[:, :W].copy(), base[:, d:d + W].copy()
+    xs, ks = [20, 45, 70, 95, 120], [10, 10, 10, 21, 22]
+    offsets = [(dy, dx) for dy in range(-5, 6) for dx in range(-5, 6) if (dy, dx) != (0, 0)]
+    for x, k in zip(xs, ks):
+        for dy, dx in offsets[:k]:
+            right[20 + dy, x - d + dx] += 1
+    left, right = left.astype(np.uint8), right.astype(np.uint8)
+    kl = _kps(xs, [20] * 5, [0] * 5)
+    kr = _kps([x - d for x in xs], [20] * 5, [0] * 5)
+    r = oracle.subpixel(left, right, kl, kr, np.arange(5), _params(oracle), 5, 5)
+    assert r["sad"].tolist() == ks
+    kept = r["disparity"] >= 0
+    assert kept.tolist() == [True, True, True, True, False]
+    assert np.all(np.abs(r["disparity"][kept] - d) <= 1.0)
+
+
+def test_search_centre_is_the_nearest_level_column(oracle):
+    """Scale 1.25 (exact Q8 weights): a right image shifted by 5 level-0
+    columns is shifted by exactly 4 columns at level 1.  For the level-1 left
+    keypoint x = 41 the true right column is 37; the match's s0 column
+    X = 41 gives xr0 = round(41 / 1.25) = 33, so the minimum lies at t* = 4,
+    inside the search of +-5 (rounding down, xr0 = 32, would put it at the
+    edge t* = 5 and reject it)."""
+    rng = np.random.default_rng(10)
+    H0, W0 = 60, 120
+    base = rng.integers(0, 256, (H0, W0 + 5))
+    left, right = base[:, :W0].astype(np.uint8), base[:, 5:W0 + 5].astype(np.uint8)
+    p = _params(oracle, levels=2, scale=1.25)
+    l1, r1 = oracle.pyramid_level(left, 1.25, 1), oracle.pyramid_level(right, 1.25, 1)
+    assert np.array_equal(r1[:, :80], l1[:, 4:84])          # the exact 4-column shift at level 1
+    r = oracle.subpixel(left, right, _kps([41], [24], [1]), _kps([41], [24], [1]), np.array([0]), p, 5, 5)
+    assert r["sad"][0] == 0
+    assert abs(r["disparity"][0] - 1.25 * 4) <= 1.25

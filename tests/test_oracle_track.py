@@ -83,3 +83,33 @@ def test_window_level_band_threshold_and_ratio(oracle):
     assert i[0] == -1 and d[0] == 1
     i, d = q(100, 50, 0, far, 10.0, 100)            # best distance 127 > max_dist
     assert i[0] == -1 and d[0] == 127
+
+
+def test_ratio_bound_second_best_and_scaled_window(oracle):
+    """The ratio test is inclusive at 0.9 (distances 18 and 20 pass, 19 and 21
+    fail); a better candidate met later makes the earlier best the second;
+    the window's half-size at level n is radius * zeta^n."""
+    def bits(k):  # a descriptor at Hamming distance k from the zero descriptor
+        d = np.zeros(8, np.uint32)
+        for i in range(k):
+            d[i // 32] |= np.uint32(1 << (i % 32))
+        return d
+
+    def kps(X, L, D):
+        n = len(X)
+        return {"count": n, "x": np.array(X, np.uint16), "y": np.full(n, 50, np.uint16),
+                "X": np.array(X, np.uint16), "Y": np.full(n, 50, np.uint16), "level": np.array(L, np.uint8),
+                "response": np.zeros(n, np.uint16), "k_levels": np.ones(n, np.uint8),
+                "k_resp": np.zeros(n, np.uint32), "angle": np.zeros(n, np.float32),
+                "angle_bin": np.zeros(n, np.uint8), "desc": np.stack(D).astype(np.uint32)}
+    z = np.zeros(8, np.uint32)
+    q = lambda kf, lvl, r: tuple(int(a[0]) for a in oracle.track(kf, 1.2, [100.0], [50.0], [lvl], [z], r, 100))
+    assert q(kps([100, 101], [0, 0], [bits(18), bits(20)]), 0, 5.0) == (0, 18)   # 180 <= 180
+    assert q(kps([100, 101], [0, 0], [bits(19), bits(21)]), 0, 5.0) == (-1, 19)  # 190 > 189
+    assert q(kps([100, 101], [0, 0], [bits(20), bits(19)]), 0, 5.0) == (-1, 19)  # 20 became the second
+    assert q(kps([100, 101, 102], [0, 0, 0], [bits(30), bits(19), bits(20)]), 0, 5.0) == (-1, 19)
+    far = kps([112], [2], [bits(3)])  # |dx| = 12 at level 2
+    assert q(far, 2, 10.0) == (0, 3)                # r = 10 * 1.44 = 14.4 >= 12
+    assert q(far, 2, 8.0) == (-1, 0xFFFF)           # r = 8 * 1.44 = 11.52 < 12
+    assert q(far, 1, 10.0) == (0, 3)                # level 1 +- 1 admits level 2; r = 12.0, inclusive
+    assert q(far, 0, 100.0) == (-1, 0xFFFF)         # level 0 +- 1 does not admit level 2
