@@ -46,6 +46,24 @@ def test_cap_keeps_highest_priority(oracle):
         assert np.array_equal(capped["desc"], full["desc"][want])
 
 
+def test_cap_breaks_ties_by_level_then_position(oracle):
+    """Where (K_l, K_r, response) tie across levels, a cap that cuts inside the
+    tie keeps the shallower level first (then smaller y, then smaller x)."""
+    img = scenes.random_image(240, 320, seed=9)
+    full = oracle.extract_image(img, _params(oracle, levels=5, max_feats=100000))
+    n = full["count"]
+    key = lambda i: (-int(full["k_levels"][i]), -int(full["k_resp"][i]), -int(full["response"][i]))
+    order = sorted(range(n), key=lambda i: key(i) + (int(full["level"][i]), int(full["y"][i]), int(full["x"][i])))
+    cuts = [c for c in range(1, n)
+            if key(order[c - 1]) == key(order[c]) and full["level"][order[c - 1]] != full["level"][order[c]]]
+    assert len(cuts) >= 3
+    for cap in cuts[:6]:
+        capped = oracle.extract_image(img, _params(oracle, levels=5, max_feats=cap))
+        want = sorted(order[:cap])
+        for f in ("x", "y", "level"):
+            assert np.array_equal(capped[f], full[f][want]), (cap, f)
+
+
 def test_fallback_threshold_fills_cells_without_a_primary_corner(oracle):
     """One level (PFA never suppresses there): per 32x32 cell, the strongest
     corner at eps = 20 (response, then y, then x), or, in a cell without one,

@@ -185,3 +185,23 @@ def test_search_centre_is_the_nearest_level_column(oracle):
     r = oracle.subpixel(left, right, _kps([41], [24], [1]), _kps([41], [24], [1]), np.array([0]), p, 5, 5)
     assert r["sad"][0] == 0
     assert abs(r["disparity"][0] - 1.25 * 4) <= 1.25
+
+
+def test_windows_must_fit_inside_the_level(oracle):
+    """The left (2w+1)^2 window and the right strip (columns xr0 +- (L + w))
+    must lie inside the level: a keypoint whose window ends on the first or
+    last column or row is evaluated, one pixel further it is rejected with no
+    SAD (w = L = 5, a 60 x 40 level)."""
+    rng = np.random.default_rng(11)
+    img = rng.integers(0, 256, (40, 60)).astype(np.uint8)
+    NONE = 0xFFFFFFFF
+
+    def sad(x, y, X):
+        r = oracle.subpixel(img, img, _kps([x], [y], [0]), _kps([X], [y], [0]), np.array([0]), _params(oracle), 5, 5)
+        return int(r["sad"][0])
+    assert sad(54, 20, 44) != NONE and sad(55, 20, 44) == NONE   # x + w = 59 fits, 60 does not
+    assert sad(30, 34, 30) != NONE and sad(30, 35, 30) == NONE   # y + w = 39 fits, 40 does not
+    assert sad(5, 20, 15) != NONE and sad(4, 20, 15) == NONE     # x - w = 0 fits, -1 does not
+    assert sad(30, 5, 30) != NONE and sad(30, 4, 30) == NONE     # y - w = 0 fits, -1 does not
+    assert sad(30, 20, 49) != NONE and sad(30, 20, 50) == NONE   # xr0 + L + w = 59 fits, 60 does not
+    assert sad(30, 20, 10) != NONE and sad(30, 20, 9) == NONE    # xr0 - L - w = 0 fits, -1 does not

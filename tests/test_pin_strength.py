@@ -49,6 +49,8 @@ MUTANTS = [
      "acc += (uint32_t)w[i + 3] * in[(size_t)y * pitch_in + clampi(x + i, 1, W - 1)];", 0),
     ("blur_no_rounding", "out[(size_t)y * pitch_out + x] = (uint8_t)((acc + 32768u) >> 16);",
      "out[(size_t)y * pitch_out + x] = (uint8_t)(acc >> 16);", 0),
+    ("blur_vertical_border", "acc += (uint32_t)w[j + 3] * h[(size_t)clampi(y + j, 0, H - 1) * W + x];",
+     "acc += (uint32_t)w[j + 3] * h[(size_t)clampi(y + j, 0, H - 2) * W + x];", 0),
     # FAST with Bounded Rectification (Sec. II-A, Eq. 1-3)
     ("ring_mirrored", "static const int32_t RING_DY[16] = { 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1, 0, 1, 2, 3 };",
      "static const int32_t RING_DY[16] = { -3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3 };", 0),
@@ -65,6 +67,9 @@ MUTANTS = [
      "return (nb >= p_min && nb <= p_max);", 0),
     ("border_one_row_short", "for (int32_t y = border; y < H - border; ++y)",
      "for (int32_t y = border; y <= H - border; ++y)", 0),
+    # Feature Culling (Sec. II-C-1)
+    ("cull_fallback_replaces", "            if (!any_hi) {\n                if (!corner_lo) continue;",
+     "            if (!any_hi || corner_lo) {\n                if (!corner_lo) continue;", 0),
     # Feature Culling (Sec. II-C-1)
     ("cull_weakest_first", "if (a->r != b->r) return a->r > b->r ? -1 : 1;",
      "if (a->r != b->r) return a->r < b->r ? -1 : 1;", 0),
@@ -104,6 +109,10 @@ MUTANTS = [
      "if (a > b) desc[i / 32] |= 1u << (i % 32);", 0),
     ("descriptor_bit_order_reversed", "if (a < b) desc[i / 32] |= 1u << (i % 32);",
      "if (a < b) desc[i / 32] |= 1u << (31 - i % 32);", 0),
+    ("descriptor_xy_swapped", "int32_t a = blur[(size_t)(y + py) * pitch + (x + px)];",
+     "int32_t a = blur[(size_t)(y + px) * pitch + (x + py)];", 0),
+    ("pattern_rotation_truncated", "out[((size_t)b * OR_NPAIRS + i) * 4 + pt * 2 + 0] = (int8_t)lround(xr);",
+     "out[((size_t)b * OR_NPAIRS + i) * 4 + pt * 2 + 0] = (int8_t)xr;", 0),
     # whole-image pipeline (cap, order, levels used)
     ("cap_kr_before_kl", "    if (a->kl != b->kl) return a->kl > b->kl ? -1 : 1;\n    if (a->kr != b->kr) return a->kr > b->kr ? -1 : 1;",
      "    if (a->kr != b->kr) return a->kr > b->kr ? -1 : 1;\n    if (a->kl != b->kl) return a->kl > b->kl ? -1 : 1;", 0),
@@ -116,6 +125,9 @@ MUTANTS = [
      "or_orient(blur[k->level], W[k->level], k->x, k->y, &m10, &m01, &theta, &bin);", 0),
     ("descriptor_on_raw_level", "or_describe(blur[k->level], W[k->level], k->x, k->y,",
      "or_describe(raw[k->level], W[k->level], k->x, k->y,", 0),
+    ("cap_deeper_level_first", "if (a->level != b->level) return a->level < b->level ? -1 : 1;",
+     "if (a->level != b->level) return a->level > b->level ? -1 : 1;", 0),
+    ("response_stores_kr", "out->response[i] = (uint16_t)k->r;", "out->response[i] = (uint16_t)k->kr;", 0),
     # stereo matching (Sec. III middle-end)
     ("match_band_floor", "return (int32_t)ceil((double)row_band_px * s);", "return (int32_t)floor((double)row_band_px * s);", 0),
     ("match_same_level_only", "if (nr < nl - 1 || nr > nl + 1) continue;", "if (nr != nl) continue;", 0),
@@ -124,9 +136,13 @@ MUTANTS = [
     ("match_tie_larger_disparity", "if (d < best_d || (d == best_d && disp < best_disp)) {",
      "if (d < best_d || (d == best_d && disp > best_disp)) {", 0),
     ("match_threshold_exclusive", "} else if (best_d <= p->match_max_dist) {", "} else if (best_d < p->match_max_dist) {", 0),
+    ("match_and_instead_of_xor", "d += popcount32(Lk->desc[(size_t)i * 8 + w] ^ Rk->desc[(size_t)j * 8 + w]);",
+     "d += popcount32(Lk->desc[(size_t)i * 8 + w] & Rk->desc[(size_t)j * 8 + w]);", 0),
     # correlation minimisation (NEXT-1)
     ("subpixel_xr0_truncated", "int32_t xr0 = (int32_t)floor((double)Rk->X[j] / s + 0.5);",
      "int32_t xr0 = (int32_t)floor((double)Rk->X[j] / s);", 0),
+    ("subpixel_window_off_by_one", "if (xi - w < 0 || xi + w >= W || yi - w < 0 || yi + w >= H",
+     "if (xi - w < 0 || xi + w > W || yi - w < 0 || yi + w > H", 0),
     ("subpixel_no_centre_normalisation", "int32_t a = (int32_t)A[(size_t)(yi + dy) * W + xi + dx] - lc;",
      "int32_t a = (int32_t)A[(size_t)(yi + dy) * W + xi + dx];", 0),
     ("subpixel_last_minimum", "if (acc < sad[best]) best = t + L;", "if (acc <= sad[best]) best = t + L;", 0),
