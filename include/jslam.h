@@ -386,8 +386,8 @@ jslam_status jslam_graph_launch(jslam_ctx *ctx);
  * any stream capture.  Nothing is allocated, ever.
  *
  * JSLAM_ERR_CAPACITY when n > 16384; JSLAM_ERR_ARG for a null array with
- * n > 0, a size outside 1..4096, levels outside 1..8, scale <= 1, nms_q not
- * odd in 1..7, a bad rule or device; JSLAM_ERR_CUDA if the table's address
+ * n > 0, a size outside 1..4096, levels outside 1..8, scale outside the open
+ * interval (1, 16), nms_q not odd in 1..7, a bad rule or device; JSLAM_ERR_CUDA if the table's address
  * or the launch fails.  n == 0 returns JSLAM_OK without work. */
 jslam_status jslam_pfa_scores_static(const uint8_t *level, const uint16_t *x, const uint16_t *y,
                                      const uint16_t *response, int32_t n, int32_t width0, int32_t height0,
