@@ -205,3 +205,23 @@ def test_windows_must_fit_inside_the_level(oracle):
     assert sad(30, 5, 30) != NONE and sad(30, 4, 30) == NONE     # y - w = 0 fits, -1 does not
     assert sad(30, 20, 49) != NONE and sad(30, 20, 50) == NONE   # xr0 + L + w = 59 fits, 60 does not
     assert sad(30, 20, 10) != NONE and sad(30, 20, 9) == NONE    # xr0 - L - w = 0 fits, -1 does not
+
+
+def test_minimum_at_either_end_of_the_search_is_rejected(oracle):
+    """Right image = left shifted by 3 columns, so left column 30 is right
+    column 27 and t* = 27 - xr0 (xr0 = X at level 0).  A minimum at t = -L or
+    t = +L may lie beyond the search and is rejected (its SAD still reported);
+    one step inside it is kept, at disparity 3 - delta."""
+    rng = np.random.default_rng(12)
+    base = rng.integers(0, 256, (40, 63))
+    left, right = base[:, :60].astype(np.uint8), base[:, 3:63].astype(np.uint8)
+
+    def run(X):
+        r = oracle.subpixel(left, right, _kps([30], [20], [0]), _kps([X], [20], [0]), np.array([0]),
+                            _params(oracle), 5, 5)
+        return int(r["sad"][0]), float(r["disparity"][0])
+    assert run(32) == (0, -1.0)                 # t* = -5 = -L
+    assert run(22) == (0, -1.0)                 # t* = +5 = +L
+    for X in (31, 23):                          # t* = -4 and +4
+        sad, d = run(X)
+        assert sad == 0 and 2.0 <= d <= 4.0

@@ -113,3 +113,6 @@ def test_ratio_bound_second_best_and_scaled_window(oracle):
     assert q(far, 2, 8.0) == (-1, 0xFFFF)           # r = 8 * 1.44 = 11.52 < 12
     assert q(far, 1, 10.0) == (0, 3)                # level 1 +- 1 admits level 2; r = 12.0, inclusive
     assert q(far, 0, 100.0) == (-1, 0xFFFF)         # level 0 +- 1 does not admit level 2
+    deep = kps([100], [7], [bits(2)])
+    assert q(deep, 7, 1.0) == (0, 2)
+    assert q(deep, 8, 1.0) == (-1, 0xFFFF)          # levels >= 8 have no candidates

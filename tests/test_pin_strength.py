@@ -135,6 +135,8 @@ MUTANTS = [
      "int32_t disp = (int32_t)Rk->X[j] - (int32_t)Lk->X[i];", 0),
     ("match_tie_larger_disparity", "if (d < best_d || (d == best_d && disp < best_disp)) {",
      "if (d < best_d || (d == best_d && disp > best_disp)) {", 0),
+    ("match_none_reports_distance_0", "right_idx[i] = -1; disparity[i] = 0; dist[i] = 0xFFFF;",
+     "right_idx[i] = -1; disparity[i] = 0; dist[i] = 0;", 0),
     ("match_threshold_exclusive", "} else if (best_d <= p->match_max_dist) {", "} else if (best_d < p->match_max_dist) {", 0),
     ("match_and_instead_of_xor", "d += popcount32(Lk->desc[(size_t)i * 8 + w] ^ Rk->desc[(size_t)j * 8 + w]);",
      "d += popcount32(Lk->desc[(size_t)i * 8 + w] & Rk->desc[(size_t)j * 8 + w]);", 0),
@@ -153,7 +155,10 @@ MUTANTS = [
     ("subpixel_outlier_factor_2", "10u * (uint64_t)sad_out[i] > 21u * median", "10u * (uint64_t)sad_out[i] > 20u * median", 0),
     ("subpixel_depth_not_inverse", "depth_out[i] = bf > 0.0 ? (float)(bf / (disp > 0.01 ? disp : 0.01)) : 0.0f;",
      "depth_out[i] = bf > 0.0 ? (float)(bf * (disp > 0.01 ? disp : 0.01)) : 0.0f;", 0),
+    ("subpixel_minimum_at_minus_L_kept", "if (ts == -L || ts == L) continue;", "if (ts == L) continue;", 0),
     # tracking (NEXT-2)
+    ("track_level_8_searched", "if (lvl[q] >= OR_MAX_LEVELS) { idx_out[q] = -1; dist_out[q] = 0xFFFF; continue; }",
+     "if (lvl[q] > OR_MAX_LEVELS) { idx_out[q] = -1; dist_out[q] = 0xFFFF; continue; }", 0),
     ("track_same_level_only", "if (m < (int32_t)lvl[q] - 1 || m > (int32_t)lvl[q] + 1) continue;",
      "if (m != (int32_t)lvl[q]) continue;", 0),
     ("track_ratio_08", "int ok = bd <= max_dist && (sd == 0x7fffffff || 10 * bd <= 9 * sd);",
