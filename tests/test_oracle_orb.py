@@ -34,6 +34,26 @@ def test_pattern_properties(oracle):
     assert len({tuple(r) for r in p.tolist()}) > 250
 
 
+def test_pattern_spread_matches_the_truncated_lattice_gaussian(oracle):
+    """Each point is (lround(sigma g1), lround(sigma g2)) for independent
+    standard normals, kept when inside the radius-13 disk: the lattice point
+    (i, j) has probability proportional to the Gaussian mass of its unit
+    square, restricted to i^2 + j^2 <= 169.  The sample mean of the 1024
+    squared coordinates lies within 3 standard errors of that distribution's
+    E[x^2] (27.9 for sigma = 31/5; a sigma of 31/4 would give 32.6)."""
+    from scipy.stats import norm
+    sigma = 31.0 / 5.0
+    i = np.arange(-13, 14)
+    m1 = norm.cdf((i + 0.5) / sigma) - norm.cdf((i - 0.5) / sigma)
+    I, J = np.meshgrid(i, i, indexing="ij")
+    P = np.outer(m1, m1) * (I ** 2 + J ** 2 <= 169)
+    P /= P.sum()
+    ex2, ex4 = (P * I ** 2).sum(), (P * I ** 4).sum()
+    se = np.sqrt((ex4 - ex2 ** 2) / 1024)
+    p = oracle.pattern_base().astype(float)
+    assert abs((p ** 2).mean() - ex2) < 3 * se, ((p ** 2).mean(), ex2, se)
+
+
 def test_rotated_pattern(oracle):
     base = oracle.pattern_base().astype(float)
     rot = oracle.pattern_rotated().astype(float)

@@ -46,6 +46,18 @@ def test_cap_keeps_highest_priority(oracle):
         assert np.array_equal(capped["desc"], full["desc"][want])
 
 
+def test_lexicographic_rule_suppresses_a_superset(oracle):
+    """Sec. II-C-2 NMS: a neighbour with larger K_l and larger K_r (rule 0)
+    also has a lexicographically larger (K_l, K_r) (rule 1), and the scores
+    do not depend on the rule, so without a cap rule 1 keeps a subset of
+    rule 0's keypoints -- a proper one on a textured image."""
+    img = scenes.random_image(240, 320, seed=9)
+    key = lambda kp: set(zip(kp["level"].tolist(), kp["y"].tolist(), kp["x"].tolist()))
+    a = key(oracle.extract_image(img, _params(oracle, levels=5, max_feats=100000)))
+    b = key(oracle.extract_image(img, _params(oracle, levels=5, max_feats=100000, pfa_rule=1)))
+    assert b < a
+
+
 def test_cap_breaks_ties_by_level_then_position(oracle):
     """Where (K_l, K_r, response) tie across levels, a cap that cuts inside the
     tie keeps the shallower level first (then smaller y, then smaller x)."""

@@ -101,6 +101,9 @@ MUTANTS = [
     ("sector_boundary_open", "return t >= 0.0;", "return t > 0.0;", 0),
     # steered BRIEF (Sec. III)
     ("splitmix_shift", "z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBull;", 0),
+    ("uniform_scale_doubled", "double u1 = (double)((or_splitmix64_next(state) >> 11) + 1) * (1.0 / 9007199254740992.0);",
+     "double u1 = (double)((or_splitmix64_next(state) >> 11) + 1) * (2.0 / 9007199254740992.0);", 0),
+    ("pattern_sigma_31_4", "const double sigma = 31.0 / 5.0;", "const double sigma = 31.0 / 4.0;", 0),
     ("pattern_radius_14", "if (v[0] * v[0] + v[1] * v[1] > 169) continue;",
      "if (v[0] * v[0] + v[1] * v[1] > 196) continue;", 0),
     ("pattern_rotated_backwards", "double xr = cx - sy;\n                double yr = sx + cy;",
@@ -121,6 +124,8 @@ MUTANTS = [
     ("fallback_uses_primary_threshold",
      "or_fast(raw[n], W[n], H[n], W[n], p->fast_thresh_lo, p->p_min, p->p_max, p->border, lo, resp_lo);",
      "or_fast(raw[n], W[n], H[n], W[n], p->fast_thresh, p->p_min, p->p_max, p->border, lo, resp_lo);", 0),
+    ("pipeline_ignores_pfa_rule", "or_pfa_core(n_cand, lev, X, Y, R, W0, H0, L, p->nms_q, p->pfa_rule, Kl, Kr, alive);",
+     "or_pfa_core(n_cand, lev, X, Y, R, W0, H0, L, p->nms_q, 0, Kl, Kr, alive);", 0),
     ("orientation_on_blurred_level", "or_orient(raw[k->level], W[k->level], k->x, k->y, &m10, &m01, &theta, &bin);",
      "or_orient(blur[k->level], W[k->level], k->x, k->y, &m10, &m01, &theta, &bin);", 0),
     ("descriptor_on_raw_level", "or_describe(blur[k->level], W[k->level], k->x, k->y,",
@@ -137,6 +142,8 @@ MUTANTS = [
      "if (d < best_d || (d == best_d && disp > best_disp)) {", 0),
     ("match_none_reports_distance_0", "right_idx[i] = -1; disparity[i] = 0; dist[i] = 0xFFFF;",
      "right_idx[i] = -1; disparity[i] = 0; dist[i] = 0;", 0),
+    ("match_max_disparity_exclusive", "if (disp < 0 || disp > p->max_disp) continue;",
+     "if (disp < 0 || disp >= p->max_disp) continue;", 0),
     ("match_threshold_exclusive", "} else if (best_d <= p->match_max_dist) {", "} else if (best_d < p->match_max_dist) {", 0),
     ("match_and_instead_of_xor", "d += popcount32(Lk->desc[(size_t)i * 8 + w] ^ Rk->desc[(size_t)j * 8 + w]);",
      "d += popcount32(Lk->desc[(size_t)i * 8 + w] & Rk->desc[(size_t)j * 8 + w]);", 0),
@@ -167,14 +174,32 @@ MUTANTS = [
     ("track_window_unscaled", "volatile float r = radius * zf;", "volatile float r = radius;", 0),
 ]
 
-# Mutants that change nothing the paper fixes, or nothing at all, listed so
-# that they are not re-added as gaps.  The Box-Muller sine branch draws an
-# equally valid Gaussian, so it only selects another of this build's own
-# BRIEF patterns (the CUDA path is held to the oracle's table in full).  The
-# p = q redraw never fires for this seed's first 256 accepted pairs, so
-# dropping it leaves the pattern unchanged.
-EQUIVALENT = [("box_muller_sine_branch", "return radius * cos(ang);", "return radius * sin(ang);"),
-              ("pattern_allows_p_equal_q", "if (v[0] == v[2] && v[1] == v[3]) continue;", "")]
+# Mutants that change no output over the oracle's domain (checked below):
+# the p = q redraw never fires for the seed's first 256 accepted pairs; the
+# projection's clamp to W0 - 1 never binds for a level pixel, since
+# x <= W_n - 1 <= W0 / zeta^n - 1/2 gives x zeta^n + 1/2 <= W0 - zeta^n / 2 + 1/2
+# < W0.
+EQUIVALENT = [("pattern_allows_p_equal_q", "if (v[0] == v[2] && v[1] == v[3]) continue;", ""),
+              ("projection_unclamped", "return X < W0 - 1 ? X : W0 - 1;", "return X;")]
+# A mutant that changes only a choice the paper leaves open: the Box-Muller
+# sine branch draws an equally valid Gaussian, i.e. another of this build's
+# own BRIEF patterns (the CUDA path is held to the oracle's table in full).
+SPEC_FREE = [("box_muller_sine_branch", "return radius * cos(ang);", "return radius * sin(ang);")]
+
+_PROBE = r"""
+import sys, hashlib
+sys.path.insert(0, {root!r})
+from oracle import oracle as O
+O._SRC, O._LIB = {src!r}, {lib!r}
+import numpy as np
+h = hashlib.sha256(O.pattern_base().tobytes())
+for W0 in (64, 377, 752, 1241, 1920, 4096):
+    W, _, _ = O.level_geometry(W0, W0, 8, 1.2, 32)
+    for n in range(8):
+        h.update(np.array([O.project(x, n, 1.2, W0) for x in range(int(W[n]))], np.int32).tobytes())
+print(h.hexdigest())
+"""
+
 
 _DRIVER = r"""
 import sys
@@ -209,7 +234,7 @@ def test_mutation_sites_exist():
     text = open(SRC).read()
     names = [m[0] for m in MUTANTS]
     assert len(set(names)) == len(names)
-    for name, old, new, occ in MUTANTS + [e + (0,) for e in EQUIVALENT]:
+    for name, old, new, occ in MUTANTS + [e + (0,) for e in EQUIVALENT + SPEC_FREE]:
         assert text.count(old) > occ and old != new, name
 
 
@@ -232,3 +257,23 @@ def test_every_mutant_fails_a_pin(outcomes):
     broken = {n: outcomes[n] for n, _, _, _ in MUTANTS if outcomes[n][0] not in (0, 1)}
     assert not broken, {n: (rc, log[-600:]) for n, (rc, log) in broken.items()}
     assert not survivors, survivors
+
+
+def test_listed_equivalent_mutants_change_no_output():
+    """The pattern and every level pixel's s0 projection (six widths, eight
+    levels) are the same with each mutant listed as equivalent."""
+    text = open(SRC).read()
+    jobs = [("unmutated", text)] + [(n, _mutate(text, o, w, 0)) for n, o, w in EQUIVALENT]
+    out = {}
+    with tempfile.TemporaryDirectory() as tmp:
+        for name, t in jobs:
+            d = os.path.join(tmp, name)
+            os.makedirs(d)
+            src, lib = os.path.join(d, "jslam_oracle.c"), os.path.join(d, "libjslam_oracle.so")
+            with open(src, "w") as f:
+                f.write(t)
+            r = subprocess.run([sys.executable, "-c", _PROBE.format(root=ROOT, src=src, lib=lib)],
+                               capture_output=True, text=True, timeout=600, cwd=ROOT)
+            assert r.returncode == 0, r.stderr[-1500:]
+            out[name] = r.stdout.strip()
+    assert all(v == out["unmutated"] for v in out.values()), out
