@@ -7,7 +7,6 @@ import subprocess
 import sys
 import time
 
-import numpy as np
 import pytest
 
 from paper_2410_04090_gb300 import scenes

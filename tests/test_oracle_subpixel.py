@@ -2,7 +2,6 @@
 matching, read as patch-SAD refinement with a parabola fit): scenes whose
 true disparity is known, integer and fractional, and the closed-form depth."""
 import numpy as np
-import pytest
 
 from parity_util import params_from
 
