@@ -14,6 +14,15 @@ def test_cell_scaling_matches_paper(oracle):
         assert c[0] == int(c0)
 
 
+def test_cells_never_shrink_below_one_pixel(oracle):
+    """c_n = max(1, floor(c / zeta^n)): for c = 2 the floor is 0 from
+    level 4 (2 / 1.2^4 = 0.96) on, and the cell stays one pixel."""
+    _, _, c = oracle.level_geometry(1241, 376, 8, 1.2, 2)
+    assert c.tolist() == [2, 1, 1, 1, 1, 1, 1, 1]
+    _, _, c = oracle.level_geometry(1241, 376, 8, 1.2, 1)
+    assert c.tolist() == [1] * 8
+
+
 def test_level_sizes_shrink_by_scale(oracle):
     for W0, H0 in ((1241, 376), (752, 480), (1920, 1080), (640, 480)):
         W, H, _ = oracle.level_geometry(W0, H0, 8, 1.2, 32)

@@ -143,28 +143,36 @@ def test_first_minimum_of_tied_sads(oracle):
     assert 3.0 <= r["disparity"][0] <= 5.0
 
 
-def test_outlier_bound_is_inclusive_at_21_tenths_of_the_median(oracle):
-    """Right image = left shifted by 3 columns, then k pixels of the window of
-    keypoint i (never its centre) raised by 1, so that SAD(t*) = k exactly:
-    k = 10, 10, 10, 21, 22.  The median of the kept SADs is 10; a match is an
-    outlier when 10 SAD > 21 median: 21 stays, 22 goes."""
+def _outlier_case(oracle, ks, d=3):
+    """Right image = left shifted by d columns, then k pixels of the window of
+    keypoint i (never its centre) raised by 1, so that SAD(t*) = k exactly."""
     rng = np.random.default_rng(9)
-    H, W, d = 40, 150, 3
+    H, W = 40, 25 * len(ks) + 25
     base = rng.integers(20, 230, (H, W + d))
     left, right = base[:, :W].copy(), base[:, d:d + W].copy()
-    xs, ks = [20, 45, 70, 95, 120], [10, 10, 10, 21, 22]
+    xs = [20 + 25 * i for i in range(len(ks))]
     offsets = [(dy, dx) for dy in range(-5, 6) for dx in range(-5, 6) if (dy, dx) != (0, 0)]
     for x, k in zip(xs, ks):
         for dy, dx in offsets[:k]:
             right[20 + dy, x - d + dx] += 1
     left, right = left.astype(np.uint8), right.astype(np.uint8)
-    kl = _kps(xs, [20] * 5, [0] * 5)
-    kr = _kps([x - d for x in xs], [20] * 5, [0] * 5)
-    r = oracle.subpixel(left, right, kl, kr, np.arange(5), _params(oracle), 5, 5)
-    assert r["sad"].tolist() == ks
+    n = len(ks)
+    r = oracle.subpixel(left, right, _kps(xs, [20] * n, [0] * n), _kps([x - d for x in xs], [20] * n, [0] * n),
+                        np.arange(n), _params(oracle), 5, 5)
+    assert r["sad"].tolist() == list(ks)
     kept = r["disparity"] >= 0
-    assert kept.tolist() == [True, True, True, True, False]
     assert np.all(np.abs(r["disparity"][kept] - d) <= 1.0)
+    return kept.tolist()
+
+
+def test_outlier_bound_is_inclusive_at_21_tenths_of_the_median(oracle):
+    """The median is element count / 2 of the kept SADs in ascending order; a
+    match is an outlier when 10 SAD > 21 median.  Odd count: SADs 10, 10, 10,
+    21, 22 have median 10, so 21 stays and 22 goes.  Even count: SADs 10, 10,
+    20, 42 have median 20 (the upper one), so 42 stays (420 <= 420)."""
+    assert _outlier_case(oracle, [10, 10, 10, 21, 22]) == [True, True, True, True, False]
+    assert _outlier_case(oracle, [10, 10, 20, 42]) == [True, True, True, True]
+    assert _outlier_case(oracle, [10, 10, 20, 43]) == [True, True, True, False]
 
 
 def test_search_centre_is_the_nearest_level_column(oracle):

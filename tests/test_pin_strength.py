@@ -32,6 +32,7 @@ MUTANTS = [
      "W[n] = (int32_t)floor((double)W0 / s);", 0),
     ("cell_size_rounded", "int32_t cn = (int32_t)floor((double)cell / s);",
      "int32_t cn = (int32_t)floor((double)cell / s + 0.5);", 0),
+    ("cell_size_may_reach_zero", "c[n] = cn < 1 ? 1 : cn;", "c[n] = cn;", 0),
     ("bilinear_corner_aligned", "double u = ((double)x + 0.5) * s - 0.5;", "double u = (double)x * s;", 0),
     ("bilinear_weight_truncated", "int32_t w = (int32_t)floor((u - (double)i) * 256.0 + 0.5);",
      "int32_t w = (int32_t)floor((u - (double)i) * 256.0);", 0),
@@ -154,6 +155,9 @@ MUTANTS = [
      "if (xi - w < 0 || xi + w > W || yi - w < 0 || yi + w > H", 0),
     ("subpixel_no_centre_normalisation", "int32_t a = (int32_t)A[(size_t)(yi + dy) * W + xi + dx] - lc;",
      "int32_t a = (int32_t)A[(size_t)(yi + dy) * W + xi + dx];", 0),
+    ("subpixel_right_centre_unshifted", "int32_t rc = B[(size_t)yi * W + xr0 + t];",
+     "int32_t rc = B[(size_t)yi * W + xr0];", 0),
+    ("subpixel_lower_median", "uint64_t median = kept[n_kept / 2];", "uint64_t median = kept[(n_kept - 1) / 2];", 0),
     ("subpixel_last_minimum", "if (acc < sad[best]) best = t + L;", "if (acc <= sad[best]) best = t + L;", 0),
     ("subpixel_parabola_sign", "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);",
      "int64_t num = d3 - d1, den = 2 * (d1 + d3 - 2 * d2);", 0),
