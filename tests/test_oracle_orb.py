@@ -28,6 +28,10 @@ def test_pattern_properties(oracle):
     assert np.all(p[:, 0] ** 2 + p[:, 1] ** 2 <= 169)
     assert np.all(p[:, 2] ** 2 + p[:, 3] ** 2 <= 169)
     assert not np.any((p[:, 0] == p[:, 2]) & (p[:, 1] == p[:, 3]))
+    # only p = q is redrawn: pairs sharing one coordinate remain (each
+    # coordinate is shared by about 1 / (2 sqrt(pi) sigma) = 4.5 % of pairs)
+    assert ((p[:, 0] == p[:, 2]) & (p[:, 1] != p[:, 3])).sum() >= 4
+    assert ((p[:, 1] == p[:, 3]) & (p[:, 0] != p[:, 2])).sum() >= 4
     # isotropic Gaussian with sigma 31/5, truncated to the radius-13 disk
     assert 4.5 < p.std() < 6.2
     assert abs(p.mean()) < 0.6

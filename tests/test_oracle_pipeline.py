@@ -58,22 +58,33 @@ def test_lexicographic_rule_suppresses_a_superset(oracle):
     assert b < a
 
 
-def test_cap_breaks_ties_by_level_then_position(oracle):
-    """Where (K_l, K_r, response) tie across levels, a cap that cuts inside the
-    tie keeps the shallower level first (then smaller y, then smaller x)."""
-    img = scenes.random_image(240, 320, seed=9)
-    full = oracle.extract_image(img, _params(oracle, levels=5, max_feats=100000))
+def _cap_cuts_hold(oracle, img, levels, pick):
+    """Cut the cap inside ties of (K_l, K_r, response) chosen by `pick`: the
+    capped set must be the first `cap` of the full set's priority order
+    (K_l, K_r, response descending, then level, y, x ascending)."""
+    full = oracle.extract_image(img, _params(oracle, levels=levels, max_feats=100000))
     n = full["count"]
     key = lambda i: (-int(full["k_levels"][i]), -int(full["k_resp"][i]), -int(full["response"][i]))
     order = sorted(range(n), key=lambda i: key(i) + (int(full["level"][i]), int(full["y"][i]), int(full["x"][i])))
-    cuts = [c for c in range(1, n)
-            if key(order[c - 1]) == key(order[c]) and full["level"][order[c - 1]] != full["level"][order[c]]]
+    cuts = [c for c in range(1, n) if key(order[c - 1]) == key(order[c]) and pick(full, order[c - 1], order[c])]
     assert len(cuts) >= 3
     for cap in cuts[:6]:
-        capped = oracle.extract_image(img, _params(oracle, levels=5, max_feats=cap))
+        capped = oracle.extract_image(img, _params(oracle, levels=levels, max_feats=cap))
         want = sorted(order[:cap])
         for f in ("x", "y", "level"):
             assert np.array_equal(capped[f], full[f][want]), (cap, f)
+
+
+def test_cap_breaks_ties_by_level_then_position(oracle):
+    """Where (K_l, K_r, response) tie, a cap cutting inside the tie keeps the
+    shallower level first, then the smaller y, then the smaller x.  Ties
+    across levels come from a random image; ties within a level whose rows
+    and columns are in opposite orders come from a texture tiled with the
+    culling period (every cell repeats its strongest corner)."""
+    _cap_cuts_hold(oracle, scenes.random_image(240, 320, seed=9), 5,
+                   lambda f, a, b: f["level"][a] != f["level"][b])
+    tiled = np.tile(scenes.random_image(32, 32, seed=9), (8, 10))
+    _cap_cuts_hold(oracle, tiled, 3, lambda f, a, b: f["level"][a] == f["level"][b] and f["x"][a] > f["x"][b])
 
 
 def test_fallback_threshold_fills_cells_without_a_primary_corner(oracle):
@@ -99,6 +110,10 @@ def test_fallback_threshold_fills_cells_without_a_primary_corner(oracle):
     got = sorted(zip(kp["y"].astype(int), kp["x"].astype(int), kp["response"].astype(int)))
     assert got == sorted(want)
     assert from_lo > 20  # the scene's flat regions leave cells to the fallback threshold
+    # eps_lo = 0 turns the fallback off: only the primary-threshold selections
+    kp0 = oracle.extract_image(img, _params(oracle, levels=1, max_feats=100000, fast_thresh_lo=0))
+    got0 = sorted(zip(kp0["y"].astype(int), kp0["x"].astype(int), kp0["response"].astype(int)))
+    assert len(got0) == len(want) - from_lo and set(got0) <= set(want)
 
 
 def test_orientation_uses_the_raw_level(oracle):
@@ -199,3 +214,42 @@ def test_parameter_checks(oracle, bad):
     assert not oracle.check_params(640, 480, p)
     assert oracle.check_params(640, 480, _params(oracle, levels=8))
     assert not oracle.check_params(60, 60, _params(oracle, levels=8))  # levels too small
+
+
+def test_parameter_limits(oracle):
+    """Each documented limit is accepted at its bound and rejected one past it;
+    every level must keep 2 border + 1 pixels on each side."""
+    def ok(W0=200, H0=200, **kw):
+        return oracle.check_params(W0, H0, _params(oracle, **{"levels": 3, "max_feats": 100, **kw}))
+    assert ok()
+    for good, bad in [(dict(fast_thresh=1), dict(fast_thresh=0)), (dict(fast_thresh=254), dict(fast_thresh=255)),
+                      (dict(fast_thresh_lo=254), dict(fast_thresh_lo=255)),
+                      (dict(p_min=1, p_max=16), dict(p_max=17)), (dict(p_min=13, p_max=13), dict(p_min=14, p_max=13)),
+                      (dict(cell=1), dict(cell=0)), (dict(cell=128), dict(cell=129)),
+                      (dict(k_per_cell=8), dict(k_per_cell=9)), (dict(nms_q=7), dict(nms_q=9)),
+                      (dict(nms_q=1), dict(nms_q=2)), (dict(border=16), dict(border=15)),
+                      (dict(W0=4096), dict(W0=4097)), (dict(H0=4096), dict(H0=4097)),
+                      # three levels: W_2 = round(W0 / 1.44) must be >= 39
+                      (dict(W0=56), dict(W0=55)), (dict(H0=56), dict(H0=55))]:
+        assert ok(**good), good
+        assert not ok(**bad), bad
+
+
+def _hand_kps(X, Y, L, D):
+    n = len(X)
+    return {"count": n, "x": np.array(X, np.uint16), "y": np.array(Y, np.uint16), "X": np.array(X, np.uint16),
+            "Y": np.array(Y, np.uint16), "level": np.array(L, np.uint8), "response": np.zeros(n, np.uint16),
+            "k_levels": np.ones(n, np.uint8), "k_resp": np.zeros(n, np.uint32), "angle": np.zeros(n, np.float32),
+            "angle_bin": np.zeros(n, np.uint8), "desc": np.array(D, np.uint32).reshape(n, 8)}
+
+
+def test_match_hand_built(oracle):
+    """Right keypoint 0 can be the match; a right keypoint to the right of the
+    left one (negative disparity) is no candidate."""
+    p = _params(oracle)
+    z, five = [0] * 8, [0x1F] + [0] * 7
+    kl = _hand_kps([100], [50], [0], [z])
+    idx, disp, dist = oracle.match(kl, _hand_kps([90, 95], [50, 50], [0, 0], [z, five]), p)
+    assert (idx[0], disp[0], dist[0]) == (0, 10, 0)
+    idx, disp, dist = oracle.match(kl, _hand_kps([120], [50], [0], [z]), p)
+    assert (idx[0], disp[0], dist[0]) == (-1, 0, 0xFFFF)

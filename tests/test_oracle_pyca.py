@@ -150,3 +150,15 @@ def test_projection_is_nearest(oracle):
     for n in range(1, 8):
         Xs = [oracle.project(x, n, 1.2, 10000) for x in range(400)]
         assert len(set(Xs)) == 400
+
+
+def test_equal_scores_do_not_suppress(oracle):
+    """Sec. II-C-2 NMS suppresses only on a strictly larger score: under either
+    rule, two neighbours with the same (K_l, K_r) both survive."""
+    for rule in (0, 1):
+        _, _, alive = oracle.pfa_core([0, 0], [10, 11], [10, 10], [50, 50], 30, 30, 1, q=3, rule=rule)
+        assert alive.tolist() == [True, True], rule
+    # and a larger K_r alone suppresses under rule 1 (equal K_l), not under rule 0
+    for rule, want in ((0, [True, True]), (1, [False, True])):
+        _, _, alive = oracle.pfa_core([0, 0], [10, 11], [10, 10], [50, 51], 30, 30, 1, q=3, rule=rule)
+        assert alive.tolist() == want, rule

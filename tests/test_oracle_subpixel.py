@@ -151,7 +151,11 @@ def _outlier_case(oracle, ks, d=3):
     base = rng.integers(20, 230, (H, W + d))
     left, right = base[:, :W].copy(), base[:, d:d + W].copy()
     xs = [20 + 25 * i for i in range(len(ks))]
-    offsets = [(dy, dx) for dy in range(-5, 6) for dx in range(-5, 6) if (dy, dx) != (0, 0)]
+    # the window's corners and edge midpoints first, so that every SAD counts
+    # its first and last rows and columns
+    edges = [(5, 5), (5, -5), (-5, 5), (-5, -5), (5, 0), (0, 5), (-5, 0), (0, -5)]
+    offsets = edges + [(dy, dx) for dy in range(-5, 6) for dx in range(-5, 6)
+                       if (dy, dx) != (0, 0) and (dy, dx) not in edges]
     for x, k in zip(xs, ks):
         for dy, dx in offsets[:k]:
             right[20 + dy, x - d + dx] += 1
@@ -232,3 +236,20 @@ def test_minimum_at_either_end_of_the_search_is_rejected(oracle):
     for X in (31, 23):                          # t* = -4 and +4
         sad, d = run(X)
         assert sad == 0 and 2.0 <= d <= 4.0
+
+
+def test_disparity_bounds_are_inclusive(oracle):
+    """A texture mirror-symmetric about the keypoint's column gives SAD(t* - 1)
+    = SAD(t* + 1), so delta = 0 and the disparity is an exact integer: 0 for
+    identical images, D for a right image shifted by D.  Both ends of
+    [0, max_disp] are kept (max_disp = D = 6)."""
+    rng = np.random.default_rng(13)
+    H, W, D = 40, 61, 6
+    B = rng.integers(0, 256, (H, W + D))
+    B[:, :61] = np.concatenate([B[:, :30], B[:, 30:31], B[:, :30][:, ::-1]], axis=1)  # symmetric about 30
+    left, right = B[:, :W].astype(np.uint8), B[:, D:D + W].astype(np.uint8)
+    p = _params(oracle, max_disp=D)
+    r = oracle.subpixel(left, left, _kps([30], [20], [0]), _kps([30], [20], [0]), np.array([0]), p, 5, 5)
+    assert r["sad"][0] == 0 and r["disparity"][0] == 0.0
+    r = oracle.subpixel(left, right, _kps([30], [20], [0]), _kps([30 - D], [20], [0]), np.array([0]), p, 5, 5)
+    assert r["sad"][0] == 0 and r["disparity"][0] == float(D)

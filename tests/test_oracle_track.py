@@ -116,3 +116,8 @@ def test_ratio_bound_second_best_and_scaled_window(oracle):
     deep = kps([100], [7], [bits(2)])
     assert q(deep, 7, 1.0) == (0, 2)
     assert q(deep, 8, 1.0) == (-1, 0xFFFF)          # levels >= 8 have no candidates
+    assert q(kps([100], [3], [bits(2)]), 4, 1.0) == (0, 2)   # level 4 - 1 is in the band
+    one = kps([100], [0], [bits(3)])
+    t = lambda v, md: tuple(int(a[0]) for a in oracle.track(one, 1.2, [100.0], [v], [0], [z], 5.0, md))
+    assert t(45.0, 100) == (0, 3) and t(44.5, 100) == (-1, 0xFFFF)   # |dy| = 5 = r is inside
+    assert t(50.0, 3) == (0, 3) and t(50.0, 2) == (-1, 3)            # max_dist is inclusive

@@ -81,6 +81,8 @@ MUTANTS = [
      "int32_t cells_x = W / c, cells_y = H / c;", 0),
     ("cull_k_plus_one", "for (int32_t i = 0; i < m && i < k; ++i) {", "for (int32_t i = 0; i < m && i <= k; ++i) {", 0),
     # Pyramidal Feature Aggregation (Sec. II-C-2)
+    ("pfa_rule1_equal_scores_dominate", ": (Kl[qp] > kl || (Kl[qp] == kl && Kr[qp] > kr));",
+     ": (Kl[qp] > kl || (Kl[qp] == kl && Kr[qp] >= kr));", 0),
     ("projection_truncated", "int32_t X = (int32_t)floor((double)x * s + 0.5);",
      "int32_t X = (int32_t)floor((double)x * s);", 0),
     ("kl_counts_every_scale", "Kl[p] += occ[(size_t)n * plane + p];", "Kl[p] += 1;", 0),
@@ -107,6 +109,10 @@ MUTANTS = [
     ("pattern_sigma_31_4", "const double sigma = 31.0 / 5.0;", "const double sigma = 31.0 / 4.0;", 0),
     ("pattern_radius_14", "if (v[0] * v[0] + v[1] * v[1] > 169) continue;",
      "if (v[0] * v[0] + v[1] * v[1] > 196) continue;", 0),
+    ("pattern_rejects_shared_y", "if (v[0] == v[2] && v[1] == v[3]) continue;",
+     "if (v[0] != v[2] && v[1] == v[3]) continue;", 0),
+    ("pattern_rejects_shared_x", "if (v[0] == v[2] && v[1] == v[3]) continue;",
+     "if (v[0] == v[2] && v[1] != v[3]) continue;", 0),
     ("pattern_rotated_backwards", "double xr = cx - sy;\n                double yr = sx + cy;",
      "double xr = cx + sy;\n                double yr = cy - sx;", 0),
     ("descriptor_comparison_reversed", "if (a < b) desc[i / 32] |= 1u << (i % 32);",
@@ -122,6 +128,16 @@ MUTANTS = [
      "    if (a->kr != b->kr) return a->kr > b->kr ? -1 : 1;\n    if (a->kl != b->kl) return a->kl > b->kl ? -1 : 1;", 0),
     ("canonical_x_before_y", "    if (a->y != b->y) return a->y < b->y ? -1 : 1;\n    if (a->x != b->x) return a->x < b->x ? -1 : 1;\n    return 0;\n}\n\nint32_t or_check_params",
      "    if (a->x != b->x) return a->x < b->x ? -1 : 1;\n    if (a->y != b->y) return a->y < b->y ? -1 : 1;\n    return 0;\n}\n\nint32_t or_check_params", 0),
+    ("cap_tie_skips_y", "    if (a->y != b->y) return a->y < b->y ? -1 : 1;\n    if (a->x != b->x) return a->x < b->x ? -1 : 1;\n    return 0;\n}\n\nstatic int cmp_canonical",
+     "    if (a->y == b->y) return a->y < b->y ? -1 : 1;\n    if (a->x != b->x) return a->x < b->x ? -1 : 1;\n    return 0;\n}\n\nstatic int cmp_canonical", 0),
+    ("fallback_runs_at_eps_0", "if (p->fast_thresh_lo > 0) {", "if (p->fast_thresh_lo >= 0) {", 0),
+    ("params_threshold_254_rejected", "p->fast_thresh > 254) return -1;", "p->fast_thresh >= 254) return -1;", 0),
+    ("params_cell_128_rejected", "if (p->cell < 1 || p->cell > 128) return -1;",
+     "if (p->cell < 1 || p->cell >= 128) return -1;", 0),
+    ("params_border_16_rejected", "if (p->border < 16) return -1;", "if (p->border <= 16) return -1;", 0),
+    ("params_size_4096_rejected", "W0 > 4096 || H0 > 4096) return -1;", "W0 >= 4096 || H0 > 4096) return -1;", 0),
+    ("params_level_size_39_rejected", "if (W[n] < 2 * p->border + 1 || H[n] < 2 * p->border + 1) return -1;",
+     "if (W[n] <= 2 * p->border + 1 || H[n] < 2 * p->border + 1) return -1;", 0),
     ("fallback_uses_primary_threshold",
      "or_fast(raw[n], W[n], H[n], W[n], p->fast_thresh_lo, p->p_min, p->p_max, p->border, lo, resp_lo);",
      "or_fast(raw[n], W[n], H[n], W[n], p->fast_thresh, p->p_min, p->p_max, p->border, lo, resp_lo);", 0),
@@ -145,6 +161,7 @@ MUTANTS = [
      "right_idx[i] = -1; disparity[i] = 0; dist[i] = 0;", 0),
     ("match_max_disparity_exclusive", "if (disp < 0 || disp > p->max_disp) continue;",
      "if (disp < 0 || disp >= p->max_disp) continue;", 0),
+    ("match_index_0_lost", "if (best_j < 0) {", "if (best_j <= 0) {", 0),
     ("match_threshold_exclusive", "} else if (best_d <= p->match_max_dist) {", "} else if (best_d < p->match_max_dist) {", 0),
     ("match_and_instead_of_xor", "d += popcount32(Lk->desc[(size_t)i * 8 + w] ^ Rk->desc[(size_t)j * 8 + w]);",
      "d += popcount32(Lk->desc[(size_t)i * 8 + w] & Rk->desc[(size_t)j * 8 + w]);", 0),
@@ -158,6 +175,11 @@ MUTANTS = [
     ("subpixel_right_centre_unshifted", "int32_t rc = B[(size_t)yi * W + xr0 + t];",
      "int32_t rc = B[(size_t)yi * W + xr0];", 0),
     ("subpixel_lower_median", "uint64_t median = kept[n_kept / 2];", "uint64_t median = kept[(n_kept - 1) / 2];", 0),
+    ("subpixel_window_last_row_dropped", "for (int32_t dy = -w; dy <= w; ++dy)", "for (int32_t dy = -w; dy < w; ++dy)", 0),
+    ("subpixel_window_last_column_dropped", "for (int32_t dx = -w; dx <= w; ++dx) {", "for (int32_t dx = -w; dx < w; ++dx) {", 0),
+    ("subpixel_zero_disparity_rejected", "if (q * den < num) continue;", "if (q * den <= num) continue;", 0),
+    ("subpixel_max_disparity_rejected", "if (s * (double)(q * den - num) > (double)p->max_disp * (double)den) continue;",
+     "if (s * (double)(q * den - num) >= (double)p->max_disp * (double)den) continue;", 0),
     ("subpixel_last_minimum", "if (acc < sad[best]) best = t + L;", "if (acc <= sad[best]) best = t + L;", 0),
     ("subpixel_parabola_sign", "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);",
      "int64_t num = d3 - d1, den = 2 * (d1 + d3 - 2 * d2);", 0),
@@ -172,6 +194,11 @@ MUTANTS = [
      "if (lvl[q] > OR_MAX_LEVELS) { idx_out[q] = -1; dist_out[q] = 0xFFFF; continue; }", 0),
     ("track_same_level_only", "if (m < (int32_t)lvl[q] - 1 || m > (int32_t)lvl[q] + 1) continue;",
      "if (m != (int32_t)lvl[q]) continue;", 0),
+    ("track_lower_level_dropped", "if (m < (int32_t)lvl[q] - 1 || m > (int32_t)lvl[q] + 1) continue;",
+     "if (m <= (int32_t)lvl[q] - 1 || m > (int32_t)lvl[q] + 1) continue;", 0),
+    ("track_dy_window_exclusive", "if (fabsf(dx) > r || fabsf(dy) > r) continue;",
+     "if (fabsf(dx) > r || fabsf(dy) >= r) continue;", 0),
+    ("track_max_dist_exclusive", "int ok = bd <= max_dist &&", "int ok = bd < max_dist &&", 0),
     ("track_ratio_08", "int ok = bd <= max_dist && (sd == 0x7fffffff || 10 * bd <= 9 * sd);",
      "int ok = bd <= max_dist && (sd == 0x7fffffff || 10 * bd <= 8 * sd);", 0),
     ("track_second_not_updated", "if (d < bd) { sd = bd; bd = d; best = k; }", "if (d < bd) { bd = d; best = k; }", 0),
