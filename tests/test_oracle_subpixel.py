@@ -253,3 +253,28 @@ def test_disparity_bounds_are_inclusive(oracle):
     assert r["sad"][0] == 0 and r["disparity"][0] == 0.0
     r = oracle.subpixel(left, right, _kps([30], [20], [0]), _kps([30 - D], [20], [0]), np.array([0]), p, 5, 5)
     assert r["sad"][0] == 0 and r["disparity"][0] == float(D)
+
+
+def test_max_disparity_is_tested_on_the_refined_value(oracle):
+    """Right image = left shifted by 3 columns and max_disp = 3: a match is
+    kept exactly when its refined disparity 3 - delta is at most 3, i.e. when
+    delta >= 0 -- the bound applies to the sub-pixel value, not to the
+    integer shift or to 3 + delta."""
+    ks = [0] * 8
+    free = _outlier_disparities(oracle, ks, max_disp=64)
+    capped = _outlier_disparities(oracle, ks, max_disp=3)
+    assert (free > 3.0).any() and (free < 3.0).any()          # both signs of delta occur
+    assert np.array_equal(capped >= 0, free <= 3.0)
+    assert np.array_equal(capped[capped >= 0], free[free <= 3.0])
+
+
+def _outlier_disparities(oracle, ks, max_disp, d=3):
+    rng = np.random.default_rng(9)
+    H, W = 40, 25 * len(ks) + 25
+    base = rng.integers(20, 230, (H, W + d))
+    left, right = base[:, :W].astype(np.uint8), base[:, d:d + W].astype(np.uint8)
+    xs = [20 + 25 * i for i in range(len(ks))]
+    n = len(ks)
+    r = oracle.subpixel(left, right, _kps(xs, [20] * n, [0] * n), _kps([x - d for x in xs], [20] * n, [0] * n),
+                        np.arange(n), _params(oracle, max_disp=max_disp), 5, 5)
+    return r["disparity"]

@@ -180,6 +180,8 @@ MUTANTS = [
     ("subpixel_zero_disparity_rejected", "if (q * den < num) continue;", "if (q * den <= num) continue;", 0),
     ("subpixel_max_disparity_rejected", "if (s * (double)(q * den - num) > (double)p->max_disp * (double)den) continue;",
      "if (s * (double)(q * den - num) >= (double)p->max_disp * (double)den) continue;", 0),
+    ("subpixel_max_disparity_on_q_plus_delta", "if (s * (double)(q * den - num) > (double)p->max_disp * (double)den) continue;",
+     "if (s * (double)(q * den + num) > (double)p->max_disp * (double)den) continue;", 0),
     ("subpixel_last_minimum", "if (acc < sad[best]) best = t + L;", "if (acc <= sad[best]) best = t + L;", 0),
     ("subpixel_parabola_sign", "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);",
      "int64_t num = d3 - d1, den = 2 * (d1 + d3 - 2 * d2);", 0),
