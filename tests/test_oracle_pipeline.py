@@ -114,6 +114,10 @@ def test_fallback_threshold_fills_cells_without_a_primary_corner(oracle):
     kp0 = oracle.extract_image(img, _params(oracle, levels=1, max_feats=100000, fast_thresh_lo=0))
     got0 = sorted(zip(kp0["y"].astype(int), kp0["x"].astype(int), kp0["response"].astype(int)))
     assert len(got0) == len(want) - from_lo and set(got0) <= set(want)
+    # eps_lo = 1 is a fallback threshold like any other
+    kp1 = oracle.extract_image(img, _params(oracle, levels=1, max_feats=100000, fast_thresh_lo=1))
+    got1 = set(zip(kp1["y"].astype(int), kp1["x"].astype(int)))
+    assert set((y, x) for y, x, _ in got0) < got1
 
 
 def test_orientation_uses_the_raw_level(oracle):
@@ -229,10 +233,21 @@ def test_parameter_limits(oracle):
                       (dict(k_per_cell=8), dict(k_per_cell=9)), (dict(nms_q=7), dict(nms_q=9)),
                       (dict(nms_q=1), dict(nms_q=2)), (dict(border=16), dict(border=15)),
                       (dict(W0=4096), dict(W0=4097)), (dict(H0=4096), dict(H0=4097)),
+                      (dict(levels=1), dict(levels=0)), (dict(levels=5), dict(levels=9)),
+                      (dict(max_feats=1), dict(max_feats=0)), (dict(pfa_rule=1), dict(pfa_rule=2)),
+                      (dict(pfa_rule=0), dict(pfa_rule=-1)), (dict(p_min=1), dict(p_min=0)),
+                      (dict(k_per_cell=1), dict(k_per_cell=0)), (dict(nms_q=5), dict(nms_q=4)),
+                      (dict(scale=1.01), dict(scale=1.0)),
                       # three levels: W_2 = round(W0 / 1.44) must be >= 39
                       (dict(W0=56), dict(W0=55)), (dict(H0=56), dict(H0=55))]:
         assert ok(**good), good
         assert not ok(**bad), bad
+        # the whole-image extraction refuses the same parameters
+        W0, H0 = bad.get("W0", 200), bad.get("H0", 200)
+        if W0 <= 4096 and H0 <= 4096:
+            kw = {k: v for k, v in bad.items() if k not in ("W0", "H0")}
+            with pytest.raises(ValueError):
+                oracle.extract_image(np.zeros((H0, W0), np.uint8), _params(oracle, **{"levels": 3, "max_feats": 100, **kw}))
 
 
 def _hand_kps(X, Y, L, D):

@@ -94,12 +94,45 @@ def test_bilinear_within_the_q8_error_bound(oracle):
     rng = np.random.default_rng(5)
     cols = np.cumsum(rng.integers(1, 6, 211)) % 2  # 0/255 columns in random runs
     steps = np.repeat((cols * 255).astype(np.uint8)[None, :], 157, axis=0)
-    for img in (smooth, steps):
-        for n in range(1, 8):
-            lvl = oracle.pyramid_level(img, 1.2, n)
-            ref = _reference_bilinear(img, n, lvl.shape[1], lvl.shape[0])
-            bound = _q8_bound(img, n, lvl.shape[1], lvl.shape[0])
-            assert np.all(np.abs(lvl - ref) <= bound), (n, float(np.max(np.abs(lvl - ref) - bound)))
+    for scale in (1.2, 1.1, 1.37, 1.63):
+        for img in (smooth, steps):
+            for n in range(1, 8 if scale < 1.5 else 4):
+                lvl = oracle.pyramid_level(img, scale, n)
+                ref = _reference_bilinear(img, n, lvl.shape[1], lvl.shape[0], scale)
+                bound = _q8_bound(img, n, lvl.shape[1], lvl.shape[0], scale)
+                assert np.all(np.abs(lvl - ref) <= bound), (scale, n, float(np.max(np.abs(lvl - ref) - bound)))
+
+
+def test_scale_two_is_the_rounded_2x2_mean(oracle):
+    """At zeta = 2 every level-1 pixel centre lies exactly between four level-0
+    centres (u = 2x + 1/2, weights 128/256), so bilinear resampling is the 2x2
+    box mean rounded half up, (sum + 2) div 4 -- with many exact ties."""
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 256, (64, 90)).astype(np.uint8)
+    lvl = oracle.pyramid_level(img, 2.0, 1)
+    H, W = lvl.shape
+    assert (H, W) == (32, 45)
+    I = img.astype(int)
+    s = I[0:2 * H:2, 0:2 * W:2] + I[1:2 * H:2, 0:2 * W:2] + I[0:2 * H:2, 1:2 * W:2] + I[1:2 * H:2, 1:2 * W:2]
+    assert np.array_equal(lvl, (s + 2) // 4)
+    assert ((s % 4) == 2).sum() > 100
+
+
+def test_blur_rounds_half_up_at_exact_ties(oracle):
+    """Two pixels on a zero image put the blurred centre exactly on a half
+    (82 at the centre and 244 beside it: (54*54*82 + 54*49*244) / 65536 = 13.5,
+    so 14) and just below one (138 at the centre and 119 diagonal:
+    (54*54*138 + 49*49*119) / 65536 = 10.49998..., so 10)."""
+    for pix, want in (({(7, 7): 82, (7, 8): 244}, 14), ({(7, 7): 138, (8, 8): 119}, 10)):
+        img = np.zeros((15, 15), np.uint8)
+        for (y, x), v in pix.items():
+            img[y, x] = v
+        out = oracle.blur(img)
+        assert out[7, 7] == want
+        w = oracle.blur_weights() / 256.0
+        ref = ndimage.convolve1d(ndimage.convolve1d(img.astype(np.float64), w, axis=1, mode="nearest"), w, axis=0,
+                                 mode="nearest")
+        assert np.array_equal(out, np.floor(ref + 0.5).astype(np.uint8))
 
 
 def test_pyramid_preserves_mirror_symmetry(oracle):

@@ -278,3 +278,44 @@ def _outlier_disparities(oracle, ks, max_disp, d=3):
     r = oracle.subpixel(left, right, _kps(xs, [20] * n, [0] * n), _kps([x - d for x in xs], [20] * n, [0] * n),
                         np.arange(n), _params(oracle, max_disp=max_disp), 5, 5)
     return r["disparity"]
+
+
+def test_refinement_against_brute_force(oracle):
+    """The SAD curve over shifts -L..L of the centre-normalised windows, its
+    first minimum, the parabola vertex delta = (d1 - d3) / (2 (d1 + d3 - 2 d2))
+    and the disparity x - xr0 - t* - delta, all computed here from their
+    definitions in numpy for keypoints of a random scene shifted by 3."""
+    rng = np.random.default_rng(14)
+    H, W, d, w, L = 40, 230, 3, 5, 5
+    base = rng.integers(0, 256, (H, W + d))
+    left, right = base[:, :W].astype(np.uint8), base[:, d:d + W].astype(np.uint8)
+    right[15:26, :] = np.clip(right[15:26, :].astype(int) + rng.integers(-6, 7, (11, W)), 0, 255)
+    xs = [20 + 25 * i for i in range(8)]
+    Xr = [x - d + o for x, o in zip(xs, (0, 1, -1, 2, -2, 0, 1, -1))]
+    r = oracle.subpixel(left, right, _kps(xs, [20] * 8, [0] * 8), _kps(Xr, [20] * 8, [0] * 8), np.arange(8),
+                        _params(oracle), w, L)
+    A, B = left.astype(np.int64), right.astype(np.int64)
+    n_ok, kept_sads, want_disp = 0, [], {}
+    for i, (x, xr0) in enumerate(zip(xs, Xr)):
+        lp = A[20 - w:21 + w, x - w:x + w + 1] - A[20, x]
+        sad = [int(np.abs(lp - (B[20 - w:21 + w, xr0 + t - w:xr0 + t + w + 1] - B[20, xr0 + t])).sum())
+               for t in range(-L, L + 1)]
+        k = int(np.argmin(sad))                      # first minimum
+        assert r["sad"][i] == sad[k]
+        if k in (0, 2 * L):
+            assert r["disparity"][i] == -1.0
+            continue
+        d1, d2, d3 = sad[k - 1], sad[k], sad[k + 1]
+        delta = (d1 - d3) / (2 * (d1 + d3 - 2 * d2))
+        want_disp[i] = x - xr0 - (k - L) - delta
+        kept_sads.append(sad[k])
+    # outliers: 10 SAD > 21 median, the median being element count / 2 of the
+    # kept SADs in ascending order
+    median = sorted(kept_sads)[len(kept_sads) // 2]
+    for i, want in want_disp.items():
+        if 10 * int(r["sad"][i]) > 21 * median:
+            assert r["disparity"][i] == -1.0
+            continue
+        assert abs(float(r["disparity"][i]) - want) <= 1e-6 * max(1.0, abs(want)), (i, r["disparity"][i], want)
+        n_ok += 1
+    assert n_ok >= 6

@@ -121,3 +121,6 @@ def test_ratio_bound_second_best_and_scaled_window(oracle):
     t = lambda v, md: tuple(int(a[0]) for a in oracle.track(one, 1.2, [100.0], [v], [0], [z], 5.0, md))
     assert t(45.0, 100) == (0, 3) and t(44.5, 100) == (-1, 0xFFFF)   # |dy| = 5 = r is inside
     assert t(50.0, 3) == (0, 3) and t(50.0, 2) == (-1, 3)            # max_dist is inclusive
+    last = np.zeros(8, np.uint32)
+    last[7] = np.uint32(0xF0000000)                                   # 4 bits in the last word
+    assert q(kps([100], [0], [last]), 0, 5.0) == (0, 4)

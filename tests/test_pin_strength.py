@@ -42,6 +42,9 @@ MUTANTS = [
      "uint32_t top = (uint32_t)a * p00 + (256u - (uint32_t)a) * p01;", 0),
     ("bilinear_no_rounding", "out[(size_t)y * pitch_out + x] = (uint8_t)((v + 32768u) >> 16);",
      "out[(size_t)y * pitch_out + x] = (uint8_t)(v >> 16);", 0),
+    ("pyramid_rounds_ties_down", "out[(size_t)y * pitch_out + x] = (uint8_t)((v + 32768u) >> 16);",
+     "out[(size_t)y * pitch_out + x] = (uint8_t)((v + 32767u) >> 16);", 0),
+    ("bilinear_shift_at_255", "if (w == 256) { i += 1; w = 0; }", "if (w == 255) { i += 1; w = 0; }", 0),
     # Gaussian (Sec. III; reading 2)
     ("blur_sigma_sqrt2", "g[i + 3] = exp(-(double)(i * i) / (2.0 * 2.0 * 2.0));",
      "g[i + 3] = exp(-(double)(i * i) / (2.0 * 2.0));", 0),
@@ -52,6 +55,10 @@ MUTANTS = [
      "out[(size_t)y * pitch_out + x] = (uint8_t)(acc >> 16);", 0),
     ("blur_vertical_border", "acc += (uint32_t)w[j + 3] * h[(size_t)clampi(y + j, 0, H - 1) * W + x];",
      "acc += (uint32_t)w[j + 3] * h[(size_t)clampi(y + j, 0, H - 2) * W + x];", 0),
+    ("blur_rounds_ties_down", "out[(size_t)y * pitch_out + x] = (uint8_t)((acc + 32768u) >> 16);",
+     "out[(size_t)y * pitch_out + x] = (uint8_t)((acc + 32767u) >> 16);", 0),
+    ("blur_rounds_just_below_half_up", "out[(size_t)y * pitch_out + x] = (uint8_t)((acc + 32768u) >> 16);",
+     "out[(size_t)y * pitch_out + x] = (uint8_t)((acc + 32769u) >> 16);", 0),
     # FAST with Bounded Rectification (Sec. II-A, Eq. 1-3)
     ("ring_mirrored", "static const int32_t RING_DY[16] = { 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1, 0, 1, 2, 3 };",
      "static const int32_t RING_DY[16] = { -3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3 };", 0),
@@ -130,6 +137,14 @@ MUTANTS = [
      "    if (a->x != b->x) return a->x < b->x ? -1 : 1;\n    if (a->y != b->y) return a->y < b->y ? -1 : 1;\n    return 0;\n}\n\nint32_t or_check_params", 0),
     ("cap_tie_skips_y", "    if (a->y != b->y) return a->y < b->y ? -1 : 1;\n    if (a->x != b->x) return a->x < b->x ? -1 : 1;\n    return 0;\n}\n\nstatic int cmp_canonical",
      "    if (a->y == b->y) return a->y < b->y ? -1 : 1;\n    if (a->x != b->x) return a->x < b->x ? -1 : 1;\n    return 0;\n}\n\nstatic int cmp_canonical", 0),
+    ("fallback_needs_eps_lo_2", "if (p->fast_thresh_lo > 0) {", "if (p->fast_thresh_lo > 1) {", 0),
+    ("params_pfa_rule_unchecked", "if (p->pfa_rule < 0 || p->pfa_rule > 1) return -1;",
+     "if (p->pfa_rule < 0 || p->pfa_rule > 1) return 0;", 0),
+    ("extract_ignores_invalid_params", "if (or_check_params(W0, H0, p) != 0) return -1;",
+     "if (or_check_params(W0, H0, p) != 0) return 0;", 0),
+    ("params_nms_q_parity_bit", "(p->nms_q & 1) == 0", "(p->nms_q & 2) == 0", 0),
+    ("params_levels_from_2", "if (p->levels < 1 || p->levels > OR_MAX_LEVELS) return -1;",
+     "if (p->levels < 2 || p->levels > OR_MAX_LEVELS) return -1;", 0),
     ("fallback_runs_at_eps_0", "if (p->fast_thresh_lo > 0) {", "if (p->fast_thresh_lo >= 0) {", 0),
     ("params_threshold_254_rejected", "p->fast_thresh > 254) return -1;", "p->fast_thresh >= 254) return -1;", 0),
     ("params_cell_128_rejected", "if (p->cell < 1 || p->cell > 128) return -1;",
@@ -182,6 +197,10 @@ MUTANTS = [
      "if (s * (double)(q * den - num) >= (double)p->max_disp * (double)den) continue;", 0),
     ("subpixel_max_disparity_on_q_plus_delta", "if (s * (double)(q * den - num) > (double)p->max_disp * (double)den) continue;",
      "if (s * (double)(q * den + num) > (double)p->max_disp * (double)den) continue;", 0),
+    ("parabola_denominator_3", "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);",
+     "int64_t num = d1 - d3, den = 3 * (d1 + d3 - 2 * d2);", 0),
+    ("parabola_centre_weight_3", "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);",
+     "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 3 * d2);", 0),
     ("subpixel_last_minimum", "if (acc < sad[best]) best = t + L;", "if (acc <= sad[best]) best = t + L;", 0),
     ("subpixel_parabola_sign", "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);",
      "int64_t num = d3 - d1, den = 2 * (d1 + d3 - 2 * d2);", 0),
@@ -201,6 +220,8 @@ MUTANTS = [
     ("track_dy_window_exclusive", "if (fabsf(dx) > r || fabsf(dy) > r) continue;",
      "if (fabsf(dx) > r || fabsf(dy) >= r) continue;", 0),
     ("track_max_dist_exclusive", "int ok = bd <= max_dist &&", "int ok = bd < max_dist &&", 0),
+    ("track_hamming_7_words", "for (int32_t w = 0; w < 8; ++w)\n                d += popcount32(desc[(size_t)q * 8 + w]",
+     "for (int32_t w = 0; w < 7; ++w)\n                d += popcount32(desc[(size_t)q * 8 + w]", 0),
     ("track_ratio_08", "int ok = bd <= max_dist && (sd == 0x7fffffff || 10 * bd <= 9 * sd);",
      "int ok = bd <= max_dist && (sd == 0x7fffffff || 10 * bd <= 8 * sd);", 0),
     ("track_second_not_updated", "if (d < bd) { sd = bd; bd = d; best = k; }", "if (d < bd) { bd = d; best = k; }", 0),
