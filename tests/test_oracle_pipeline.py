@@ -173,10 +173,12 @@ def _brute_match(kl, kr, p, oracle):
 
 def test_match_brute_force(oracle):
     pair = scenes.planes_pair(400, 220, 0, 17, 18)
-    p = _params(oracle, levels=3, max_feats=300, match_max_dist=90)
-    kl, kr, (idx, disp, dist) = oracle.extract_pair(pair.left, pair.right, p)
-    want = _brute_match(kl, kr, p, oracle)
-    assert list(zip(idx.tolist(), disp.tolist(), dist.tolist())) == want
+    for feats in (300, 100000):  # equal counts (capped), then different counts
+        p = _params(oracle, levels=3, max_feats=feats, match_max_dist=90)
+        kl, kr, (idx, disp, dist) = oracle.extract_pair(pair.left, pair.right, p)
+        want = _brute_match(kl, kr, p, oracle)
+        assert list(zip(idx.tolist(), disp.tolist(), dist.tolist())) == want
+    assert kl["count"] != kr["count"]
     assert (idx >= 0).sum() > 20
 
 
@@ -268,3 +270,51 @@ def test_match_hand_built(oracle):
     assert (idx[0], disp[0], dist[0]) == (0, 10, 0)
     idx, disp, dist = oracle.match(kl, _hand_kps([120], [50], [0], [z]), p)
     assert (idx[0], disp[0], dist[0]) == (-1, 0, 0xFFFF)
+    # more right keypoints than left ones, the best at index 2; levels come
+    # from each list (left levels 0 and 2; right keypoint 1 is at level 2)
+    kl2 = _hand_kps([100, 100], [50, 50], [0, 2], [z, z])
+    kr2 = _hand_kps([97, 92, 90], [50, 50, 50], [2, 0, 0], [z, z, five])
+    idx, disp, dist = oracle.match(kl2, kr2, p)
+    assert (idx[0], disp[0], dist[0]) == (1, 8, 0)    # right 0 (level 2) is outside left 0's band
+    assert (idx[1], disp[1], dist[1]) == (0, 3, 0)    # level 2: right 0 only
+    idx, disp, dist = oracle.match(kl, _hand_kps([95, 90], [50, 50], [0, 0], [five, z]), p)
+    assert (idx[0], disp[0], dist[0]) == (1, 10, 0)   # the best right index is past the left list's length
+
+
+def test_pipeline_composes_its_pinned_parts(oracle):
+    """The whole-image extraction (no cap) equals its parts composed here:
+    each level resampled (pinned on its own), its CRF at both thresholds,
+    the cell culling, the s0 projection, then PFA by brute force -- K_l and
+    K_r summed per s0 pixel, a keypoint suppressed by a q x q neighbour with
+    larger K_l and larger K_r -- on a ragged, non-square image."""
+    img = scenes.random_image(210, 333, seed=12)
+    H0, W0 = img.shape
+    p = _params(oracle, levels=4, max_feats=100000, fast_thresh_lo=7)
+    kp = oracle.extract_image(img, p)
+    W, H, c = oracle.level_geometry(W0, H0, p.levels, p.scale, p.cell)
+    cand = []
+    for n in range(p.levels):
+        lvl = img if n == 0 else oracle.pyramid_level(img, p.scale, n)
+        assert lvl.shape == (H[n], W[n])
+        hi, resp = oracle.fast(lvl, p.fast_thresh, p.p_min, p.p_max, p.border)
+        lo, _ = oracle.fast(lvl, p.fast_thresh_lo, p.p_min, p.p_max, p.border)
+        xs, ys, rs = oracle.cull_level(hi, lo, resp, int(c[n]), p.k_per_cell)
+        for x, y, r in zip(xs.tolist(), ys.tolist(), rs.tolist()):
+            cand.append((n, x, y, r, oracle.project(x, n, p.scale, W0), oracle.project(y, n, p.scale, H0)))
+    Kl, Kr = {}, {}
+    for n, x, y, r, X, Y in cand:
+        Kl[X, Y] = Kl.get((X, Y), 0) + 1
+        Kr[X, Y] = Kr.get((X, Y), 0) + r
+    rad = (p.nms_q - 1) // 2
+    want = []
+    for n, x, y, r, X, Y in cand:
+        kl, kr = Kl[X, Y], Kr[X, Y]
+        dominated = any(Kl.get((X + dx, Y + dy), 0) > kl and Kr.get((X + dx, Y + dy), 0) > kr
+                        for dy in range(-rad, rad + 1) for dx in range(-rad, rad + 1) if dx or dy)
+        if not dominated:
+            want.append((n, y, x, X, Y, r, kl, kr))
+    want.sort()
+    got = list(zip(*(kp[f].astype(int).tolist() for f in ("level", "y", "x", "X", "Y", "response", "k_levels",
+                                                          "k_resp"))))
+    assert got == want
+    assert len(set(lv for lv, *_ in want)) == p.levels and any(k > 1 for *_, k, _ in want)

@@ -319,3 +319,42 @@ def test_refinement_against_brute_force(oracle):
         assert abs(float(r["disparity"][i]) - want) <= 1e-6 * max(1.0, abs(want)), (i, r["disparity"][i], want)
         n_ok += 1
     assert n_ok >= 6
+
+
+def test_matches_are_looked_up_through_right_idx(oracle):
+    """Each left keypoint is refined against the right keypoint its match
+    names, on the left keypoint's level: two left keypoints whose matches are
+    listed in the other order, a right list longer than the left one whose
+    entries carry other levels, and an unmatched left keypoint (-1)."""
+    rng = np.random.default_rng(15)
+    H, W, d = 40, 120, 3
+    base = rng.integers(0, 256, (H, W + d))
+    left, right = base[:, :W].astype(np.uint8), base[:, d:d + W].astype(np.uint8)
+    kl = _kps([30, 70, 50], [20, 20, 20], [0, 0, 0])
+    kr = _kps([67, 27, 5, 90], [20, 20, 20, 20], [1, 1, 1, 1])   # 70 - 3 and 30 - 3, then two others
+    r = oracle.subpixel(left, right, kl, kr, np.array([1, 0, -1]), _params(oracle), 5, 5)
+    assert r["sad"][0] == 0 and r["sad"][1] == 0 and r["sad"][2] == 0xFFFFFFFF
+    assert np.all(np.abs(r["disparity"][:2] - d) <= 1.0) and r["disparity"][2] == -1.0
+
+
+def test_outlier_rule_covers_every_left_keypoint(oracle):
+    """Two left keypoints at the same place share one right keypoint (SAD 22
+    each) after three with SAD 10: the rule runs over the left list, so both
+    late ones are rejected although the right list is shorter."""
+    rng = np.random.default_rng(9)
+    H, W, d = 40, 125, 3
+    base = rng.integers(20, 230, (H, W + d))
+    left, right = base[:, :W].copy(), base[:, d:d + W].copy()
+    xs = [20, 45, 70, 95]
+    edges = [(5, 5), (5, -5), (-5, 5), (-5, -5), (5, 0), (0, 5), (-5, 0), (0, -5)]
+    offsets = edges + [(dy, dx) for dy in range(-5, 6) for dx in range(-5, 6)
+                       if (dy, dx) != (0, 0) and (dy, dx) not in edges]
+    for x, k in zip(xs, (10, 10, 10, 22)):
+        for dy, dx in offsets[:k]:
+            right[20 + dy, x - d + dx] += 1
+    left, right = left.astype(np.uint8), right.astype(np.uint8)
+    kl = _kps(xs + [95], [20] * 5, [0] * 5)
+    kr = _kps([x - d for x in xs], [20] * 4, [0] * 4)
+    r = oracle.subpixel(left, right, kl, kr, np.array([0, 1, 2, 3, 3]), _params(oracle), 5, 5)
+    assert r["sad"].tolist() == [10, 10, 10, 22, 22]
+    assert (r["disparity"] >= 0).tolist() == [True, True, True, False, False]

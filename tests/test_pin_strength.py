@@ -158,6 +158,10 @@ MUTANTS = [
      "or_fast(raw[n], W[n], H[n], W[n], p->fast_thresh, p->p_min, p->p_max, p->border, lo, resp_lo);", 0),
     ("pipeline_ignores_pfa_rule", "or_pfa_core(n_cand, lev, X, Y, R, W0, H0, L, p->nms_q, p->pfa_rule, Kl, Kr, alive);",
      "or_pfa_core(n_cand, lev, X, Y, R, W0, H0, L, p->nms_q, 0, Kl, Kr, alive);", 0),
+    ("pipeline_pyramid_width_as_height", "or_pyramid_level(L0, W0, H0, pitch0, p->scale, n, raw[n], W[n], H[n], W[n]);",
+     "or_pyramid_level(L0, H0, H0, pitch0, p->scale, n, raw[n], W[n], H[n], W[n]);", 0),
+    ("pipeline_pfa_width_as_height", "or_pfa_core(n_cand, lev, X, Y, R, W0, H0, L, p->nms_q, p->pfa_rule, Kl, Kr, alive);",
+     "or_pfa_core(n_cand, lev, X, Y, R, H0, H0, L, p->nms_q, p->pfa_rule, Kl, Kr, alive);", 0),
     ("orientation_on_blurred_level", "or_orient(raw[k->level], W[k->level], k->x, k->y, &m10, &m01, &theta, &bin);",
      "or_orient(blur[k->level], W[k->level], k->x, k->y, &m10, &m01, &theta, &bin);", 0),
     ("descriptor_on_raw_level", "or_describe(blur[k->level], W[k->level], k->x, k->y,",
@@ -177,6 +181,8 @@ MUTANTS = [
     ("match_max_disparity_exclusive", "if (disp < 0 || disp > p->max_disp) continue;",
      "if (disp < 0 || disp >= p->max_disp) continue;", 0),
     ("match_index_0_lost", "if (best_j < 0) {", "if (best_j <= 0) {", 0),
+    ("match_loops_over_left_count", "for (int32_t j = 0; j < Rk->count; ++j) {", "for (int32_t j = 0; j < Lk->count; ++j) {", 0),
+    ("match_right_level_from_left", "int32_t nr = Rk->level[j];", "int32_t nr = Lk->level[j];", 0),
     ("match_threshold_exclusive", "} else if (best_d <= p->match_max_dist) {", "} else if (best_d < p->match_max_dist) {", 0),
     ("match_and_instead_of_xor", "d += popcount32(Lk->desc[(size_t)i * 8 + w] ^ Rk->desc[(size_t)j * 8 + w]);",
      "d += popcount32(Lk->desc[(size_t)i * 8 + w] & Rk->desc[(size_t)j * 8 + w]);", 0),
@@ -201,6 +207,12 @@ MUTANTS = [
      "int64_t num = d1 - d3, den = 3 * (d1 + d3 - 2 * d2);", 0),
     ("parabola_centre_weight_3", "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);",
      "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 3 * d2);", 0),
+    ("subpixel_left_x_by_match_index", "int32_t n = Lk->level[i], xi = Lk->x[i], yi = Lk->y[i];",
+     "int32_t n = Lk->level[i], xi = Lk->x[j], yi = Lk->y[i];", 0),
+    ("subpixel_level_from_right", "int32_t n = Lk->level[i], xi = Lk->x[i], yi = Lk->y[i];",
+     "int32_t n = Rk->level[i], xi = Lk->x[i], yi = Lk->y[i];", 0),
+    ("subpixel_outlier_loop_over_right", "for (int32_t i = 0; i < Lk->count; ++i)\n            if (disp_out[i] >= 0.0f",
+     "for (int32_t i = 0; i < Rk->count; ++i)\n            if (disp_out[i] >= 0.0f", 0),
     ("subpixel_last_minimum", "if (acc < sad[best]) best = t + L;", "if (acc <= sad[best]) best = t + L;", 0),
     ("subpixel_parabola_sign", "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);",
      "int64_t num = d3 - d1, den = 2 * (d1 + d3 - 2 * d2);", 0),
