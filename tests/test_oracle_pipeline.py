@@ -87,6 +87,27 @@ def test_cap_breaks_ties_by_level_then_position(oracle):
     _cap_cuts_hold(oracle, tiled, 3, lambda f, a, b: f["level"][a] == f["level"][b] and f["x"][a] > f["x"][b])
 
 
+def test_cap_orders_by_summed_response_before_own_response(oracle):
+    """Among keypoints with equal K_l, the cap keeps the larger K_r (summed over
+    the levels) even when its own response is the smaller: a cap cut between
+    such neighbours in the priority order."""
+    img = scenes.random_image(240, 320, seed=9)
+    p = _params(oracle, levels=5, max_feats=100000)
+    full = oracle.extract_image(img, p)
+    n = full["count"]
+    pr = lambda i: (-int(full["k_levels"][i]), -int(full["k_resp"][i]), -int(full["response"][i]),
+                    int(full["level"][i]), int(full["y"][i]), int(full["x"][i]))
+    order = sorted(range(n), key=pr)
+    cuts = [c for c in range(1, n) if full["k_levels"][order[c - 1]] == full["k_levels"][order[c]]
+            and full["response"][order[c - 1]] < full["response"][order[c]]]
+    assert len(cuts) >= 3
+    for cap in cuts[:6]:
+        capped = oracle.extract_image(img, _params(oracle, levels=5, max_feats=cap))
+        want = sorted(order[:cap])
+        for f in ("x", "y", "level"):
+            assert np.array_equal(capped[f], full[f][want]), (cap, f)
+
+
 def test_fallback_threshold_fills_cells_without_a_primary_corner(oracle):
     """One level (PFA never suppresses there): per 32x32 cell, the strongest
     corner at eps = 20 (response, then y, then x), or, in a cell without one,
@@ -136,6 +157,33 @@ def test_orientation_uses_the_raw_level(oracle):
         m10, m01 = int((dx * patch).sum()), int((dy * patch).sum())
         assert (kp["m10"][i], kp["m01"][i]) == (m10, m01)
         assert abs(float(kp["angle"][i]) - np.arctan2(m01, m10)) < 1e-6
+
+
+def test_level0_sector_and_descriptor_by_brute_force(oracle):
+    """Level-0 keypoints: the sector is the 12-degree sector of theta (away
+    from exact boundaries), and the descriptor is BRIEF on the blurred input
+    image with that sector's rotated pattern -- bit i = [B(p_i) < B(q_i)],
+    bit i in word i / 32 -- computed here pair by pair."""
+    img = scenes.random_image(200, 260, seed=4)
+    kp = oracle.extract_image(img, _params(oracle, levels=3, max_feats=10000))
+    blur = oracle.blur(img).astype(int)
+    rot = oracle.pattern_rotated()
+    lv0 = np.nonzero(kp["level"] == 0)[0]
+    sectors = set()
+    for i in lv0:
+        x, y = int(kp["x"][i]), int(kp["y"][i])
+        theta = np.arctan2(int(kp["m01"][i]), int(kp["m10"][i])) % (2 * np.pi)
+        b = int(kp["angle_bin"][i])
+        edge = theta / (2 * np.pi / 30)
+        if abs(edge - round(edge)) > 1e-9:
+            assert b == int(edge) % 30, (i, b, edge)
+        sectors.add(b)
+        want = np.zeros(8, np.uint32)
+        for j, (px, py, qx, qy) in enumerate(rot[b].astype(int).tolist()):
+            if blur[y + py, x + px] < blur[y + qy, x + qx]:
+                want[j // 32] |= np.uint32(1 << (j % 32))
+        assert np.array_equal(kp["desc"][i], want), i
+    assert len(sectors) > 10
 
 
 def test_pfa_reduces_keypoints_across_levels(oracle):

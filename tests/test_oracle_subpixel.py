@@ -177,6 +177,8 @@ def test_outlier_bound_is_inclusive_at_21_tenths_of_the_median(oracle):
     assert _outlier_case(oracle, [10, 10, 10, 21, 22]) == [True, True, True, True, False]
     assert _outlier_case(oracle, [10, 10, 20, 42]) == [True, True, True, True]
     assert _outlier_case(oracle, [10, 10, 20, 43]) == [True, True, True, False]
+    # the median is taken in SAD order, not in keypoint order
+    assert _outlier_case(oracle, [22, 10, 21, 10, 10]) == [False, True, True, True, True]
 
 
 def test_search_centre_is_the_nearest_level_column(oracle):
@@ -253,6 +255,22 @@ def test_disparity_bounds_are_inclusive(oracle):
     assert r["sad"][0] == 0 and r["disparity"][0] == 0.0
     r = oracle.subpixel(left, right, _kps([30], [20], [0]), _kps([30 - D], [20], [0]), np.array([0]), p, 5, 5)
     assert r["sad"][0] == 0 and r["disparity"][0] == float(D)
+
+
+def test_negative_refined_disparity_is_rejected(oracle):
+    """Identical images: the true disparity is 0 and the refined one is
+    -delta, so a match is kept exactly when delta <= 0."""
+    ks = [0] * 8
+    free = _outlier_disparities(oracle, ks, max_disp=64, d=0)
+    assert ((free == -1.0).sum() >= 2) and ((free >= 0).sum() >= 2)
+    rng = np.random.default_rng(9)
+    H, W = 40, 25 * len(ks) + 25
+    img = rng.integers(20, 230, (H, W)).astype(np.int64)
+    for i, x in enumerate(20 + 25 * k for k in range(len(ks))):
+        lp = img[15:26, x - 5:x + 6] - img[20, x]
+        sad = [int(np.abs(lp - (img[15:26, x + t - 5:x + t + 6] - img[20, x + t])).sum()) for t in (-1, 0, 1)]
+        delta = (sad[0] - sad[2]) / (2 * (sad[0] + sad[2] - 2 * sad[1]))
+        assert (free[i] >= 0) == (delta <= 0), (i, delta, free[i])
 
 
 def test_max_disparity_is_tested_on_the_refined_value(oracle):

@@ -153,6 +153,10 @@ MUTANTS = [
     ("params_size_4096_rejected", "W0 > 4096 || H0 > 4096) return -1;", "W0 >= 4096 || H0 > 4096) return -1;", 0),
     ("params_level_size_39_rejected", "if (W[n] < 2 * p->border + 1 || H[n] < 2 * p->border + 1) return -1;",
      "if (W[n] <= 2 * p->border + 1 || H[n] < 2 * p->border + 1) return -1;", 0),
+    ("cap_ignores_summed_response", "    if (a->kl != b->kl) return a->kl > b->kl ? -1 : 1;\n    if (a->kr != b->kr) return a->kr > b->kr ? -1 : 1;\n",
+     "    if (a->kl != b->kl) return a->kl > b->kl ? -1 : 1;\n", 0),
+    ("angle_bin_not_stored", "out->angle_bin[i] = (uint8_t)bin;", ";", 0),
+    ("descriptor_uses_sector_0", "rot + (size_t)bin * OR_NPAIRS * 4", "rot + (size_t)0 * OR_NPAIRS * 4", 0),
     ("fallback_uses_primary_threshold",
      "or_fast(raw[n], W[n], H[n], W[n], p->fast_thresh_lo, p->p_min, p->p_max, p->border, lo, resp_lo);",
      "or_fast(raw[n], W[n], H[n], W[n], p->fast_thresh, p->p_min, p->p_max, p->border, lo, resp_lo);", 0),
@@ -213,6 +217,8 @@ MUTANTS = [
      "int32_t n = Rk->level[i], xi = Lk->x[i], yi = Lk->y[i];", 0),
     ("subpixel_outlier_loop_over_right", "for (int32_t i = 0; i < Lk->count; ++i)\n            if (disp_out[i] >= 0.0f",
      "for (int32_t i = 0; i < Rk->count; ++i)\n            if (disp_out[i] >= 0.0f", 0),
+    ("negative_disparity_kept", "if (q * den < num) continue;", ";", 0),
+    ("median_of_unsorted_sads", "qsort(kept, (size_t)n_kept, sizeof(uint32_t), cmp_u32);", ";", 0),
     ("subpixel_last_minimum", "if (acc < sad[best]) best = t + L;", "if (acc <= sad[best]) best = t + L;", 0),
     ("subpixel_parabola_sign", "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);",
      "int64_t num = d3 - d1, den = 2 * (d1 + d3 - 2 * d2);", 0),
