@@ -1,8 +1,9 @@
-"""The binding's ctypes structures have the layout of the C structures in
-include/jslam.h: a small C program, compiled here against the header,
-prints sizeof and offsetof of every field the binding declares, and each
-must equal ctypes' size and offset (a field added, dropped, reordered or
-retyped on one side only fails here, on the CPU)."""
+"""The binding agrees with include/jslam.h.  Structures: a small C program,
+compiled here against the header, prints sizeof and offsetof of every field
+the binding declares, and each must equal ctypes' size and offset.
+Functions: every prototype's arguments and result have the kinds the
+binding declares.  A field or argument added, dropped, reordered or retyped
+on one side only fails here, on the CPU."""
 import ctypes
 import os
 import shutil
@@ -43,3 +44,50 @@ def test_struct_layout_matches_the_header(c_layout, cname, cls):
     assert ctypes.sizeof(cls) == c_layout[cname, "sizeof"], cname
     for fname, _ in cls._fields_:
         assert getattr(cls, fname).offset == c_layout[cname, fname], (cname, fname)
+
+
+def _c_kind(decl):
+    d = " ".join(decl.replace("const", " ").split())
+    if "*" in d:
+        return "ptr"
+    t = d.rsplit(" ", 1)[0] if " " in d else d
+    return {"int32_t": "i32", "int": "i32", "float": "f32", "double": "f64", "size_t": "size",
+            "jslam_status": "i32", "void": "void"}.get(t, "struct:" + t)
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return "void"
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or getattr(t, "_type_", None) is not None and \
+            isinstance(t, type) and issubclass(t, ctypes._Pointer):
+        return "ptr"
+    names = {cls: c for c, cls in PAIRS}
+    if t in names:
+        return "struct:" + names[t]
+    if t is ctypes.c_size_t:  # checked before the integers: an alias of c_ulong here
+        return "size"
+    return {ctypes.c_int32: "i32", ctypes.c_float: "f32", ctypes.c_double: "f64"}[t]
+
+
+def test_prototypes_match_the_binding():
+    """Every entry point the header declares has, in the binding, the same
+    number of arguments and the same kind (pointer, 32-bit integer, float,
+    double, size_t or a structure by value) at every position, and the same
+    kind of result."""
+    import re
+    text = open(os.path.join(ROOT, "include", "jslam.h")).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    protos = re.findall(r"\b(jslam_status|void|int32_t|const char\s*\*)\s*(jslam_\w+)\s*\(([^;{]*?)\)\s*;", text,
+                        flags=re.S)
+    lib = jslam.lib()
+    seen = set()
+    for ret, name, params in protos:
+        params = [p.strip() for p in params.split(",")]
+        want = [] if params == ["void"] else [_c_kind(p) for p in params]
+        fn = getattr(lib, name)
+        got = [_ctypes_kind(t) for t in fn.argtypes]
+        assert got == want, (name, got, want)
+        rk = "ptr" if "*" in ret else _c_kind(ret + " r")
+        assert _ctypes_kind(fn.restype) == rk, (name, fn.restype, ret)
+        seen.add(name)
+    assert seen == set(jslam.SYMBOLS)
