@@ -20,6 +20,11 @@ PAIRS = [("jslam_config", jslam.Config), ("jslam_image", jslam.Image), ("jslam_s
          ("jslam_level_view", jslam.LevelView), ("jslam_tuning", jslam.Tuning), ("jslam_skip_view", jslam.SkipView)]
 
 
+CONSTANTS = {"JSLAM_OK": "OK", "JSLAM_ERR_ARG": "ERR_ARG", "JSLAM_ERR_CUDA": "ERR_CUDA", "JSLAM_ERR_NOMEM": "ERR_NOMEM",
+             "JSLAM_ERR_CAPACITY": "ERR_CAPACITY", "JSLAM_ERR_TIMEOUT": "ERR_TIMEOUT", "JSLAM_ERR_STATE": "ERR_STATE",
+             "JSLAM_MEM_DEVICE": "MEM_DEVICE", "JSLAM_MEM_HOST": "MEM_HOST"}
+
+
 @pytest.fixture(scope="module")
 def c_layout(tmp_path_factory):
     if shutil.which("gcc") is None:
@@ -30,6 +35,8 @@ def c_layout(tmp_path_factory):
         lines.append(f'  printf("{cname} sizeof %zu\\n", sizeof({cname}));')
         for fname, _ in cls._fields_:
             lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    for name in CONSTANTS:
+        lines.append(f'  printf("const {name} %d\\n", (int){name});')
     lines += ["  return 0;", "}"]
     src, exe = d / "layout.c", d / "layout"
     src.write_text("\n".join(lines) + "\n")
@@ -37,6 +44,11 @@ def c_layout(tmp_path_factory):
                            "-o", str(exe)])
     out = subprocess.check_output([str(exe)], text=True)
     return {(a, b): int(c) for a, b, c in (ln.split() for ln in out.splitlines())}
+
+
+def test_constants_match_the_header(c_layout):
+    for cname, pyname in CONSTANTS.items():
+        assert getattr(jslam, pyname) == c_layout["const", cname], cname
 
 
 @pytest.mark.parametrize("cname,cls", PAIRS, ids=[c for c, _ in PAIRS])
