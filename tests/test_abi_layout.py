@@ -103,3 +103,14 @@ def test_prototypes_match_the_binding():
         assert _ctypes_kind(fn.restype) == rk, (name, fn.restype, ret)
         seen.add(name)
     assert seen == set(jslam.SYMBOLS)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    """No fallback: with the compiled library absent, the first call into the
+    binding raises (and names the build step), in a fresh process state."""
+    monkeypatch.setattr(jslam, "LIB_PATH", str(tmp_path / "libjslam.so"))
+    monkeypatch.setattr(jslam, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        jslam.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        jslam.Frontend(max_width=64, max_height=64, max_feats=10)
