@@ -8,6 +8,7 @@ mutant counts as caught only by a genuine test failure (pytest exit code 1),
 not by a crash or a collection error."""
 import glob
 import os
+import re
 import subprocess
 import sys
 import tempfile
@@ -49,6 +50,7 @@ MUTANTS = [
     ("blur_sigma_sqrt2", "g[i + 3] = exp(-(double)(i * i) / (2.0 * 2.0 * 2.0));",
      "g[i + 3] = exp(-(double)(i * i) / (2.0 * 2.0));", 0),
     ("blur_rounding_to_edge_tap", "w[3] += 256 - total;", "w[0] += 256 - total;", 0),
+    ("clamp_low_to_high", "return v < lo ? lo : (v > hi ? hi : v);", "return v < lo ? hi : (v > hi ? hi : v);", 0),
     ("blur_border_shifted", "acc += (uint32_t)w[i + 3] * in[(size_t)y * pitch_in + clampi(x + i, 0, W - 1)];",
      "acc += (uint32_t)w[i + 3] * in[(size_t)y * pitch_in + clampi(x + i, 1, W - 1)];", 0),
     ("blur_no_rounding", "out[(size_t)y * pitch_out + x] = (uint8_t)((acc + 32768u) >> 16);",
@@ -62,6 +64,7 @@ MUTANTS = [
     # FAST with Bounded Rectification (Sec. II-A, Eq. 1-3)
     ("ring_mirrored", "static const int32_t RING_DY[16] = { 3, 3, 2, 1, 0, -1, -2, -3, -3, -3, -2, -1, 0, 1, 2, 3 };",
      "static const int32_t RING_DY[16] = { -3, -3, -2, -1, 0, 1, 2, 3, 3, 3, 2, 1, 0, -1, -2, -3 };", 0),
+    ("ring_axes_swapped", "dx[k] = RING_DX[k]; dy[k] = RING_DY[k];", "dx[k] = RING_DY[k]; dy[k] = RING_DX[k];", 0),
     ("bright_not_strict", "if (d > eps) Bb |= 1u << k;", "if (d >= eps) Bb |= 1u << k;", 0),
     ("dark_not_strict", "if (d < -eps) Bd |= 1u << k;", "if (d <= -eps) Bd |= 1u << k;", 0),
     ("response_over_arc_only", "r += d < 0 ? -d : d;", "r += (d > eps || d < -eps) ? (d < 0 ? -d : d) : 0;", 0),
@@ -107,6 +110,7 @@ MUTANTS = [
      "if (dx * dx + dy * dy >= OR_DISK_R * OR_DISK_R) continue;", 0),
     ("atan2_arguments_swapped", "*theta = atan2((double)m01, (double)m10);",
      "*theta = atan2((double)m10, (double)m01);", 0),
+    ("sector_tables_swapped", "cosb[b] = cos(phi);\n        sinb[b] = sin(phi);", "cosb[b] = sin(phi);\n        sinb[b] = cos(phi);", 0),
     ("sector_test_sign", "double t = t1 - t2;", "double t = t1 + t2;", 0),
     ("sector_boundary_open", "return t >= 0.0;", "return t > 0.0;", 0),
     # steered BRIEF (Sec. III)
@@ -188,6 +192,7 @@ MUTANTS = [
     ("match_loops_over_left_count", "for (int32_t j = 0; j < Rk->count; ++j) {", "for (int32_t j = 0; j < Lk->count; ++j) {", 0),
     ("match_right_level_from_left", "int32_t nr = Rk->level[j];", "int32_t nr = Lk->level[j];", 0),
     ("match_threshold_exclusive", "} else if (best_d <= p->match_max_dist) {", "} else if (best_d < p->match_max_dist) {", 0),
+    ("popcount_skips_bits", "while (v) { c += (int32_t)(v & 1u); v >>= 1; }", "while (v) { c += (int32_t)(v & 1u); v >>= 2; }", 0),
     ("match_and_instead_of_xor", "d += popcount32(Lk->desc[(size_t)i * 8 + w] ^ Rk->desc[(size_t)j * 8 + w]);",
      "d += popcount32(Lk->desc[(size_t)i * 8 + w] & Rk->desc[(size_t)j * 8 + w]);", 0),
     # correlation minimisation (NEXT-1)
@@ -219,6 +224,9 @@ MUTANTS = [
      "for (int32_t i = 0; i < Rk->count; ++i)\n            if (disp_out[i] >= 0.0f", 0),
     ("negative_disparity_kept", "if (q * den < num) continue;", ";", 0),
     ("median_of_unsorted_sads", "qsort(kept, (size_t)n_kept, sizeof(uint32_t), cmp_u32);", ";", 0),
+    ("median_of_descending_sads", "return x < y ? -1 : (x > y ? 1 : 0);", "return x > y ? -1 : (x < y ? 1 : 0);", 0),
+    ("subpixel_levels_one_scale_short", "or_pyramid_level(L0, W0, H0, pitch0, p->scale, n, lev[n], Wn[n], Hn[n], Wn[n]);",
+     "or_pyramid_level(L0, W0, H0, pitch0, p->scale, n - 1, lev[n], Wn[n], Hn[n], Wn[n]);", 0),
     ("subpixel_last_minimum", "if (acc < sad[best]) best = t + L;", "if (acc <= sad[best]) best = t + L;", 0),
     ("subpixel_parabola_sign", "int64_t num = d1 - d3, den = 2 * (d1 + d3 - 2 * d2);",
      "int64_t num = d3 - d1, den = 2 * (d1 + d3 - 2 * d2);", 0),
@@ -349,3 +357,28 @@ def test_listed_equivalent_mutants_change_no_output():
             assert r.returncode == 0, r.stderr[-1500:]
             out[name] = r.stdout.strip()
     assert all(v == out["unmutated"] for v in out.values()), out
+
+
+def _functions(text):
+    """(name, start, end) of every function defined at column 0."""
+    out = []
+    for m in re.finditer(r"^(?=[A-Za-z_])[\w \*]*?\b(\w+)\s*\([^;{}]*\)\s*\{", text, flags=re.M):
+        out.append((m.group(1), m.start(), text.find("\n}\n", m.end())))
+    return out
+
+
+def test_every_oracle_function_hosts_a_mutant():
+    """Each function of the oracle carries at least one named mutant, so that a
+    function added later without pins that catch a mistake in it is noticed."""
+    text = open(SRC).read()
+    funcs = _functions(text)
+    assert len(funcs) > 30
+    hosted = {name: 0 for name, _, _ in funcs}
+    for _, old, _, occ in MUTANTS:
+        at = -1
+        for _ in range(occ + 1):
+            at = text.find(old, at + 1)
+        for name, a, b in funcs:
+            if a <= at < b:
+                hosted[name] += 1
+    assert not [n for n, c in hosted.items() if c == 0], hosted
