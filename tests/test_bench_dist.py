@@ -69,3 +69,13 @@ def test_reference_arm_runs_on_rank_zero_only():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["value"] > 0
+    # the rest of the line's contract: the same metric, unit and direction as our arm
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT == d["e2e"]["unit"]
+    assert (d["steps"], d["warmup"], d["higher_is_better"], d["scaling"]) == (1, 0, True, "weak")
+    assert d["vs_baseline"] is None and d["data"] == "synthetic" and d["ms_per_step"] > 0
+    assert d["config"]["workload"].startswith("single_640x480_L1")
+    cb = d["cpu_baseline"]
+    assert cb["value"] == d["value"] == d["e2e"]["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"]["d2h_bytes_per_step"] == 0
