@@ -52,3 +52,42 @@ def test_code_hash_ignores_comments_and_whitespace(tmp_path):
     assert bench.code_hash(str(a)) == bench.code_hash(str(b))
     b.write_text("int f(int x) { return x + 2; }\n")
     assert bench.code_hash(str(a)) != bench.code_hash(str(b))
+
+
+def test_emitted_line_carries_the_contract(monkeypatch, capsys):
+    """Our arm's JSON line, emitted on the CPU from synthetic stage times with
+    the committed ncu summaries: every contract key, the integer-issue
+    roofline of the dominant stage with its instruction count and DRAM
+    traffic taken from the summary, the HBM view beside it, and the launch
+    count of the timed mode."""
+    import json
+    import types
+    import bench
+    monkeypatch.setattr(bench, "alu_peak", lambda dev: (40.3e12, 152, 2070.0))
+    args = types.SimpleNamespace(steps=50, warmup=3, workload="kitti_1241x376_L8", mode="graph_streams4",
+                                 no_cpu_baseline=True)
+    pairs, params, lo = bench.make_workload(args.workload, 2)
+    stage = {"pyramid": 0.774, "skip": 0.0, "detect": 0.865, "pfa_nms": 0.048, "pfa_final": 0.066, "orb": 0.259,
+             "match": 0.172}
+    clocks = types.SimpleNamespace(summary=lambda: {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []})
+    e2e = {"value": 43000.0, "unit": bench.UNIT, "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1}
+    bench.emit(args, 1, len(pairs), 47800.0, 2.09 * 50, {"graph_streams4": 47800.0},
+               {k: v * 50 for k, v in stage.items()}, [2000] * 4, pairs, params, lo, e2e, clocks, (128, 128),
+               None, 0)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "clocks",
+                "gpu_launches"):
+        assert key in line, key
+    assert line["config"]["workload"].startswith("kitti_1241x376_L8")
+    assert line["gpu_launches"] == 4 * bench.LAUNCHES_PER_CALL * 50
+    roof = line["roofline"]
+    prof = bench.profile_summary("k_fast_bits", "kitti_1241x376_L8")
+    assert prof is not None and roof["bound"] == "alu" and roof["kernel"] == "k_fast_bits"
+    lane_ops = bench.profile_number(prof, "inst_executed_warp_per_launch") * 32
+    assert roof["inst_per_launch"] == lane_ops
+    assert abs(roof["achieved"] - lane_ops / 0.865e-3) < 1e-6 * roof["achieved"]
+    assert abs(roof["frac"] - roof["achieved"] / 40.3e12) < 1e-12
+    assert roof["traffic"] == bench.profile_number(prof, "dram_bytes_per_launch_full_workload")
+    assert roof["hbm"]["algorithmic_bytes_per_launch"] == bench.algorithmic_bytes("detect", pairs, params, [1])
+    assert line["path_hbm"]["frac"] > 0 and line["cpu_baseline"] is None
