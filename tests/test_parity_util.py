@@ -93,3 +93,23 @@ def test_match_fields_fail(ref):
     got["count"] = n - 1
     with pytest.raises(AssertionError):
         compare_matches(got, (idx, disp, dist))
+
+
+def test_smoke_comparison_accepts_the_oracle_and_rejects_a_change(oracle):
+    """The comparison smoke() applies on the GPU: an oracle result passes it
+    (angles compared on the circle), a one-bit change does not."""
+    import __graft_entry__ as G
+    pair = scenes.planes_pair(320, 240, 0, 11, 12)
+    p = params_from(oracle, levels=4, max_feats=400, fast_thresh_lo=7)
+    ol, orr, _ = oracle.extract_pair(pair.left, pair.right, p)
+    for want in (ol, orr):
+        got = _as_gpu(want)
+        G._same_keypoints(got, want, "copy")
+        wrapped = copy.deepcopy(want)
+        wrapped["angle"][0] = np.float32(np.pi - 2e-5)
+        g2 = _as_gpu(wrapped)
+        g2["angle"][0] = np.float32(-np.pi + 2e-5)   # 4e-5 apart on the circle
+        G._same_keypoints(g2, wrapped, "wrap")
+        got["desc"][want["count"] - 1, 0] ^= np.uint32(1)
+        with pytest.raises(AssertionError):
+            G._same_keypoints(got, want, "changed")
