@@ -182,7 +182,8 @@ jslam_status jslam_track(jslam_ctx *ctx, int32_t pair, int32_t side, const float
 jslam_status jslam_fc_ablation(jslam_ctx *ctx, int32_t n_max);
 
 /* Device views of one level's per-cell keys (cells_y x cells_x, row-major)
- * from the ablation and from the fused detection kernel. */
+ * from the ablation and from the fused detection kernel: each cell's
+ * Feature Culling result (Sec. II-C-1), computed both ways. */
 jslam_status jslam_fc_ablation_view(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t level,
                                     const uint32_t **ablation_keys, const uint32_t **fused_keys,
                                     int32_t *cells_x, int32_t *cells_y);
@@ -209,7 +210,8 @@ jslam_status jslam_crf_view(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t 
                             int32_t *width, int32_t *height);
 
 /* Milliseconds of the ablation's CRF-matrix kernel and of its culling
- * kernels (after jslam_sync). */
+ * kernels (after jslam_sync); the per-stage kernel times the paper reports
+ * for Feature Culling (Sec. IV-B) are measured this way. */
 jslam_status jslam_fc_ablation_times(jslam_ctx *ctx, float *crf_ms, float *fc_ms);
 
 /* Views of one pair's refinement, one entry per left keypoint. */
@@ -220,10 +222,12 @@ typedef struct {
     const uint32_t *sad;          /* SAD at the best shift; 0xFFFFFFFF when none was computed */
 } jslam_refined;
 
-/* Device views of pair `pair`'s refinement (after jslam_refine_matches). */
+/* Device views of pair `pair`'s refinement (after jslam_refine_matches):
+ * the correlation-minimisation outputs of the middle-end (Sec. III). */
 jslam_status jslam_get_refined(jslam_ctx *ctx, int32_t pair, jslam_refined *out);
 
-/* Host views of the refinement inside a downloaded result block of pair `pair`. */
+/* Host views of the refinement (Sec. III, middle-end correlation
+ * minimisation) inside a downloaded result block of pair `pair`. */
 jslam_status jslam_result_refined_view(jslam_ctx *ctx, int32_t pair, const void *block, jslam_refined *out);
 
 /* Device views of one pyramid level of one image (for consumers that share
@@ -237,62 +241,94 @@ typedef struct {
 
 /* Fill `cfg` with the defaults (device 0, NULL stream, 1920x1080, 8 levels,
  * 4000 features, 64 pairs, P_min 9, P_max 13, k 1, q 3, border 19,
- * max_disp 128, band 2, distance 100, fallback off, dominance rule). */
+ * max_disp 128, band 2, distance 100, fallback off, dominance rule).  The
+ * paper fixes P_min, P_max (Sec. II-A, Eq. 3), one corner per cell
+ * (Sec. II-C-1) and the 3x3 PFA window (Sec. II-C-2); the other values are
+ * this library's readings of points the paper leaves open. */
 void jslam_default_config(jslam_config *cfg);
 
 /* Create a context on cfg->device.  Validates the configuration
  * (JSLAM_ERR_ARG), uploads the constant tables (ring, blur weights, angle
  * sectors, rotated BRIEF pattern) and creates the stream if none is given.
+ * The context's grow-only device buffers play the part of the paper's
+ * Synchronized Shared Memory (Sec. III): frames, levels and keypoints stay
+ * on the GPU between stages.  The ring and the corner rule are those of
+ * Sec. II-A (Eq. 1-3).
  * On success *out owns the context; release it with jslam_destroy. */
 jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg);
 
-/* Enqueue the frontend for one stereo pair: pyramid, blur, FAST with Bounded
- * Rectification, per-cell culling, PFA, keypoint cap, orientation and
- * descriptors for both images.  Arguments as in jslam_stereo_job.
- * JSLAM_ERR_ARG: null context, bad image (null data, pitch < width, size
- * above the configured maximum), levels out of range, scale <= 1,
- * threshold or cell out of range, or a level smaller than 2*border+1. */
+/* Enqueue the frontend for one stereo pair: pyramid and Gaussian filter
+ * (Sec. III, streamlined multiscale detection and extraction), FAST with
+ * Bounded Rectification (Sec. II-A, Eq. 1-3; Sec. III, efficient FAST
+ * detection: bit masks and the sum-of-absolute-differences response),
+ * per-cell culling (Sec. II-C-1, Feature Culling), Pyramidal Feature
+ * Aggregation (Sec. II-C-2), keypoint cap, orientation and descriptors
+ * (Sec. III, ORB for all scales at once) for both images.  Arguments as in
+ * jslam_stereo_job.  JSLAM_ERR_ARG: null context, bad image (null data,
+ * pitch < width, size above the configured maximum), levels out of range,
+ * scale <= 1, threshold or cell out of range, or a level smaller than
+ * 2*border+1. */
 jslam_status jslam_extract(jslam_ctx *ctx, jslam_image left, jslam_image right,
                            int32_t levels, float scale, int32_t fast_thresh,
                            int32_t cell, int32_t max_feats);
 
 /* Enqueue the frontend for n stereo pairs (1 <= n <= config.max_pairs) of
- * possibly different sizes and depths in one set of launches.  Results of
- * pair i are read with pair index i. */
+ * possibly different sizes and depths in one set of launches: the steps of
+ * jslam_extract (Sec. II-A, II-C-1, II-C-2, III) for every image at once.
+ * Batching many streams is this library's own addition (no counterpart in
+ * the paper, which runs one camera).  Results of pair i are read with pair
+ * index i. */
 jslam_status jslam_extract_batch(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n);
 
-/* Enqueue stereo row matching (descriptor-distance minimisation) for every
- * pair of the last extraction.  JSLAM_ERR_STATE before any extraction. */
+/* Enqueue stereo row matching for every pair of the last extraction: the
+ * middle-end's descriptor-distance minimisation along rectified rows
+ * (Sec. III, Middle-end; the paper names the step, the search band and
+ * tie-break are readings).  Results are read with jslam_get_matches (one
+ * call enqueues, a second reads, instead of one call filling a struct).
+ * JSLAM_ERR_STATE before any extraction. */
 jslam_status jslam_match(jslam_ctx *ctx);
 
 /* Wait for the context stream, copy counts to the host and surface any
- * device-side error flag.  Returns the context's sticky status. */
+ * device-side error flag.  Returns the context's sticky status.  The
+ * paper's Synchronized Shared Memory (Sec. III) synchronises host and
+ * device views of the frontend's data; here this is the one point where the
+ * host waits for the device. */
 jslam_status jslam_sync(jslam_ctx *ctx);
 
 /* Keypoint views of `side` (0 = left, 1 = right) of pair `pair` of the last
- * extraction.  JSLAM_ERR_ARG for an out-of-range pair or side. */
+ * extraction: the keypoints kept by Pyramidal Feature Aggregation
+ * (Sec. II-C-2) with their K_l, K_r scores, FAST response (Sec. II-A) and
+ * ORB angle and descriptor (Sec. III).  The `pair` argument selects one
+ * pair of a batch.  JSLAM_ERR_ARG for an out-of-range pair or side. */
 jslam_status jslam_get_keypoints(jslam_ctx *ctx, int32_t pair, int32_t side, jslam_keypoints *out);
 
-/* Match views of pair `pair` (valid after jslam_match). */
+/* Match views of pair `pair` (valid after jslam_match): the stereo matches
+ * of the middle-end (Sec. III). */
 jslam_status jslam_get_matches(jslam_ctx *ctx, int32_t pair, jslam_matches *out);
 
-/* Level views of `side` of pair `pair` (valid after extraction). */
+/* Level views of `side` of pair `pair` (valid after extraction): the
+ * pyramid of Sec. III, shared with the middle-end as the paper's
+ * Synchronized Shared Memory shares frames. */
 jslam_status jslam_get_level(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t level,
                              jslam_level_view *out);
 
 /* Size in bytes of pair `pair`'s result block: both images' keypoints at
- * capacity, the matches and a 16-byte header of counts. */
+ * capacity, the matches and a 16-byte header of counts.  Result blocks and
+ * their download are this library's transport (no counterpart in the
+ * paper). */
 jslam_status jslam_result_bytes(jslam_ctx *ctx, int32_t pair, size_t *bytes);
 
 /* Enqueue an asynchronous copy of pair `pair`'s result block into host
  * memory `dst` of at least jslam_result_bytes bytes (pinned memory keeps it
  * asynchronous).  After jslam_sync the block can be read with
- * jslam_result_view. */
+ * jslam_result_view.  The keypoint download that the paper's throughput
+ * figures include (Sec. IV-C). */
 jslam_status jslam_download(jslam_ctx *ctx, int32_t pair, void *dst, size_t bytes);
 
 /* The result blocks of pairs [first, first + count) lie back to back in
  * device memory: their total size in *bytes and, if `offsets` is not NULL,
- * pair first + i's block at offsets[i] (count entries) from the first.
+ * pair first + i's block at offsets[i] (count entries) from the first
+ * (transport; no counterpart in the paper).
  * JSLAM_ERR_ARG for an empty or out-of-range span, JSLAM_ERR_STATE before
  * the first extraction. */
 jslam_status jslam_result_range(jslam_ctx *ctx, int32_t first, int32_t count, size_t *bytes, size_t *offsets);
@@ -300,12 +336,14 @@ jslam_status jslam_result_range(jslam_ctx *ctx, int32_t first, int32_t count, si
 /* Enqueue ONE asynchronous copy of the result blocks of pairs [first,
  * first + count) into host memory `dst` of at least the jslam_result_range
  * bytes; pair first + i's block is then at dst + offsets[i], readable with
- * jslam_result_view after jslam_sync. */
+ * jslam_result_view after jslam_sync (the keypoint download of Sec. IV-C,
+ * for a whole batch). */
 jslam_status jslam_download_range(jslam_ctx *ctx, int32_t first, int32_t count, void *dst, size_t bytes);
 
 /* Interpret a downloaded result block: fill host views of `side` (0 or 1)
  * into *kp and, for side 0, the matches into *m (may be NULL).  Pure host
- * function; `block` must hold jslam_result_bytes bytes of pair `pair`. */
+ * function; `block` must hold jslam_result_bytes bytes of pair `pair`
+ * (transport; no counterpart in the paper). */
 jslam_status jslam_result_view(jslam_ctx *ctx, int32_t pair, const void *block, int32_t side,
                                jslam_keypoints *kp, jslam_matches *m);
 
@@ -324,12 +362,14 @@ enum {
 
 /* Turn per-stage timing on or off.  When on, every extraction and match
  * records a CUDA event on the context stream after each stage (a small
- * overhead per stage). */
+ * overhead per stage).  Per-stage times as the paper reports them for CRF,
+ * FC and PFA (Sec. IV-B, IV-C). */
 jslam_status jslam_enable_stage_timing(jslam_ctx *ctx, int32_t enable);
 
 /* Device durations in milliseconds of each stage of the last extraction
- * (and match, if one followed it), measured between the recorded events.
- * Valid after jslam_sync(); JSLAM_ERR_STATE if timing was off. */
+ * (and match, if one followed it), measured between the recorded events
+ * (the stage timings of Sec. IV-B, IV-C).  Valid after jslam_sync();
+ * JSLAM_ERR_STATE if timing was off. */
 jslam_status jslam_stage_times(jslam_ctx *ctx, float *ms /* JSLAM_NUM_STAGES entries */);
 
 /* Launch-shape tuning: the target detection tile in pixels (whole culling
@@ -340,18 +380,23 @@ typedef struct {
 } jslam_tuning;
 
 /* Use `t` for the following extractions (plans are rebuilt on change).
+ * Launch-shape tuning has no counterpart in the paper (its MLPT / TEWA
+ * thread allocation, Sec. II-C-1, is fixed per cell size).
  * JSLAM_ERR_ARG for values outside the ranges above. */
 jslam_status jslam_set_tuning(jslam_ctx *ctx, const jslam_tuning *t);
 
 /* Time the detection stage of the batch `jobs` (n pairs, as for
  * jslam_extract_batch) under a set of candidate tile shapes with the stage
  * events, keep the fastest for the context and return it in *out (may be
- * NULL).  Runs the batch several times; results are unaffected. */
+ * NULL).  Runs the batch several times; results are unaffected.  No
+ * counterpart in the paper (an autotuner in place of the fixed thread
+ * allocation of Sec. II-C-1). */
 jslam_status jslam_autotune(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n, jslam_tuning *out);
 
 /* Capture extraction + matching of the batch `jobs` into a CUDA graph owned
  * by the context (the batch runs once uncaptured first, so that the plan
- * and buffers exist).  Replays read the same input buffers: device images
+ * and buffers exist); no counterpart in the paper, which launches per
+ * scale on streams (Sec. III).  Replays read the same input buffers: device images
  * in place, host images (which must then be pinned) copied again.  The
  * context stream must not be the legacy default stream.  Replaces any
  * earlier graph. */
@@ -359,11 +404,12 @@ jslam_status jslam_graph_capture(jslam_ctx *ctx, const jslam_stereo_job *jobs, i
 
 /* Enqueue one replay of the captured graph on the context stream; results
  * are read as after jslam_extract_batch + jslam_match.  JSLAM_ERR_STATE if
- * nothing was captured. */
+ * nothing was captured.  No counterpart in the paper. */
 jslam_status jslam_graph_launch(jslam_ctx *ctx);
 
 /* PFA scores of one image's culled corners, computed without allocating
- * device memory.  No counterpart in the paper: it exists for callers that
+ * device memory.  The allocation-free variant itself has no counterpart in
+ * the paper (the scores are those of Sec. II-C-2): it exists for callers that
  * cannot call cudaMalloc -- a real-time loop that forbids allocation after
  * start-up, a plug-in running inside another framework's enqueue hook, a
  * process whose device memory comes from a fixed pool.
@@ -396,7 +442,7 @@ jslam_status jslam_pfa_scores_static(const uint8_t *level, const uint16_t *x, co
                                      uint8_t *alive, int32_t device, void *cuda_stream);
 
 /* Learned cell-skip proposal (opt-in, approximate; no counterpart in the
- * paper).  `blob` holds a versioned model: the 16-byte header
+ * paper: it proposes which Feature Culling cells of Sec. II-C-1 to skip).  `blob` holds a versioned model: the 16-byte header
  * {"JSKP", version 1, channels 16, downsample 8} (little-endian uint32
  * fields after the 4 magic bytes), then FP32 biases b1[16], b2[16], b3[1],
  * then BF16 weights w1[16][1][3][3], w2[16][16][3][3], w3[1][16][3][3] of
@@ -409,7 +455,8 @@ jslam_status jslam_set_skip_model(jslam_ctx *ctx, const void *blob, size_t bytes
 
 /* Device views of the skip proposal of `side` of pair `pair` (after an
  * extraction in skip mode): the 1/8-scale logits (h8 x w8 floats) and the
- * per-cell skip flags (cells_y x cells_x bytes, 1 = skipped). */
+ * per-cell skip flags (cells_y x cells_x bytes, 1 = skipped).  No
+ * counterpart in the paper. */
 typedef struct {
     int32_t w8, h8, cells_x, cells_y;
     const float *logits;
@@ -417,25 +464,32 @@ typedef struct {
 } jslam_skip_view;
 jslam_status jslam_get_skip_view(jslam_ctx *ctx, int32_t pair, int32_t side, jslam_skip_view *out);
 
-/* Release the context and everything it owns.  NULL is ignored. */
+/* Release the context and everything it owns (the device buffers that
+ * stand for the Synchronized Shared Memory of Sec. III).  NULL is ignored. */
 void jslam_destroy(jslam_ctx *ctx);
 
-/* Static description of a status code. */
+/* Static description of a status code (error reporting; no counterpart in
+ * the paper). */
 const char *jslam_status_str(jslam_status s);
 
 /* ---- host-side tables (no device work; usable without a GPU) ---- */
 
 /* The 256-pair steered BRIEF pattern rotated to each of the 30 angle
  * sectors: out[(b * 256 + i) * 4 + {0,1,2,3}] = (px, py, qx, qy) of pair i
- * in sector b.  `out` holds 30 * 256 * 4 bytes. */
+ * in sector b.  `out` holds 30 * 256 * 4 bytes.  The descriptor of the
+ * ORB extraction of Sec. III; the pattern is this library's own seeded
+ * draw, not ORB's learned one. */
 void jslam_pattern_table(int8_t *out);
 
 /* Level geometry of an image: width, height and culling cell size of each
- * of `levels` levels for scale factor `scale` and s0 cell `cell`. */
+ * of `levels` levels for scale factor `scale` and s0 cell `cell` (the
+ * pyramid of Sec. III; the cell shrinks with the level as Sec. IV-F states,
+ * 32 x 32 at s0 to 8 x 8 at the eighth scale). */
 jslam_status jslam_level_geometry(int32_t width, int32_t height, int32_t levels, float scale,
                                   int32_t cell, int32_t *w, int32_t *h, int32_t *c);
 
-/* Projection of level-n coordinate v to s0 (clamped to extent-1). */
+/* Projection of level-n coordinate v to s0 (clamped to extent-1): step 1
+ * of Pyramidal Feature Aggregation (Sec. II-C-2), rounded to nearest. */
 int32_t jslam_project(int32_t v, int32_t level, float scale, int32_t extent);
 
 /* Corner look-up table of Sec. III for Eq. 3: bit m of out[m / 32] (bit
@@ -443,7 +497,8 @@ int32_t jslam_project(int32_t v, int32_t level, float scale, int32_t extent);
  * set bits in [p_min, p_max].  `out` holds 2048 words. */
 jslam_status jslam_corner_table(int32_t p_min, int32_t p_max, uint32_t *out);
 
-/* Stereo row band at level n: ceil(row_band_px * zeta^n). */
+/* Stereo row band at level n: ceil(row_band_px * zeta^n), the search band
+ * of the middle-end's stereo matching (Sec. III). */
 int32_t jslam_match_band(int32_t level, float scale, int32_t row_band_px);
 
 #ifdef __cplusplus

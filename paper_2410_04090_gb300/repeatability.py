@@ -2,7 +2,7 @@
 
 The paper measures corner quality on synthetic images with known corners,
 rotated through the full circle, as the F1 score of the detected corners,
-Bounded Rectification against plain FAST (Sec. V-A and its repeatability
+Bounded Rectification against plain FAST (Sec. IV-A and its repeatability
 figure).  This module runs that study on the library:
 
 * scenes: ``scenes.corner_scene`` -- convex polygons with labeled vertices,

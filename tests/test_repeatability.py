@@ -1,6 +1,6 @@
 """Host side of the Bounded Rectification repeatability study: the F1 score,
 the labeled rotated scenes, and the study run on the oracle's corner sets
-(Sec. V-A, repeatability figure)."""
+(Sec. IV-A, repeatability figure)."""
 import numpy as np
 import pytest
 
