@@ -415,24 +415,31 @@ jslam_status jslam_graph_launch(jslam_ctx *ctx);
  * process whose device memory comes from a fixed pool.
  *
  * For the n corners (level[i], x[i], y[i], response[i]) (device arrays, level
- * coordinates, distinct (level, x, y), level < levels, response <= 4080) it
- * writes, per corner, its s0 projection X[i], Y[i], the number of levels
- * k_levels[i] and summed response k_resp[i] at that s0 pixel, and alive[i] =
- * 1 when no occupied pixel of the nms_q x nms_q window dominates it (pfa_rule
- * as in jslam_config) -- the k_levels / k_resp that jslam_extract reports for
- * the corners it keeps.  Outputs are device arrays of n entries, owned by the
- * caller.  Runs asynchronously on `cuda_stream` (NULL: legacy default stream)
- * of `device`; the calling thread's current device is restored on return.
+ * coordinates) it writes, per corner, its s0 projection X[i], Y[i], the
+ * number of levels k_levels[i] and summed response k_resp[i] at that s0
+ * pixel, and alive[i] = 1 when no occupied pixel of the nms_q x nms_q window
+ * dominates it, 0 when one does (pfa_rule as in jslam_config) -- the
+ * k_levels / k_resp that jslam_extract reports for the corners it keeps.
+ * A corner outside the domain -- level[i] >= levels, response[i] > 4080 (the
+ * largest sum of 16 differences of 8-bit pixels), or a repeat of an earlier
+ * (level, x, y) of the list -- takes no part in the scores and gets alive[i]
+ * = 2, X = Y = 0xFFFF, k_levels = k_resp = 0 (of repeated corners, one is
+ * scored and the others are marked, whichever the GPU reaches first).
+ * Outputs are device arrays of n entries, owned by the caller.  Runs
+ * asynchronously on `cuda_stream` (NULL: legacy default stream) of
+ * `device`; the calling thread's current device is restored on return.
  *
  * Scratch: a 256 KB table in a statically allocated device array that every
  * GPU loading the library holds until the process exits.  Every call clears
  * and reuses it, so calls whose work overlaps on a GPU race and give wrong
  * results: serialise them (one stream, or events).  The first call on a
  * device looks up the table's device address; make that first call before
- * any stream capture.  Nothing is allocated, ever.
+ * any stream capture.  The address is kept for the life of the process, so
+ * after cudaDeviceReset the entry point must not be called on that device
+ * again.  Nothing is allocated, ever.
  *
- * JSLAM_ERR_CAPACITY when n > 16384; JSLAM_ERR_ARG for a null array with
- * n > 0, a size outside 1..4096, levels outside 1..8, scale outside the open
+ * JSLAM_ERR_CAPACITY when n > 16384; JSLAM_ERR_ARG for n < 0, a null array
+ * with n > 0, a size outside 1..4096, levels outside 1..8, scale outside the open
  * interval (1, 16), nms_q not odd in 1..7, a bad rule or device; JSLAM_ERR_CUDA if the table's address
  * or the launch fails.  n == 0 returns JSLAM_OK without work. */
 jslam_status jslam_pfa_scores_static(const uint8_t *level, const uint16_t *x, const uint16_t *y,

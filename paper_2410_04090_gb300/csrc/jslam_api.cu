@@ -6,6 +6,7 @@
 #include <vector>
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "jslam.h"
 #include "jslam_internal.h"
@@ -18,6 +19,19 @@ int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, int max_plane
 using namespace jslam;
 
 namespace {
+
+// Host-side NVTX range around each stage's launch, named by stage, so that a
+// profiler's timeline shows which launch belongs to which step of the path.
+// With no profiler attached the push and pop are no-ops.
+const char *const kStageNames[JSLAM_NUM_STAGES] = { "jslam pyramid", "jslam skip proposal", "jslam detect",
+                                                     "jslam PFA NMS",  "jslam PFA final",     "jslam ORB",
+                                                     "jslam match",    "jslam refine" };
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -824,6 +838,7 @@ jslam_status jslam_extract_batch(jslam_ctx *ctx, const jslam_stereo_job *jobs, i
     for (bool &d : ctx->stage_done) d = false;
     if (ctx->timing && (e = cudaEventRecord(ctx->events[0], ctx->stream)) != cudaSuccess) return fail(ctx, e);
     for (int i = 0; i < JSLAM_STAGE_MATCH; ++i) {
+        const NvtxRange range(kStageNames[i]);
         switch (i) {
         case JSLAM_STAGE_PYRAMID: e = launch_pyramid(b, ctx->stream); break;
         case JSLAM_STAGE_SKIP:
@@ -863,7 +878,11 @@ jslam_status jslam_match(jslam_ctx *ctx)
     if (!ctx->have_extract) return JSLAM_ERR_STATE;
     jslam_status st = use_device(ctx);
     if (st != JSLAM_OK) return st;
-    cudaError_t e = launch_match(ctx->batch, ctx->stream);
+    cudaError_t e;
+    {
+        const NvtxRange range(kStageNames[JSLAM_STAGE_MATCH]);
+        e = launch_match(ctx->batch, ctx->stream);
+    }
     if (e != cudaSuccess) return fail(ctx, e);
     if (ctx->timing && ctx->stage_done[JSLAM_STAGE_ORB]) {
         if ((e = cudaEventRecord(ctx->events[JSLAM_STAGE_MATCH + 1], ctx->stream)) != cudaSuccess) return fail(ctx, e);
@@ -883,7 +902,11 @@ jslam_status jslam_refine_matches(jslam_ctx *ctx, int32_t half_window, int32_t s
     if (!ctx->have_match) return JSLAM_ERR_STATE;
     jslam_status st = use_device(ctx);
     if (st != JSLAM_OK) return st;
-    cudaError_t e = launch_refine(ctx->batch, half_window, search, (double)bf, ctx->stream);
+    cudaError_t e;
+    {
+        const NvtxRange range(kStageNames[JSLAM_STAGE_REFINE]);
+        e = launch_refine(ctx->batch, half_window, search, (double)bf, ctx->stream);
+    }
     if (e != cudaSuccess) return fail(ctx, e);
     if (ctx->timing && ctx->stage_done[JSLAM_STAGE_MATCH]) {
         if ((e = cudaEventRecord(ctx->events[JSLAM_STAGE_REFINE + 1], ctx->stream)) != cudaSuccess) return fail(ctx, e);
@@ -915,6 +938,7 @@ jslam_status jslam_track(jslam_ctx *ctx, int32_t pair, int32_t side, const float
     for (int l = 0; l < kMaxLevels; ++l) a.zeta_f[l] = static_cast<float>(zeta_pow(ctx->pair_scale[pair], l));
     a.u = u; a.v = v; a.level = level; a.desc = desc;
     a.out_idx = out_idx; a.out_dist = out_dist;
+    const NvtxRange range("jslam track");
     return fail(ctx, launch_track(ctx->batch, a, ctx->stream));
 }
 

@@ -29,7 +29,7 @@ constexpr int kStaticThreads = 1024;
 
 struct StaticPfaScratch {
     uint32_t key[kStaticSlots];  // s0 pixel index + 1; 0 = empty
-    uint32_t val[kStaticSlots];  // K_l << 16 | K_r
+    uint32_t val[kStaticSlots];  // mask of the levels seen << 16 | K_r (K_l = bits of the mask)
 };
 
 // 256 KB of device memory per GPU, reserved when the library is loaded.
@@ -73,11 +73,26 @@ __device__ __forceinline__ int project_s0(int v, double s, int extent)
     return p < extent - 1 ? p : extent - 1;
 }
 
+// Outputs of a corner that takes no part in the scores: a level outside the
+// image's pyramid, a response above the largest SAD (16 x 255), or a repeat
+// of a corner already counted.
+__device__ __forceinline__ void reject(int i, uint16_t *Xo, uint16_t *Yo, uint8_t *k_levels, uint32_t *k_resp,
+                                       uint8_t *alive)
+{
+    Xo[i] = 0xFFFFu;
+    Yo[i] = 0xFFFFu;
+    k_levels[i] = 0;
+    k_resp[i] = 0u;
+    alive[i] = 2;
+}
+
 // One CTA: clear, accumulate (K_l, K_r) per s0 pixel, then the NMS test.
+// Each thread handles the same corners i in both phases, so the rejections it
+// writes in the first are its own to read in the second.
 __global__ void __launch_bounds__(kStaticThreads)
 k_pfa_scores_static(StaticPfaScratch *t, const uint8_t *level, const uint16_t *x, const uint16_t *y,
-                    const uint16_t *response, int n, int W0, int H0, LevelScales sc, int rad, int rule,
-                    uint16_t *Xo, uint16_t *Yo, uint8_t *k_levels, uint32_t *k_resp, uint8_t *alive)
+                    const uint16_t *response, int n, int W0, int H0, int levels, LevelScales sc, int rad,
+                    int rule, uint16_t *Xo, uint16_t *Yo, uint8_t *k_levels, uint32_t *k_resp, uint8_t *alive)
 {
     for (int i = threadIdx.x; i < kStaticSlots; i += kStaticThreads) {
         t->key[i] = 0u;
@@ -85,18 +100,26 @@ k_pfa_scores_static(StaticPfaScratch *t, const uint8_t *level, const uint16_t *x
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += kStaticThreads) {
-        const int l = min((int)level[i], kMaxLevels - 1);
+        const int l = level[i];
+        const uint32_t r = response[i];
+        if (l >= levels || r > 16u * 255u) { reject(i, Xo, Yo, k_levels, k_resp, alive); continue; }
         const int X = project_s0(x[i], sc.s[l], W0), Y = project_s0(y[i], sc.s[l], H0);
+        const int h = table_insert(t, (uint32_t)(Y * W0 + X) + 1u);
+        // distinct pixels of one level project to distinct s0 pixels (zeta^n
+        // >= 1), so a level already in this pixel's mask is a repeated corner
+        const uint32_t bit = 1u << (16 + l);
+        if (h < 0 || (atomicOr(&t->val[h], bit) & bit)) { reject(i, Xo, Yo, k_levels, k_resp, alive); continue; }
+        atomicAdd(&t->val[h], r);  // at most 8 x 4080 < 2^16: never reaches the mask
         Xo[i] = (uint16_t)X;
         Yo[i] = (uint16_t)Y;
-        const int h = table_insert(t, (uint32_t)(Y * W0 + X) + 1u);
-        if (h >= 0) atomicAdd(&t->val[h], (1u << 16) + response[i]);
+        alive[i] = 1;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += kStaticThreads) {
+        if (alive[i] == 2) continue;
         const int X = Xo[i], Y = Yo[i];
         const uint32_t own = table_value(t, (uint32_t)(Y * W0 + X) + 1u);
-        const uint32_t kl = own >> 16, kr = own & 0xFFFFu;
+        const uint32_t kl = __popc(own >> 16), kr = own & 0xFFFFu;
         bool dom = false;
         for (int dy = -rad; dy <= rad; ++dy) {
             const int qy = Y + dy;
@@ -106,7 +129,7 @@ k_pfa_scores_static(StaticPfaScratch *t, const uint8_t *level, const uint16_t *x
                 if ((dx | dy) == 0 || qx < 0 || qx >= W0) continue;
                 const uint32_t w = table_value(t, (uint32_t)(qy * W0 + qx) + 1u);
                 if (!w) continue;
-                const uint32_t ql = w >> 16, qr = w & 0xFFFFu;
+                const uint32_t ql = __popc(w >> 16), qr = w & 0xFFFFu;
                 dom |= rule == 0 ? (ql > kl && qr > kr) : (ql > kl || (ql == kl && qr > kr));
             }
         }
@@ -123,7 +146,10 @@ std::mutex g_setup_mutex;
 StaticPfaScratch *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the static table on `device` (which must be current).
-// Looked up once per device; later calls reuse it.
+// Looked up once per device; later calls reuse it.  The address belongs to
+// the device's primary context: after cudaDeviceReset the cached value is
+// stale, so a process that resets a device must not call the entry point on
+// it again.
 cudaError_t scratch_on(int device, StaticPfaScratch **out)
 {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
@@ -149,7 +175,8 @@ extern "C" jslam_status jslam_pfa_scores_static(const uint8_t *level, const uint
                                                 uint32_t *k_resp, uint8_t *alive, int32_t device,
                                                 void *cuda_stream)
 {
-    if (n < 0 || n > kStaticMaxCandidates) return JSLAM_ERR_CAPACITY;
+    if (n < 0) return JSLAM_ERR_ARG;
+    if (n > kStaticMaxCandidates) return JSLAM_ERR_CAPACITY;
     if (width0 < 1 || width0 > 4096 || height0 < 1 || height0 > 4096) return JSLAM_ERR_ARG;
     if (levels < 1 || levels > kMaxLevels || !(scale > 1.0f) || !(scale < 16.0f)) return JSLAM_ERR_ARG;
     if (nms_q < 1 || nms_q > 7 || (nms_q & 1) == 0 || pfa_rule < 0 || pfa_rule > 1) return JSLAM_ERR_ARG;
@@ -167,8 +194,8 @@ extern "C" jslam_status jslam_pfa_scores_static(const uint8_t *level, const uint
         LevelScales sc;
         for (int l = 0; l < kMaxLevels; ++l) sc.s[l] = zeta_pow(scale, l < levels ? l : levels - 1);
         k_pfa_scores_static<<<1, kStaticThreads, 0, static_cast<cudaStream_t>(cuda_stream)>>>(
-            table, level, x, y, response, n, width0, height0, sc, (nms_q - 1) / 2, pfa_rule, X, Y, k_levels,
-            k_resp, alive);
+            table, level, x, y, response, n, width0, height0, levels, sc, (nms_q - 1) / 2, pfa_rule, X, Y,
+            k_levels, k_resp, alive);
         e = cudaGetLastError();
     }
     if (prev != device) cudaSetDevice(prev);

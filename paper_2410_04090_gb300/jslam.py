@@ -247,9 +247,20 @@ def pfa_scores_static(level, x, y, response, width0: int, height0: int, levels: 
                       nms_q: int = 3, pfa_rule: int = 0, stream=None) -> dict:
     """PFA scores of culled corners (CUDA tensors: level u8, x/y/response
     u16) through jslam_pfa_scores_static, which allocates no device memory.
-    The output tensors are allocated here, by the caller side."""
+    The output tensors are allocated here, by the caller side.  The four
+    inputs must be contiguous 1-D tensors of equal length on one CUDA device
+    (the kernel reads n entries of each by raw pointer)."""
     import torch
-    n = int(level.numel())
+    ins = {"level": (level, torch.uint8), "x": (x, torch.uint16), "y": (y, torch.uint16),
+           "response": (response, torch.uint16)}
+    n = int(level.numel()) if isinstance(level, torch.Tensor) else -1
+    for name, (t, dt) in ins.items():
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt or t.dim() != 1 or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous 1-D {dt} tensor")
+        if t.numel() != n or t.device != level.device:
+            raise ValueError(f"{name} must have the length and device of level")
     dev = level.device
     out = {"X": torch.empty(n, dtype=torch.uint16, device=dev), "Y": torch.empty(n, dtype=torch.uint16, device=dev),
            "k_levels": torch.empty(n, dtype=torch.uint8, device=dev),
