@@ -16,6 +16,8 @@ Modes, each timed over the same steps:
   batched         all pairs of the step in one C-ABI call (one launch per stage)
   graph           the batched call captured once as a CUDA graph and replayed
   plain           one C-ABI call per stereo pair
+  plain_graph     one C-ABI call per stereo pair, each a replay of a captured
+                  single-pair graph pointed at that pair's frames
   learned_skip    batched, with the learned cell-skip proposal (approximate;
                   its feature recall against the exact path is reported)
 Inputs are resident in HBM before the timed region; L2 is flushed (256 MB
@@ -77,6 +79,9 @@ KERNEL_SOURCES = {"k_pyramid": "k_detect.cu", "k_fast_cull": "k_detect.cu", "k_f
                   "k_skipnet": "k_skipnet.cu"}
 LAUNCHES_PER_CALL = 6  # pyramid, detect, PFA NMS, PFA final, ORB, match (exact path)
 SKIP_MODEL = os.path.join(ROOT, "paper_2410_04090_gb300", "skipnet_v1.bin")
+# the autotuner's cache of picks (keyed by GPU, configuration and batch shape)
+TUNE_CACHE = os.environ.get("JSLAM_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "jslam",
+                                                              "tune.json"))
 REFINE_BF = 386.1448  # fx * baseline (pixels x metres) of a KITTI-like stereo rig, for the depth output
 
 
@@ -88,7 +93,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="kitti_1241x376_L8", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--frames", type=int, default=100, help="pairs per step (sequence workloads)")
-    ap.add_argument("--mode", choices=["batched", "graph", "plain", "streams2", "graph_streams2", "streams4",
+    ap.add_argument("--mode", choices=["batched", "graph", "plain", "plain_graph", "streams2", "graph_streams2", "streams4",
                                        "graph_streams4"],
                     default="graph_streams4", help="the headline mode (the others are timed beside it)")
     ap.add_argument("--cpu-pairs", type=int, default=12, help="pairs in the oracle CPU-baseline sample")
@@ -134,6 +139,19 @@ def path_bytes_per_pair(pairs, params, counts):
         A = sum(px)
         total += sum(px[0] + (A - px[0]) + A + 48 * counts[2 * i + s] for s in (0, 1))
     return total / max(len(pairs), 1)
+
+
+ALG_OPS_DEFINITION = ("Eq. 1-3 per tested pixel, one pixel per lane: 16 ring differences, 32 labels (Eq. 1, "
+                      "bright and dark), 32 bit inserts into the two 16-bit masks, 3 for the Eq. 3 table "
+                      "look-ups (Sec. III) = 83; per corner 31 for the response (16 absolute values, 15 adds) "
+                      "and 1 for the cell maximum (Sec. II-C-1)")
+
+
+def alg_ops_per_pixel(corner_fraction):
+    """Integer operations per tested pixel of the scalar formulation of FAST
+    with Bounded Rectification and per-cell culling (see ALG_OPS_DEFINITION);
+    loads are not counted."""
+    return 16 + 32 + 32 + 3 + (31 + 1) * corner_fraction
 
 
 def level_pixels_batch(pairs, params):
@@ -412,6 +430,7 @@ def main():
     else:
         torch.cuda.set_device(0)
         B.build()
+    os.makedirs(os.path.dirname(TUNE_CACHE), exist_ok=True)
     from paper_2410_04090_gb300 import jslam
 
     pairs, params, lo = make_workload(args.workload, args.frames)
@@ -419,6 +438,7 @@ def main():
     dev = torch.device("cuda", torch.cuda.current_device())
     lefts = [torch.from_numpy(f.left).to(dev) for f in pairs]
     rights = [torch.from_numpy(f.right).to(dev) for f in pairs]
+    torch.cuda.synchronize()  # the uploads land before any context stream reads them
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)  # torch work (flush, events) and the library share this stream
     dims = dict(max_width=max(p.left.shape[1] for p in pairs), max_height=max(p.left.shape[0] for p in pairs),
@@ -427,9 +447,11 @@ def main():
     jobs = fe.prepare_batch([jslam.Job(l, r, **p) for l, r, p in zip(lefts, rights, params)])
     if args.tile:
         fe.set_tuning(*args.tile)
-        tuning = tuple(args.tile)
+        tuning = tuple(args.tile) + (0, 0)
+        tune_source = "--tile"
     else:
-        tuning = fe.autotune(jobs)
+        tuning = fe.autotune(jobs, cache=TUNE_CACHE)
+        tune_source = "cache hit" if fe.last_tune_hit else "tuned (stored in the cache)"
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
 
     def step_batched():
@@ -442,9 +464,15 @@ def main():
             fe.match()
 
     graph_fe = None
+    plain_graph_fe = None
+    single_jobs = None
 
     def step_graph():
         graph_fe.graph_launch()
+
+    def step_plain_graph():
+        for j in single_jobs:
+            plain_graph_fe.graph_launch(j)
 
     def timed(step, k, on_step=None):
         total = 0.0
@@ -481,6 +509,15 @@ def main():
         graph_fe.graph_capture(jobs)
         modes["graph"] = step_graph
         modes["plain"] = step_plain
+        if len({(p.left.shape, tuple(sorted(q.items()))) for p, q in zip(pairs, params)}) == 1:
+            # one stereo pair per call, each call one replay of a single-pair
+            # graph pointed at that pair's frames
+            plain_graph_fe = jslam.Frontend(device=dev.index, stream=stream, **dict(dims, max_pairs=1))
+            plain_graph_fe.set_tuning(*tuning)
+            single_jobs = [plain_graph_fe.prepare_batch([jslam.Job(l, r, **p)])
+                           for l, r, p in zip(lefts, rights, params)]
+            plain_graph_fe.graph_capture(single_jobs[0])
+            modes["plain_graph"] = step_plain_graph
     def split_modes(S):
         """The step's pairs split over S contexts on S streams (fork and join
         on the timing stream): one part's kernels fill the others' launch
@@ -667,7 +704,15 @@ def main():
             fe.sync()
             t = fe.fc_ablation_times()
             crf.append(t["crf_ms"]); fc.append(t["fc_ms"])
+        # corner fraction of the first pair (primary threshold, every level), for the algorithmic op count
+        corners = px = 0
+        for side in (0, 1):
+            for lv in range(params[0]["levels"]):
+                c = fe.crf(0, side, lv).cpu().numpy()  # (torch has no uint16 compare on the GPU)
+                corners += int((c > 0).sum())
+                px += c.size
         fc_abl = {"crf_matrix_ms": statistics.median(crf[1:]), "mlpt_tewa_fc_ms": statistics.median(fc[1:]),
+                  "corner_fraction_pair0": corners / max(px, 1),
                   "n_max": 8, "fused_detect_ms": stage_acc["detect"] / args.steps,
                   "note": "paper scheme: CRF-matrix of every level written to HBM (primary threshold), then "
                           "per-level MLPT/TEWA culling kernels; fused: FAST + BR + culling + PFA scatter in one "
@@ -692,9 +737,9 @@ def main():
         e2e = run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, stream)
     if rank == 0:
         emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks,
-             tuning, skip_quality, dev.index, refine, track, fc_abl, br_rep)
+             tuning, skip_quality, dev.index, refine, track, fc_abl, br_rep, tune_source)
     fe.close()
-    for extra in [graph_fe, skip_fe] + extra_fes:
+    for extra in [graph_fe, skip_fe, plain_graph_fe] + extra_fes:
         if extra:
             extra.close()
     if dist:
@@ -765,7 +810,7 @@ def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, 
 
 
 def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks, tuning,
-         skip_quality, dev_index, refine=None, track=None, fc_abl=None, br_rep=None):
+         skip_quality, dev_index, refine=None, track=None, fc_abl=None, br_rep=None, tune_source="--tile"):
     import numpy as np
     peak, peak_kind = measured_peaks()
     stage_ms = {k: v / args.steps for k, v in stage_acc.items()}
@@ -801,9 +846,19 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
     per_pair = path_bytes_per_pair(pairs, params, counts)
     path_hbm = {"algorithmic_bytes_per_pair": per_pair, "achieved": per_pair * value / 1e9, "peak": peak,
                 "unit": "GB/s", "frac": per_pair * value / 1e9 / peak,
-                "definition": "A0 (1 + (S_L - 1) + S_L) + 48 N_kp per image, at the headline pairs/s"}
+                "definition": "A0 (1 + (S_L - 1) + S_L) + 48 N_kp per image, at the headline pairs/s",
+                "by_mode": {m: {"pairs_per_s": v, "achieved": per_pair * v / 1e9, "frac": per_pair * v / 1e9 / peak}
+                            for m, v in mode_values.items()}}
+    if roof and roof.get("bound") == "alu" and fc_abl and "corner_fraction_pair0" in fc_abl:
+        f = fc_abl["corner_fraction_pair0"]
+        alg = alg_ops_per_pixel(f)
+        pixels = level_pixels_batch(pairs, params)
+        rate = alg * pixels / (stage_ms["detect"] / 1e3)
+        roof["algorithmic"] = {"ops_per_pixel": alg, "corner_fraction": f, "achieved": rate, "frac": rate / roof["peak"],
+                               "definition": ALG_OPS_DEFINITION}
     cpu = None if (args.no_cpu_baseline or world > 1) else cpu_baseline(args, pairs, params, lo)
     launches = {"batched": LAUNCHES_PER_CALL, "graph": LAUNCHES_PER_CALL, "plain": LAUNCHES_PER_CALL * n,
+                "plain_graph": LAUNCHES_PER_CALL * n,
                 "learned_skip": LAUNCHES_PER_CALL + 2, "streams2": 2 * LAUNCHES_PER_CALL,
                 "graph_streams2": 2 * LAUNCHES_PER_CALL, "streams4": 4 * LAUNCHES_PER_CALL,
                 "graph_streams4": 4 * LAUNCHES_PER_CALL}
@@ -811,7 +866,9 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
             "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
-                       "pairs_per_step": n, "mode": args.mode, "detect_tile_px": list(tuning),
+                       "pairs_per_step": n, "mode": args.mode, "detect_tile_px": list(tuning[:2]),
+                       "tuning": {"nms_kernel": tuning[2], "detect_ctas_per_sm": tuning[3],
+                                  "source": tune_source},
                        "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
             "modes": mode_values, "learned_skip": skip_quality, "refine": refine, "track": track,
             "fc_ablation": fc_abl, "br_repeatability": br_rep,

@@ -91,6 +91,12 @@ typedef struct {
     int32_t row_band_px;     /* stereo row band at s0, scaled by zeta^n (default 2) */
     int32_t match_max_dist;  /* Hamming distance accepted as a match (default 100) */
     int32_t pfa_rule;        /* 0: suppress when a neighbour has larger K_l AND K_r; 1: lexicographic */
+    int32_t response_mode;   /* corner response: 0 the sum of |I_p - I_c| over all 16 ring pixels (default);
+                              * 1 the arc reading: for each polarity whose longest run satisfies Eq. 3, the
+                              * sum of (|I_p - I_c| - eps) over the pixels of its longest run, the larger of
+                              * the two (with the fallback threshold for fallback corners) */
+    int32_t pyramid_mode;    /* 0: every level resampled from level 0 by zeta^n (default); 1: cascaded, level
+                              * n resampled from level n - 1 by zeta (one launch per level) */
 } jslam_config;
 
 /* One stereo pair of a batch; the per-pair parameters of jslam_extract. */
@@ -241,7 +247,8 @@ typedef struct {
 
 /* Fill `cfg` with the defaults (device 0, NULL stream, 1920x1080, 8 levels,
  * 4000 features, 64 pairs, P_min 9, P_max 13, k 1, q 3, border 19,
- * max_disp 128, band 2, distance 100, fallback off, dominance rule).  The
+ * max_disp 128, band 2, distance 100, fallback off, dominance rule, circle
+ * response, direct pyramid).  The
  * paper fixes P_min, P_max (Sec. II-A, Eq. 3), one corner per cell
  * (Sec. II-C-1) and the 3x3 PFA window (Sec. II-C-2); the other values are
  * this library's readings of points the paper leaves open. */
@@ -312,8 +319,9 @@ jslam_status jslam_get_matches(jslam_ctx *ctx, int32_t pair, jslam_matches *out)
 jslam_status jslam_get_level(jslam_ctx *ctx, int32_t pair, int32_t side, int32_t level,
                              jslam_level_view *out);
 
-/* Size in bytes of pair `pair`'s result block: both images' keypoints at
- * capacity, the matches and a 16-byte header of counts.  Result blocks and
+/* Size in bytes of pair `pair`'s result block: a 16-byte header of int32
+ * counts (left keypoints, right keypoints, two reserved), both images'
+ * keypoints at capacity and the matches.  Result blocks and
  * their download are this library's transport (no counterpart in the
  * paper). */
 jslam_status jslam_result_bytes(jslam_ctx *ctx, int32_t pair, size_t *bytes);
@@ -341,8 +349,10 @@ jslam_status jslam_result_range(jslam_ctx *ctx, int32_t first, int32_t count, si
 jslam_status jslam_download_range(jslam_ctx *ctx, int32_t first, int32_t count, void *dst, size_t bytes);
 
 /* Interpret a downloaded result block: fill host views of `side` (0 or 1)
- * into *kp and, for side 0, the matches into *m (may be NULL).  Pure host
- * function; `block` must hold jslam_result_bytes bytes of pair `pair`
+ * into *kp and, for side 0, the matches into *m (may be NULL).  The count
+ * comes from the block's own header, so a block downloaded from an earlier
+ * extraction of the same batch shape reads correctly.  Pure host function;
+ * `block` must hold jslam_result_bytes bytes of pair `pair`
  * (transport; no counterpart in the paper). */
 jslam_status jslam_result_view(jslam_ctx *ctx, int32_t pair, const void *block, int32_t side,
                                jslam_keypoints *kp, jslam_matches *m);
@@ -372,26 +382,65 @@ jslam_status jslam_enable_stage_timing(jslam_ctx *ctx, int32_t enable);
  * JSLAM_ERR_STATE if timing was off. */
 jslam_status jslam_stage_times(jslam_ctx *ctx, float *ms /* JSLAM_NUM_STAGES entries */);
 
-/* Launch-shape tuning: the target detection tile in pixels (whole culling
- * cells, so results never depend on it).  Defaults 128 x 64. */
+/* Launch-shape tuning.  None of these changes a result: detection tiles hold
+ * whole culling cells, and every kernel variant computes the same outputs. */
 typedef struct {
-    int32_t tile_w_px;   /* 32..128, multiple of 4 */
-    int32_t tile_h_px;   /* 8..128 */
+    int32_t tile_w_px;           /* detection tile width: 32..128, multiple of 4 (default 128) */
+    int32_t tile_h_px;           /* detection tile height: 8..128 (default 64) */
+    int32_t nms_kernel;          /* PFA NMS: 0 one warp per segment when every segment of the batch has at most
+                                  * 96 candidate slots, else one CTA per segment (default); 1 one CTA per
+                                  * segment always */
+    int32_t detect_ctas_per_sm;  /* persistent detection CTAs per SM: 0 as many as fit (default), 1..8 at most
+                                  * that many (never more than fit) */
 } jslam_tuning;
 
-/* Use `t` for the following extractions (plans are rebuilt on change).
- * Launch-shape tuning has no counterpart in the paper (its MLPT / TEWA
- * thread allocation, Sec. II-C-1, is fixed per cell size).
+/* Use `t` for the following extractions (plans are rebuilt when the tile
+ * changes).  Launch-shape tuning has no counterpart in the paper (its MLPT /
+ * TEWA thread allocation, Sec. II-C-1, is fixed per cell size).
  * JSLAM_ERR_ARG for values outside the ranges above. */
 jslam_status jslam_set_tuning(jslam_ctx *ctx, const jslam_tuning *t);
 
-/* Time the detection stage of the batch `jobs` (n pairs, as for
- * jslam_extract_batch) under a set of candidate tile shapes with the stage
- * events, keep the fastest for the context and return it in *out (may be
- * NULL).  Runs the batch several times; results are unaffected.  No
- * counterpart in the paper (an autotuner in place of the fixed thread
- * allocation of Sec. II-C-1). */
+/* Tune the launch shapes on the batch `jobs` (n pairs, as for
+ * jslam_extract_batch), timing the stages with the stage events: the
+ * detection tile among five shapes, then the number of persistent detection
+ * CTAs per SM, then (when every segment fits a warp) the NMS kernel.  Keeps
+ * the fastest for the context and returns it in *out (may be NULL).  Runs the
+ * batch several times; results are unaffected.  No counterpart in the paper
+ * (an autotuner in place of the fixed thread allocation of Sec. II-C-1). */
 jslam_status jslam_autotune(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n, jslam_tuning *out);
+
+/* jslam_autotune with a persistent cache: looks the batch up in the JSON
+ * file `cache_path` under the key of jslam_tune_key (GPU name and SM count of
+ * the context's device, its configuration, the batch's shapes and
+ * parameters).  On a hit the stored pick is applied without any device work
+ * and *hit = 1; on a miss the batch is tuned, the pick is added to the file
+ * (created if missing) and *hit = 0.  `hit` may be NULL.  A file that does
+ * not parse counts as empty and is rewritten.  JSLAM_ERR_ARG for a null
+ * path or an unwritable file.  No counterpart in the paper. */
+jslam_status jslam_autotune_cached(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n, const char *cache_path,
+                                   jslam_tuning *out, int32_t *hit);
+
+/* Key of a batch in the tuning cache (host only, no device work): GPU name
+ * and SM count, the configuration fields that shape the kernels' work
+ * (P_min, P_max, k, q, border, rule, fallback threshold) and every pair's
+ * size, depth, scale bits, threshold, cell, cap and memory kinds, written to
+ * buf (len bytes) as a NUL-terminated string.  JSLAM_ERR_CAPACITY when it
+ * does not fit, JSLAM_ERR_ARG for null arguments.  No counterpart in the
+ * paper. */
+jslam_status jslam_tune_key(const char *gpu_name, int32_t sm_count, const jslam_config *cfg,
+                            const jslam_stereo_job *jobs, int32_t n, char *buf, size_t len);
+
+/* Look `key` up in the tuning cache file (host only): *found = 1 and *out
+ * set on a hit, *found = 0 when the file is missing, does not parse or has
+ * no valid entry for the key.  No counterpart in the paper. */
+jslam_status jslam_tune_cache_get(const char *path, const char *key, jslam_tuning *out, int32_t *found);
+
+/* Add or replace the entry of `key` in the tuning cache file (host only),
+ * with the tuned stage time for reference; the file is rewritten through a
+ * temporary file and a rename.  JSLAM_ERR_ARG for an invalid tuning, a key
+ * holding a quote or backslash, or a file that cannot be written.  No
+ * counterpart in the paper. */
+jslam_status jslam_tune_cache_put(const char *path, const char *key, const jslam_tuning *t, float stage_ms);
 
 /* Capture extraction + matching of the batch `jobs` into a CUDA graph owned
  * by the context (the batch runs once uncaptured first, so that the plan
@@ -404,8 +453,21 @@ jslam_status jslam_graph_capture(jslam_ctx *ctx, const jslam_stereo_job *jobs, i
 
 /* Enqueue one replay of the captured graph on the context stream; results
  * are read as after jslam_extract_batch + jslam_match.  JSLAM_ERR_STATE if
- * nothing was captured.  No counterpart in the paper. */
+ * nothing was captured, or if an extraction since the capture rebuilt the
+ * context's plan (another batch shape, tuning or skip model: the graph's
+ * tables and buffers are gone).  No counterpart in the paper. */
 jslam_status jslam_graph_launch(jslam_ctx *ctx);
+
+/* Replay the captured graph on new frames: `jobs` (n pairs) must match the
+ * capture pair for pair in sizes, depths and parameters, with every image in
+ * device memory; their pointers and pitches replace the captured ones (the
+ * pyramid launch, the one kernel that reads the frames, is updated in the
+ * instantiated graph).  For a camera stream processed one stereo pair per
+ * call this makes every call one graph launch.  The images must stay valid
+ * until jslam_sync().  JSLAM_ERR_ARG when the batch differs from the capture
+ * or an image is in host memory; JSLAM_ERR_STATE as for jslam_graph_launch.
+ * No counterpart in the paper (it launches per scale on streams, Sec. III). */
+jslam_status jslam_graph_launch_jobs(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n);
 
 /* PFA scores of one image's culled corners, computed without allocating
  * device memory.  The allocation-free variant itself has no counterpart in

@@ -58,6 +58,8 @@ typedef struct {
     int32_t max_disp;      /* stereo search range in s0 pixels */
     int32_t row_band_px;   /* stereo row band at s0, scaled per level */
     int32_t match_max_dist;/* Hamming acceptance threshold */
+    int32_t response_mode; /* 0: SAD over the whole circle (default); 1: the arc reading, see or_arc_response */
+    int32_t pyramid_mode;  /* 0: each level resampled from level 0 (default); 1: cascaded, from level n - 1 */
 } or_params;
 
 typedef struct {
@@ -248,6 +250,70 @@ void or_fast(const uint8_t *img, int32_t W, int32_t H, int32_t pitch, int32_t ep
             }
             corner[(size_t)y * W + x] = (uint8_t)or_corner_from_masks(Bb, Bd, p_min, p_max);
             resp[(size_t)y * W + x] = (uint16_t)r;
+        }
+}
+
+/* The alternative reading of the response (Sec. III, "sum of absolute
+ * differences over the circle", read as over the arc that makes the corner):
+ * for each polarity whose longest circular run N satisfies Eq. 3, the sum of
+ * (|d_k| - eps) over the ring positions that lie on a circular run of that
+ * polarity of length N (for N >= 9 there is one such run); the response is
+ * the larger of the two sums (one polarity qualifies when P_min >= 9), 0 when
+ * neither qualifies.  Every term is at least 1, so a corner's response is at
+ * least P_min and at most 16 x 254.                                         */
+
+/* Bit k set when ring position k lies on a circular run of set bits of
+ * `mask` (16 bits) whose length is the longest run's. */
+uint32_t or_arc_positions(uint32_t mask)
+{
+    int32_t n = or_longest_run(mask);
+    uint32_t on = 0;
+    if (n == 0) return 0;
+    for (int32_t start = 0; start < 16; ++start) {
+        int32_t len = 0;
+        while (len < n && ((mask >> ((start + len) % 16)) & 1u)) ++len;
+        if (len == n)
+            for (int32_t j = 0; j < n; ++j) on |= 1u << ((start + j) % 16);
+    }
+    return on;
+}
+
+int32_t or_arc_response(const int32_t d[16], uint32_t Bb, uint32_t Bd, int32_t eps, int32_t p_min, int32_t p_max)
+{
+    int32_t best = 0;
+    uint32_t masks[2] = { Bb, Bd };
+    for (int32_t s = 0; s < 2; ++s) {
+        int32_t n = or_longest_run(masks[s]);
+        if (n < p_min || n > p_max) continue;
+        uint32_t on = or_arc_positions(masks[s]);
+        int32_t sum = 0;
+        for (int32_t k = 0; k < 16; ++k)
+            if ((on >> k) & 1u) sum += (d[k] < 0 ? -d[k] : d[k]) - eps;
+        if (sum > best) best = sum;
+    }
+    return best;
+}
+
+/* CRF-matrix of one level with the arc response (corners as in or_fast). */
+void or_fast_arc(const uint8_t *img, int32_t W, int32_t H, int32_t pitch, int32_t eps,
+                 int32_t p_min, int32_t p_max, int32_t border,
+                 uint8_t *corner, uint16_t *resp)
+{
+    memset(corner, 0, (size_t)W * (size_t)H);
+    memset(resp, 0, sizeof(uint16_t) * (size_t)W * (size_t)H);
+    for (int32_t y = border; y < H - border; ++y)
+        for (int32_t x = border; x < W - border; ++x) {
+            int32_t ic = img[(size_t)y * pitch + x];
+            int32_t d[16];
+            uint32_t Bb = 0, Bd = 0;
+            for (int32_t k = 0; k < 16; ++k) {
+                d[k] = (int32_t)img[(size_t)(y + RING_DY[k]) * pitch + (x + RING_DX[k])] - ic;
+                if (d[k] > eps) Bb |= 1u << k;
+                if (d[k] < -eps) Bd |= 1u << k;
+            }
+            int32_t is_corner = or_corner_from_masks(Bb, Bd, p_min, p_max);
+            corner[(size_t)y * W + x] = (uint8_t)is_corner;
+            resp[(size_t)y * W + x] = (uint16_t)(is_corner ? or_arc_response(d, Bb, Bd, eps, p_min, p_max) : 0);
         }
 }
 
@@ -542,6 +608,7 @@ int32_t or_check_params(int32_t W0, int32_t H0, const or_params *p)
     if (p->border < 16) return -1;
     if (p->max_feats < 1) return -1;
     if (p->pfa_rule < 0 || p->pfa_rule > 1) return -1;
+    if (p->response_mode < 0 || p->response_mode > 1 || p->pyramid_mode < 0 || p->pyramid_mode > 1) return -1;
     if (W0 < 1 || H0 < 1 || W0 > 4096 || H0 > 4096) return -1;
     int32_t W[OR_MAX_LEVELS], H[OR_MAX_LEVELS], c[OR_MAX_LEVELS];
     or_level_geometry(W0, H0, p->levels, p->scale, p->cell, W, H, c);
@@ -564,6 +631,8 @@ int32_t or_extract_image(const uint8_t *L0, int32_t W0, int32_t H0, int32_t pitc
         blur[n] = (uint8_t *)malloc((size_t)W[n] * (size_t)H[n]);
         if (n == 0)
             for (int32_t y = 0; y < H0; ++y) memcpy(raw[0] + (size_t)y * W0, L0 + (size_t)y * pitch0, (size_t)W0);
+        else if (p->pyramid_mode == 1)  /* cascaded: level n from level n - 1 by one factor zeta */
+            or_pyramid_level(raw[n - 1], W[n - 1], H[n - 1], W[n - 1], p->scale, 1, raw[n], W[n], H[n], W[n]);
         else
             or_pyramid_level(L0, W0, H0, pitch0, p->scale, n, raw[n], W[n], H[n], W[n]);
         or_blur(raw[n], W[n], H[n], W[n], blur[n], W[n]);
@@ -585,6 +654,21 @@ int32_t or_extract_image(const uint8_t *L0, int32_t W0, int32_t H0, int32_t pitc
             lo = (uint8_t *)malloc(area);
             or_fast(raw[n], W[n], H[n], W[n], p->fast_thresh_lo, p->p_min, p->p_max, p->border, lo, resp_lo);
             free(resp_lo);
+        }
+        if (p->response_mode == 1) {
+            /* the arc response depends on the threshold: the corners of a
+             * cell with no primary-threshold corner (the only cells whose
+             * fallback corners are ranked) take it at the fallback threshold */
+            or_fast_arc(raw[n], W[n], H[n], W[n], p->fast_thresh, p->p_min, p->p_max, p->border, hi, resp);
+            if (lo) {
+                uint8_t *lo_arc = (uint8_t *)malloc(area);
+                uint16_t *resp_arc = (uint16_t *)malloc(area * sizeof(uint16_t));
+                or_fast_arc(raw[n], W[n], H[n], W[n], p->fast_thresh_lo, p->p_min, p->p_max, p->border, lo_arc,
+                            resp_arc);
+                for (size_t q = 0; q < area; ++q)
+                    if (!hi[q]) resp[q] = resp_arc[q];
+                free(lo_arc); free(resp_arc);
+            }
         }
         size_t cells = (size_t)((W[n] + c[n] - 1) / c[n]) * (size_t)((H[n] + c[n] - 1) / c[n]) * (size_t)p->k_per_cell;
         int32_t *cx = (int32_t *)malloc(sizeof(int32_t) * (cells + 1));

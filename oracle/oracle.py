@@ -47,6 +47,7 @@ class Params(C.Structure):
         ("cell", C.c_int32), ("k_per_cell", C.c_int32), ("nms_q", C.c_int32),
         ("border", C.c_int32), ("max_feats", C.c_int32), ("pfa_rule", C.c_int32),
         ("max_disp", C.c_int32), ("row_band_px", C.c_int32), ("match_max_dist", C.c_int32),
+        ("response_mode", C.c_int32), ("pyramid_mode", C.c_int32),
     ]
 
 
@@ -80,6 +81,8 @@ class FrontendParams:
     max_disp: int = 128
     row_band_px: int = 2
     match_max_dist: int = 100
+    response_mode: int = 0   # 1: arc response (reading O3's alternative)
+    pyramid_mode: int = 0    # 1: cascaded pyramid (reading O1's alternative)
 
     def to_c(self) -> Params:
         return Params(**asdict(self))
@@ -112,6 +115,11 @@ def lib():
         L.or_corner_from_masks.restype = i32
         L.or_corner_from_masks.argtypes = [C.c_uint32, C.c_uint32, i32, i32]
         L.or_fast.argtypes = [u8p, i32, i32, i32, i32, i32, i32, i32, u8p, u16p]
+        L.or_fast_arc.argtypes = [u8p, i32, i32, i32, i32, i32, i32, i32, u8p, u16p]
+        L.or_arc_positions.restype = C.c_uint32
+        L.or_arc_positions.argtypes = [C.c_uint32]
+        L.or_arc_response.restype = i32
+        L.or_arc_response.argtypes = [i32p, C.c_uint32, C.c_uint32, i32, i32, i32]
         L.or_cull_level.restype = i32
         L.or_cull_level.argtypes = [u8p, C.c_void_p, u16p, i32, i32, i32, i32, i32p, i32p, i32p, i32]
         L.or_project.restype = i32
@@ -207,6 +215,25 @@ def fast(img: np.ndarray, eps: int, p_min: int = 9, p_max: int = 13, border: int
     corner = np.zeros((H, W), np.uint8); resp = np.zeros((H, W), np.uint16)
     lib().or_fast(img, W, H, W, eps, p_min, p_max, border, corner, resp)
     return corner, resp
+
+
+def fast_arc(img: np.ndarray, eps: int, p_min: int = 9, p_max: int = 13, border: int = 3):
+    """CRF-matrix with the arc response (the alternative reading of the
+    response): corners as fast(), response = sum of (|d| - eps) over the
+    qualifying arc."""
+    img = np.ascontiguousarray(img, np.uint8)
+    H, W = img.shape
+    corner = np.zeros((H, W), np.uint8); resp = np.zeros((H, W), np.uint16)
+    lib().or_fast_arc(img, W, H, W, eps, p_min, p_max, border, corner, resp)
+    return corner, resp
+
+
+def arc_positions(mask: int) -> int:
+    return lib().or_arc_positions(mask)
+
+
+def arc_response(d, Bb: int, Bd: int, eps: int, p_min: int = 9, p_max: int = 13) -> int:
+    return lib().or_arc_response(np.ascontiguousarray(d, np.int32), Bb, Bd, eps, p_min, p_max)
 
 
 def cull_level(corner_hi, corner_lo, resp, c: int, k: int):

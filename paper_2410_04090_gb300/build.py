@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libjslam.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 CUDA_SOURCES = ["k_detect.cu", "k_pyca.cu", "k_orb_match.cu", "k_refine.cu", "k_fc_ablation.cu", "k_skipnet.cu", "jslam_api.cu", "pfa_static.cu"]
-HOST_SOURCES = ["tables.cpp"]
+HOST_SOURCES = ["tables.cpp", "tune_cache.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -66,7 +66,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     for s in HOST_SOURCES:
         obj = os.path.join(BUILD, s + ".o")
         jobs.append((["g++", "-std=c++17", "-O2", "-fPIC", "-ffp-contract=off", "-fno-fast-math",
-                      "-I", CSRC, "-c", os.path.join(CSRC, s), "-o", obj], obj))
+                      "-I", CSRC, "-I", INCLUDE, "-c", os.path.join(CSRC, s), "-o", obj], obj))
     with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         logs = list(ex.map(lambda j: _run(j[0]), jobs))
     if verbose_ptxas:

@@ -14,6 +14,8 @@
 
 namespace jslam {
 int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, int max_planes);
+const void *pyramid_kernel();
+cudaError_t detect_ctas_that_fit(const Batch &b, int *per_sm);
 }
 
 using namespace jslam;
@@ -148,6 +150,10 @@ SideLayout side_layout(int C, size_t base)
     return s;
 }
 
+// A pair's result block starts with a 16-byte header of int32 counts (left
+// keypoints, right keypoints, two reserved), written by the finalisation, so
+// that a downloaded block describes itself.
+constexpr size_t kBlockHeader = 16;
 struct PairLayout {
     int capacity;
     SideLayout side[2];
@@ -158,7 +164,7 @@ PairLayout pair_layout(int max_feats)
 {
     PairLayout p;
     p.capacity = (int)align_up((size_t)max_feats, 32);
-    p.side[0] = side_layout(p.capacity, 0);
+    p.side[0] = side_layout(p.capacity, align_up(kBlockHeader, 256));
     p.side[1] = side_layout(p.capacity, p.side[0].end);
     size_t o = p.side[1].end;
     p.match_idx = o; o = align_up(o + (size_t)p.capacity * 4, 256);
@@ -223,11 +229,23 @@ struct jslam_ctx {
     bool plan_skip = false;  // the current plan has skip buffers
 
     // launch-shape tuning and the captured graph
-    jslam_tuning tune{128, 64};
-    jslam_tuning plan_tune{0, 0};  // tuning the current plan was built with
+    jslam_tuning tune{128, 64, 0, 0};
+    jslam_tuning plan_tune{0, 0, 0, 0};  // tuning the current plan was built with (tile fields)
     cudaGraphExec_t graph = nullptr;
+    cudaGraph_t graph_src = nullptr;    // the captured graph (its node handles address `graph`)
+    // its pyramid launches (one, or one per level in the cascaded pyramid):
+    // the kernel that reads the input images, with the batch each got
+    std::vector<cudaGraphNode_t> graph_pyr;
+    std::vector<cudaKernelNodeParams> graph_pyr_params;
+    std::vector<Batch> graph_pyr_batch;
+    std::vector<JobKey> graph_keys;     // batch signature of the capture
+    uint64_t graph_gen = 0;             // plan generation the graph was captured on
     int graph_pairs = 0;
     bool graph_timed = false;  // the graph records the stage events
+    // generation of the plan: bumped whenever build_plan rebuilds the tables
+    // or buffers, which invalidates a graph captured on an earlier plan
+    uint64_t plan_gen = 0;
+    float tune_ms = 0.0f;  // detection stage time of the last autotuned pick
 };
 
 namespace {
@@ -302,6 +320,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     if (keys == ctx->keys && ctx->plan_tune.tile_w_px == ctx->tune.tile_w_px &&
         ctx->plan_tune.tile_h_px == ctx->tune.tile_h_px && ctx->plan_skip == ctx->skip_on)
         return JSLAM_OK;
+    ++ctx->plan_gen;
 
     const int n_img = 2 * n;
     const int k = cfg.k_per_cell;
@@ -392,6 +411,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
         }
     const size_t o_ftl = reserve(sizeof(int32_t) * (n_fast_tiles + 1));
     const size_t o_ptl = reserve(sizeof(int32_t) * (n_pyr_tiles + 1));
+    const size_t o_porder = reserve(sizeof(int32_t) * (n_pyr_tiles + 1));
     const size_t o_trec = reserve(sizeof(TileRec) * (n_fast_tiles + 1));
     const size_t o_lstart = reserve(sizeof(int32_t) * (kMaxLevels + 1) * n_img);
     const size_t o_tmaps = reserve(sizeof(CUtensorMap) * (size_t)n_levels);
@@ -433,6 +453,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
             I.map = ctx->maps.as<uint32_t>(map_off);
             map_off += align_up((size_t)g.W[0] * g.H[0] * 4, 256);
             I.count = dcounts + img;
+            I.count_hdr = reinterpret_cast<int32_t *>(rblock) + s;
             I.skip = nullptr;
             I.skip_logits = nullptr;
             I.skip_w8 = (g.W[0] + 7) / 8;
@@ -489,8 +510,17 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 uint32_t *tx = reinterpret_cast<uint32_t *>(host.data() + t_off);
                 L.tapx = reinterpret_cast<const uint32_t *>(dplan + t_off);
                 L.tapy = L.tapx + L.W;
-                for (int x = 0; x < L.W; ++x) tx[x] = bilinear_tap(x, sc, g.W[0]);
-                for (int y = 0; y < L.H; ++y) tx[L.W + y] = bilinear_tap(y, sc, g.H[0]);
+                // source of the resampling: level 0 by zeta^n, or (cascaded)
+                // the level above by one factor zeta
+                const bool cascade = cfg.pyramid_mode == 1 && l > 0;
+                const LevelDesc *up = cascade ? &levels[li - 1] : nullptr;
+                L.src = up ? up->raw : nullptr;
+                L.src_W = up ? up->W : g.W[0];
+                L.src_H = up ? up->H : g.H[0];
+                L.src_pitch = up ? up->pitch : 0;
+                const double tap_s = cascade ? zeta_pow(jobs[p].scale, 1) : sc;
+                for (int x = 0; x < L.W; ++x) tx[x] = bilinear_tap(x, tap_s, L.src_W);
+                for (int y = 0; y < L.H; ++y) tx[L.W + y] = bilinear_tap(y, tap_s, L.src_H);
                 t_off += align_up((size_t)(L.W + L.H) * 4, 16);
                 uint16_t *px = reinterpret_cast<uint16_t *>(host.data() + t_off);
                 L.projx = reinterpret_cast<const uint16_t *>(dplan + t_off);
@@ -586,6 +616,18 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
         }
     }
 
+    // pyramid tiles by level number (the cascaded pyramid launches level
+    // number n once level n - 1 of every image is complete)
+    int pass_first[kMaxLevels + 1] = {};
+    {
+        auto porder = reinterpret_cast<int32_t *>(host.data() + o_porder);
+        int count[kMaxLevels] = {};
+        for (int t = 0; t < pyr; ++t) ++count[levels[ptile_level[t]].level];
+        for (int d = 0; d < kMaxLevels; ++d) pass_first[d + 1] = pass_first[d] + count[d];
+        int fill[kMaxLevels];
+        for (int d = 0; d < kMaxLevels; ++d) fill[d] = pass_first[d];
+        for (int t = 0; t < pyr; ++t) porder[fill[levels[ptile_level[t]].level]++] = t;
+    }
     e = cudaMemcpyAsync(ctx->plan.ptr, host.data(), off, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return fail(ctx, e);
 
@@ -595,6 +637,9 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.pairs = reinterpret_cast<const PairDesc *>(dplan + o_pairs);
     b.pyr_tile_base = reinterpret_cast<const int32_t *>(dplan + o_pyr);
     b.pyr_tile_level = reinterpret_cast<const int32_t *>(dplan + o_ptl);
+    b.pyr_order = reinterpret_cast<const int32_t *>(dplan + o_porder);
+    b.pyr_pass = cfg.pyramid_mode == 1 ? 0 : -1;
+    for (int d = 0; d <= kMaxLevels; ++d) b.pyr_pass_first[d] = pass_first[d];
     b.fast_tile_base = reinterpret_cast<const int32_t *>(dplan + o_fast);
     b.seg_level = reinterpret_cast<const int32_t *>(dplan + o_seg);
     b.fast_tile_level = reinterpret_cast<const int32_t *>(dplan + o_ftl);
@@ -646,6 +691,45 @@ jslam_status enqueue_counts(jslam_ctx *ctx)
     return fail(ctx, cudaMemcpyAsync(ctx->h_counts, ctx->counts.ptr, bytes, cudaMemcpyDeviceToHost, ctx->stream));
 }
 
+// Signature of one job (see JobKey).
+JobKey job_key(const jslam_stereo_job &j)
+{
+    JobKey k;
+    std::memset(&k, 0, sizeof(k));
+    k.W = j.left.width; k.H = j.left.height; k.levels = j.levels;
+    k.eps = j.fast_thresh; k.cell = j.cell; k.feats = j.max_feats;
+    std::memcpy(&k.scale_bits, &j.scale, 4);
+    k.mem[0] = j.left.memory;
+    k.mem[1] = j.right.memory;
+    return k;
+}
+
+// Release the captured graph, if any.
+void drop_graph(jslam_ctx *ctx)
+{
+    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    if (ctx->graph_src) cudaGraphDestroy(ctx->graph_src);
+    ctx->graph = nullptr;
+    ctx->graph_src = nullptr;
+    ctx->graph_pyr.clear();
+    ctx->graph_pyr_params.clear();
+    ctx->graph_pyr_batch.clear();
+    ctx->graph_keys.clear();
+}
+
+// Context state after a graph replay (extraction and matching; refinement is
+// enqueued separately).
+jslam_status graph_launched(jslam_ctx *ctx)
+{
+    ctx->have_extract = true;
+    ctx->have_match = true;
+    ctx->have_refine = false;
+    ctx->synced = false;
+    for (int i = 0; i < JSLAM_NUM_STAGES; ++i)
+        ctx->stage_done[i] = i <= JSLAM_STAGE_MATCH && ctx->graph_timed && ctx->timing;
+    return JSLAM_OK;
+}
+
 jslam_status use_device(jslam_ctx *ctx)
 {
     int cur = -1;
@@ -679,6 +763,8 @@ void jslam_default_config(jslam_config *cfg)
     cfg->row_band_px = 2;
     cfg->match_max_dist = 100;
     cfg->pfa_rule = 0;
+    cfg->response_mode = 0;
+    cfg->pyramid_mode = 0;
 }
 
 jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
@@ -696,6 +782,7 @@ jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
     if (c.border < 16 || c.border > 512) return JSLAM_ERR_ARG;
     if (c.max_disp < 0 || c.max_disp > 4096 || c.row_band_px < 0 || c.row_band_px > 64) return JSLAM_ERR_ARG;
     if (c.match_max_dist < 0 || c.pfa_rule < 0 || c.pfa_rule > 1) return JSLAM_ERR_ARG;
+    if (c.response_mode < 0 || c.response_mode > 1 || c.pyramid_mode < 0 || c.pyramid_mode > 1) return JSLAM_ERR_ARG;
 
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
@@ -706,6 +793,7 @@ jslam_status jslam_create(jslam_ctx **out, const jslam_config *cfg)
     ctx->cfg = c;
     ctx->prm.p_min = c.p_min; ctx->prm.p_max = c.p_max; ctx->prm.k = c.k_per_cell;
     ctx->prm.nms_rad = (c.nms_q - 1) / 2; ctx->prm.border = c.border; ctx->prm.rule = c.pfa_rule;
+    ctx->prm.resp_arc = c.response_mode;
     ctx->prm.max_disp = c.max_disp; ctx->prm.max_dist = c.match_max_dist;
 
     jslam_status st = JSLAM_OK;
@@ -835,6 +923,8 @@ jslam_status jslam_extract_batch(jslam_ctx *ctx, const jslam_stereo_job *jobs, i
         img = last + 1;
     }
     cudaError_t e;
+    b.nms_kernel = ctx->tune.nms_kernel;
+    b.fast_ctas_per_sm = ctx->tune.detect_ctas_per_sm;
     for (bool &d : ctx->stage_done) d = false;
     if (ctx->timing && (e = cudaEventRecord(ctx->events[0], ctx->stream)) != cudaSuccess) return fail(ctx, e);
     for (int i = 0; i < JSLAM_STAGE_MATCH; ++i) {
@@ -1052,6 +1142,14 @@ jslam_status jslam_fc_ablation_times(jslam_ctx *ctx, float *crf_ms, float *fc_ms
     return fail(ctx, e);
 }
 
+// Keypoint count of `side` in a downloaded result block (its header).
+static int32_t block_count(const void *block, int side)
+{
+    int32_t c;
+    std::memcpy(&c, static_cast<const char *>(block) + 4 * side, 4);
+    return c;
+}
+
 static void refined_views(const PairLayout &pl, const char *b, int32_t count, jslam_refined *out)
 {
     out->count = count;
@@ -1120,7 +1218,7 @@ jslam_status jslam_result_refined_view(jslam_ctx *ctx, int32_t pair, const void 
     if (!ctx || !block || !out) return JSLAM_ERR_ARG;
     if (!ctx->have_refine) return JSLAM_ERR_STATE;
     if (pair < 0 || pair >= (int)ctx->layouts.size()) return JSLAM_ERR_ARG;
-    refined_views(ctx->layouts[pair], static_cast<const char *>(block), synced_count(ctx, 2 * pair), out);
+    refined_views(ctx->layouts[pair], static_cast<const char *>(block), block_count(block, 0), out);
     return JSLAM_OK;
 }
 
@@ -1196,7 +1294,7 @@ jslam_status jslam_result_view(jslam_ctx *ctx, int32_t pair, const void *block, 
     const PairLayout &pl = ctx->layouts[pair];
     const SideLayout &s = pl.side[side];
     const char *b = static_cast<const char *>(block);
-    kp->count = synced_count(ctx, 2 * pair + side);
+    kp->count = block_count(block, side);
     kp->capacity = pl.capacity;
     kp->desc = reinterpret_cast<const uint32_t *>(b + s.desc);
     kp->k_resp = reinterpret_cast<const uint32_t *>(b + s.k_resp);
@@ -1305,37 +1403,118 @@ jslam_status jslam_set_tuning(jslam_ctx *ctx, const jslam_tuning *t)
     if (!ctx || !t) return JSLAM_ERR_ARG;
     if (t->tile_w_px < 32 || t->tile_w_px > kFastMaxTile || t->tile_w_px % 4 != 0) return JSLAM_ERR_ARG;
     if (t->tile_h_px < 8 || t->tile_h_px > kFastMaxTile) return JSLAM_ERR_ARG;
+    if (t->nms_kernel < 0 || t->nms_kernel > 1 || t->detect_ctas_per_sm < 0 || t->detect_ctas_per_sm > 8)
+        return JSLAM_ERR_ARG;
     ctx->tune = *t;
     return JSLAM_OK;
 }
+
+namespace {
+
+// Median-free minimum of a stage's time over `reps` runs of the batch (the
+// first run of a new tuning also rebuilds the plan and is not counted).
+jslam_status time_stage(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n, int stage, int reps, float *best)
+{
+    *best = -1.0f;
+    for (int rep = 0; rep <= reps; ++rep) {
+        jslam_status st = jslam_extract_batch(ctx, jobs, n);
+        if (st == JSLAM_OK) st = jslam_sync(ctx);
+        float ms[JSLAM_NUM_STAGES];
+        if (st == JSLAM_OK) st = jslam_stage_times(ctx, ms);
+        if (st != JSLAM_OK) return st;
+        if (rep > 0 && (*best < 0 || ms[stage] < *best)) *best = ms[stage];
+    }
+    return JSLAM_OK;
+}
+
+}  // namespace
 
 jslam_status jslam_autotune(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n, jslam_tuning *out)
 {
     if (!ctx || !jobs) return JSLAM_ERR_ARG;
     if (ctx->status != JSLAM_OK) return ctx->status;
-    static const jslam_tuning candidates[] = { { 128, 64 }, { 128, 32 }, { 128, 128 }, { 64, 64 }, { 64, 128 } };
+    static const int tiles[][2] = { { 128, 64 }, { 128, 32 }, { 128, 128 }, { 64, 64 }, { 64, 128 } };
     const bool was_timing = ctx->timing;
     jslam_status st = jslam_enable_stage_timing(ctx, 1);
     if (st != JSLAM_OK) return st;
     jslam_tuning best = ctx->tune;
+    best.nms_kernel = 0;
+    best.detect_ctas_per_sm = 0;
+    // 1. the detection tile
     float best_ms = -1.0f;
-    for (const jslam_tuning &cand : candidates) {
-        ctx->tune = cand;
-        float fastest = -1.0f;
-        for (int rep = 0; rep < 4; ++rep) {  // the first run builds the plan
-            if ((st = jslam_extract_batch(ctx, jobs, n)) != JSLAM_OK) break;
-            if ((st = jslam_sync(ctx)) != JSLAM_OK) break;
-            float ms[JSLAM_NUM_STAGES];
-            if ((st = jslam_stage_times(ctx, ms)) != JSLAM_OK) break;
-            if (rep > 0 && (fastest < 0 || ms[JSLAM_STAGE_DETECT] < fastest)) fastest = ms[JSLAM_STAGE_DETECT];
+    for (const auto &tl : tiles) {
+        ctx->tune = best;
+        ctx->tune.tile_w_px = tl[0];
+        ctx->tune.tile_h_px = tl[1];
+        float ms;
+        if ((st = time_stage(ctx, jobs, n, JSLAM_STAGE_DETECT, 3, &ms)) != JSLAM_OK) break;
+        if (best_ms < 0 || ms < best_ms) {
+            best_ms = ms;
+            best.tile_w_px = tl[0];
+            best.tile_h_px = tl[1];
         }
-        if (st != JSLAM_OK) break;
-        if (best_ms < 0 || fastest < best_ms) { best_ms = fastest; best = cand; }
+    }
+    // 2. fewer persistent detection CTAs per SM than fit (one less, then two)
+    int fit = 0;
+    if (st == JSLAM_OK) {
+        ctx->tune = best;
+        if ((st = jslam_extract_batch(ctx, jobs, n)) == JSLAM_OK) st = jslam_sync(ctx);
+        if (st == JSLAM_OK) {
+            const cudaError_t e = detect_ctas_that_fit(ctx->batch, &fit);
+            if (e != cudaSuccess) st = fail(ctx, e);
+        }
+    }
+    for (int c = fit - 1; st == JSLAM_OK && c >= 1 && c >= fit - 2; --c) {
+        ctx->tune = best;
+        ctx->tune.detect_ctas_per_sm = c;
+        float ms;
+        if ((st = time_stage(ctx, jobs, n, JSLAM_STAGE_DETECT, 3, &ms)) != JSLAM_OK) break;
+        if (ms < best_ms) { best_ms = ms; best.detect_ctas_per_sm = c; }
+    }
+    // 3. the NMS kernel, where the warp-per-segment variant applies
+    if (st == JSLAM_OK && ctx->batch.max_segment <= 96) {
+        float nms_ms[2] = { -1.0f, -1.0f };
+        for (int v = 0; v < 2 && st == JSLAM_OK; ++v) {
+            ctx->tune = best;
+            ctx->tune.nms_kernel = v;
+            st = time_stage(ctx, jobs, n, JSLAM_STAGE_PFA_NMS, 3, &nms_ms[v]);
+        }
+        if (st == JSLAM_OK) best.nms_kernel = nms_ms[1] < nms_ms[0] ? 1 : 0;
     }
     ctx->tune = best;
+    ctx->tune_ms = best_ms;
     if (st == JSLAM_OK) st = jslam_enable_stage_timing(ctx, was_timing ? 1 : 0);
     if (st == JSLAM_OK && out) *out = best;
     return st;
+}
+
+jslam_status jslam_autotune_cached(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n, const char *cache_path,
+                                   jslam_tuning *out, int32_t *hit)
+{
+    if (!ctx || !jobs || !cache_path || n < 1) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (hit) *hit = 0;
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, ctx->cfg.device);
+    if (e != cudaSuccess) return fail(ctx, e);
+    std::vector<char> key(256 + 96 * (size_t)n);
+    st = jslam_tune_key(prop.name, prop.multiProcessorCount, &ctx->cfg, jobs, n, key.data(), key.size());
+    if (st != JSLAM_OK) return st;
+    jslam_tuning t{};
+    int32_t found = 0;
+    if ((st = jslam_tune_cache_get(cache_path, key.data(), &t, &found)) != JSLAM_OK) return st;
+    if (found) {
+        if ((st = jslam_set_tuning(ctx, &t)) != JSLAM_OK) return st;
+        if (hit) *hit = 1;
+        if (out) *out = t;
+        return JSLAM_OK;
+    }
+    if ((st = jslam_autotune(ctx, jobs, n, &t)) != JSLAM_OK) return st;
+    if ((st = jslam_tune_cache_put(cache_path, key.data(), &t, ctx->tune_ms)) != JSLAM_OK) return st;
+    if (out) *out = t;
+    return JSLAM_OK;
 }
 
 jslam_status jslam_graph_capture(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n)
@@ -1347,7 +1526,7 @@ jslam_status jslam_graph_capture(jslam_ctx *ctx, const jslam_stereo_job *jobs, i
     if (st == JSLAM_OK) st = jslam_match(ctx);
     if (st == JSLAM_OK) st = jslam_sync(ctx);
     if (st != JSLAM_OK) return st;
-    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+    drop_graph(ctx);
     cudaError_t e = cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail(ctx, e);
     jslam_status cap = jslam_extract_batch(ctx, jobs, n);
@@ -1356,9 +1535,37 @@ jslam_status jslam_graph_capture(jslam_ctx *ctx, const jslam_stereo_job *jobs, i
     e = cudaStreamEndCapture(ctx->stream, &graph);
     if (cap != JSLAM_OK) { if (graph) cudaGraphDestroy(graph); return cap; }
     if (e != cudaSuccess) return fail(ctx, e);
-    e = cudaGraphInstantiate(&ctx->graph, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) { ctx->graph = nullptr; return fail(ctx, e); }
+    // the pyramid launch is the one node that reads the input images: keep
+    // its handle (and the graph it belongs to) so that replays can point it
+    // at new frames
+    size_t n_nodes = 0;
+    e = cudaGraphGetNodes(graph, nullptr, &n_nodes);
+    std::vector<cudaGraphNode_t> nodes(n_nodes);
+    if (e == cudaSuccess && n_nodes) e = cudaGraphGetNodes(graph, nodes.data(), &n_nodes);
+    for (size_t i = 0; e == cudaSuccess && i < n_nodes; ++i) {
+        cudaGraphNodeType type;
+        if ((e = cudaGraphNodeGetType(nodes[i], &type)) != cudaSuccess || type != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp{};
+        if ((e = cudaGraphKernelNodeGetParams(nodes[i], &kp)) != cudaSuccess) break;
+        if (kp.func == pyramid_kernel()) {
+            if (!kp.kernelParams || !kp.kernelParams[0]) { e = cudaErrorInvalidValue; break; }
+            ctx->graph_pyr.push_back(nodes[i]);
+            ctx->graph_pyr_params.push_back(kp);
+            ctx->graph_pyr_batch.push_back(*static_cast<const Batch *>(kp.kernelParams[0]));
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ctx->graph, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        ctx->graph = nullptr;
+        ctx->graph_pyr.clear();
+        ctx->graph_pyr_params.clear();
+        ctx->graph_pyr_batch.clear();
+        return fail(ctx, e);
+    }
+    ctx->graph_src = graph;
+    ctx->graph_keys = ctx->keys;
+    ctx->graph_gen = ctx->plan_gen;
     ctx->graph_pairs = n;
     ctx->graph_timed = ctx->timing;
     return JSLAM_OK;
@@ -1368,19 +1575,51 @@ jslam_status jslam_graph_launch(jslam_ctx *ctx)
 {
     if (!ctx) return JSLAM_ERR_ARG;
     if (ctx->status != JSLAM_OK) return ctx->status;
-    if (!ctx->graph) return JSLAM_ERR_STATE;
+    if (!ctx->graph || ctx->graph_gen != ctx->plan_gen) return JSLAM_ERR_STATE;
     jslam_status st = use_device(ctx);
     if (st != JSLAM_OK) return st;
     cudaError_t e = cudaGraphLaunch(ctx->graph, ctx->stream);
     if (e != cudaSuccess) return fail(ctx, e);
-    ctx->have_extract = true;
-    ctx->have_match = true;
-    ctx->have_refine = false;
-    ctx->synced = false;
-    // the graph holds extraction and matching (refinement is enqueued separately)
-    for (int i = 0; i < JSLAM_NUM_STAGES; ++i)
-        ctx->stage_done[i] = i <= JSLAM_STAGE_MATCH && ctx->graph_timed && ctx->timing;
-    return JSLAM_OK;
+    return graph_launched(ctx);
+}
+
+jslam_status jslam_graph_launch_jobs(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_t n)
+{
+    if (!ctx || !jobs) return JSLAM_ERR_ARG;
+    if (ctx->status != JSLAM_OK) return ctx->status;
+    if (!ctx->graph || ctx->graph_gen != ctx->plan_gen) return JSLAM_ERR_STATE;
+    if (n != ctx->graph_pairs || ctx->graph_pyr.empty()) return JSLAM_ERR_ARG;
+    for (int p = 0; p < n; ++p) {
+        const jslam_status s = check_job(ctx, jobs[p]);
+        if (s != JSLAM_OK) return s;
+        if (jobs[p].left.memory != JSLAM_MEM_DEVICE || jobs[p].right.memory != JSLAM_MEM_DEVICE)
+            return JSLAM_ERR_ARG;
+        if (!(job_key(jobs[p]) == ctx->graph_keys[p])) return JSLAM_ERR_ARG;
+    }
+    jslam_status st = use_device(ctx);
+    if (st != JSLAM_OK) return st;
+    // each pyramid launch as captured, with this call's frames; the nodes
+    // keep copies of their parameters, so `b` may go out of scope after
+    Inputs in = ctx->batch.in;
+    for (int img = 0; img < 2 * n; ++img) {
+        const jslam_image &im = img & 1 ? jobs[img >> 1].right : jobs[img >> 1].left;
+        in.ptr[img] = im.data;
+        in.pitch[img] = im.pitch;
+    }
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < ctx->graph_pyr.size() && e == cudaSuccess; ++i) {
+        Batch b = ctx->graph_pyr_batch[i];
+        b.in = in;
+        void *args[] = { &b };
+        cudaKernelNodeParams kp = ctx->graph_pyr_params[i];
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        e = cudaGraphExecKernelNodeSetParams(ctx->graph, ctx->graph_pyr[i], &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(ctx->graph, ctx->stream);
+    if (e != cudaSuccess) return fail(ctx, e);
+    ctx->batch.in = in;
+    return graph_launched(ctx);
 }
 
 void jslam_destroy(jslam_ctx *ctx)
@@ -1405,7 +1644,7 @@ void jslam_destroy(jslam_ctx *ctx)
         if (ev) cudaEventDestroy(ev);
     for (cudaEvent_t ev : ctx->abl_ev)
         if (ev) cudaEventDestroy(ev);
-    if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+    drop_graph(ctx);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     cudaGetLastError();
     delete ctx;

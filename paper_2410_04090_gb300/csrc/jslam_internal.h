@@ -66,6 +66,10 @@ struct LevelDesc {
     const uint32_t *tapy;
     const uint16_t *projx;   // s0 projection of each x / y of the level
     const uint16_t *projy;
+    // source of the resampling: nullptr = level 0 (the input image); in the
+    // cascaded pyramid the raw level n - 1 (taps then use one factor zeta)
+    const uint8_t *src;
+    int32_t src_W, src_H, src_pitch;
     int32_t W, H, pitch;     // pitch of raw: width rounded up to 128
     int32_t blur_pitch;
     int32_t c, cells_x, cells_y;
@@ -90,6 +94,7 @@ struct ImageDesc {
     int32_t seg_base, seg_count;
     uint32_t *map;           // W0 * H0 packed (K_l << 16 | K_r); all zero between runs
     int32_t *count;          // keypoint count written by finalisation
+    int32_t *count_hdr;      // the same count in the header of the pair's result block
     int32_t *level_start;    // kMaxLevels + 1 entries
     KpOut out;
     // learned cell-skip (skip == nullptr: exact mode)
@@ -119,6 +124,7 @@ struct PairDesc {
 struct Params {
     int32_t p_min, p_max, k, nms_rad, border, rule;
     int32_t max_disp, max_dist;
+    int32_t resp_arc;        // 1: arc response (see ring_response.cuh); 0: sum over the whole circle
 };
 
 // Level-0 pixels of every image of the call.  Passed by value as a kernel
@@ -157,6 +163,9 @@ struct Batch {
     const PairDesc *pairs;
     const int32_t *pyr_tile_base;   // n_levels + 1
     const int32_t *pyr_tile_level;  // level index of each pyramid tile
+    const int32_t *pyr_order;       // pyramid tiles ordered by level number (cascaded pyramid)
+    int32_t pyr_pass_first[kMaxLevels + 1];  // first entry of pyr_order of each level number
+    int32_t pyr_pass;               // -1: one launch over every tile; n: the tiles of level number n
     const int32_t *fast_tile_base;  // n_levels + 1
     const int32_t *fast_tile_level; // level index of each detection tile
     const int32_t *seg_level;       // level index of each segment
@@ -183,6 +192,8 @@ struct Batch {
     uint32_t *err;
     Params prm;
     int32_t skip_max_tiles, skip_max_cells;  // learned cell-skip launch shape
+    int32_t nms_kernel;             // 0: a warp per segment where segments allow, 1: a CTA per segment
+    int32_t fast_ctas_per_sm;       // persistent detection CTAs per SM (0: as many as fit)
     Inputs in;
 };
 

@@ -23,6 +23,7 @@
 #include <cuda.h>
 
 #include "jslam_internal.h"
+#include "ring_response.cuh"
 
 namespace jslam {
 
@@ -67,14 +68,18 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
     __shared__ int s_ya[kPyrRows];
     __shared__ int nsrc;
 
-    const int li = __ldg(b.pyr_tile_level + blockIdx.x);
+    const int tile = b.pyr_pass < 0 ? (int)blockIdx.x : __ldg(b.pyr_order + b.pyr_pass_first[b.pyr_pass] + blockIdx.x);
+    const int li = __ldg(b.pyr_tile_level + tile);
     const LevelDesc &L = b.levels[li];
     const ImageDesc &I = b.images[L.image];
-    const int t = blockIdx.x - b.pyr_tile_base[li];
+    const int t = tile - b.pyr_tile_base[li];
     const int tiles_x = (L.W + kPyrTW - 1) / kPyrTW;
     const int x0 = (t % tiles_x) * kPyrTW, y0 = (t / tiles_x) * kPyrTH;
-    const uint8_t *L0 = b.in.ptr[L.image];
-    const int W0 = I.W0, H0 = I.H0, pitch0 = b.in.pitch[L.image];
+    // level 0 reads the input; deeper levels resample the input, or in the
+    // cascaded pyramid the level above (complete: an earlier launch)
+    const uint8_t *L0 = L.src ? L.src : b.in.ptr[L.image];
+    const int W0 = L.src ? L.src_W : I.W0, H0 = L.src ? L.src_H : I.H0;
+    const int pitch0 = L.src ? L.src_pitch : b.in.pitch[L.image];
     const int W = L.W, H = L.H;
     constexpr int WPR = kPyrCols / 4;
 
@@ -239,11 +244,26 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
     }
 }
 
+const void *pyramid_kernel() { return reinterpret_cast<const void *>(k_pyramid); }
+
 cudaError_t launch_pyramid(const Batch &b, cudaStream_t stream)
 {
     if (b.pyr_tiles == 0) return cudaSuccess;
-    k_pyramid<<<b.pyr_tiles, kPyrThreads, 0, stream>>>(b);
-    return cudaGetLastError();
+    if (b.pyr_pass < 0) {
+        k_pyramid<<<b.pyr_tiles, kPyrThreads, 0, stream>>>(b);
+        return cudaGetLastError();
+    }
+    // cascaded: level number n after n - 1, each launch over every image
+    for (int n = 0; n < kMaxLevels; ++n) {
+        const int tiles = b.pyr_pass_first[n + 1] - b.pyr_pass_first[n];
+        if (tiles == 0) continue;
+        Batch bn = b;
+        bn.pyr_pass = n;
+        k_pyramid<<<tiles, kPyrThreads, 0, stream>>>(bn);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- FAST + FC
@@ -308,12 +328,15 @@ __host__ __device__ inline FastLayout fast_layout(int max_box, int max_px, int m
 // Dynamic shared memory of the bit-sliced kernel: the two tile boxes, the
 // box's bit-planes (max_planes bytes: box rows of (chunks + 1) x 8 words and
 // a 16-byte pad, see bs_row_units), the corner list and keys only for k > 1
-// (k = 1 takes each cell's best corner as it is found), cell states and
-// selections.  The fixed-size parts (corner windows, tile records, staged
-// projections, mbarriers) are static arrays of the kernel.
-constexpr int kBitsWin = 256;
+// (k = 1 takes each cell's best corner as it is found), cell states,
+// selections and the work list of a pass (16-bit item indices; a tile has at
+// most kFastMaxTile rows of 4 items).  The fixed-size parts (corner windows,
+// tile records, staged projections, mbarriers) are static arrays of the
+// kernel.
+constexpr int kBitsWin = 128;
+constexpr int kBitsMaxItems = kFastMaxTile * (kFastMaxTile / 32);
 struct BitsLayout {
-    int buf0, buf1, planes, clist, ckey, has_hi, sel, total;
+    int buf0, buf1, planes, clist, ckey, has_hi, sel, wlist, total;
 };
 __host__ __device__ inline BitsLayout bits_layout(int max_box, int max_px, int max_cells, int k, int max_planes)
 {
@@ -326,6 +349,7 @@ __host__ __device__ inline BitsLayout bits_layout(int max_box, int max_px, int m
     l.ckey = o;   o += k > 1 ? fast_align(max_px * 4, 16) : 0;
     l.has_hi = o; o += fast_align(max_cells, 16);
     l.sel = o;    o += fast_align(max_cells * k * 4, 16);
+    l.wlist = o;  o += kBitsMaxItems * 2;
     l.total = o;
     return l;
 }
@@ -680,6 +704,39 @@ __device__ __forceinline__ uint32_t cell_bits(const uint8_t *st, int px0, int tw
 
 __device__ __forceinline__ int div_small(int v, uint32_t cinv) { return (int)(((uint32_t)v * cinv) >> 16); }
 
+// Bits j of the 32 pixels px0 + j of a tile row that lie inside the level's
+// evaluated columns [plo, phi) (tile coordinates).
+__device__ __forceinline__ uint32_t border_bits(int px0, int plo, int phi)
+{
+    const int lo = min(max(plo - px0, 0), 32), hi = min(max(phi - px0, 0), 32);
+    return (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & (lo >= 32 ? 0u : (0xFFFFFFFFu << lo));
+}
+
+// Work list of a pass of k_fast_bits: appends to wlist (count in *n) every
+// item (row r0 + itm / nch, chunk itm % nch) holding an evaluated pixel whose
+// cell state satisfies keep(state), so that the pass runs full warps over
+// those items only.  Warp-uniform loop; one atomic per warp and round.
+template <typename Keep>
+__device__ __forceinline__ void list_items(uint16_t *wlist, int *n, int items, int nch, uint32_t nchinv, int r0,
+                                           int plo, int phi, const uint8_t *has_hi, int ncx, int tw, int c,
+                                           uint32_t cinv, int lane, int warp, Keep keep)
+{
+    for (int base = warp * 32; base < items; base += kFastThreads) {
+        const int itm = base + lane;
+        bool need = false;
+        if (itm < items) {
+            const int rr = div_small(itm, nchinv), px0 = 32 * (itm - rr * nch);
+            const uint32_t v = border_bits(px0, plo, phi);
+            need = v && (v & cell_bits(has_hi + div_small(r0 + rr, cinv) * ncx, px0, tw, c, cinv, keep));
+        }
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, need);
+        int at = 0;
+        if (lane == 0 && bal) at = atomicAdd(n, __popc(bal));
+        at = __shfl_sync(0xFFFFFFFFu, at, 0);
+        if (need) wlist[at + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)itm;
+    }
+}
+
 // Byte-lane ring test with the cardinal pre-test and the corner table (any
 // P_min, P_max).
 __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
@@ -898,11 +955,17 @@ __global__ void __launch_bounds__(kFastThreads) k_fast_cull(Batch b)
             const int e = clist[i];
             const int py = e >> 7, px = e & 127;
             const uint8_t *p = tbytes + (py + 3) * rowb + (px + 4);
-            const int ic = p[0];
-            int r = 0;
-#pragma unroll
-            for (int q = 0; q < 16; ++q) r += abs((int)p[c_ring_dy[q] * rowb + c_ring_dx[q]] - ic);
             const int cy = div_small(py, cinv), cx = div_small(px, cinv);
+            int r = 0;
+            if (b.prm.resp_arc) {
+                // the threshold the corner was found at: fallback corners lie
+                // in cells without a primary-threshold corner
+                r = ring_arc(p, rowb, has_hi[cy * ncx + cx] == 1 ? I.eps_hi : I.eps_lo, b.prm.p_min, b.prm.p_max);
+            } else {
+                const int ic = p[0];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) r += abs((int)p[c_ring_dy[q] * rowb + c_ring_dx[q]] - ic);
+            }
             const uint32_t inidx = (uint32_t)((py - cy * c) * c + (px - cx * c));
             const uint32_t key = ((uint32_t)r << 16) | (0xFFFFu - inidx);
             const int cell = cy * ncx + cx;
@@ -1011,6 +1074,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
     // per set: corners listed (k > 1), skipped cells, cells open at the
     // start (state 0), open cells that got a primary-threshold corner
     __shared__ int cnt[2][4];
+    __shared__ int s_nlist[2];  // work-list lengths of pass 0 (cells skipped) and pass 1
     __shared__ int s_abort;
     __shared__ uint32_t s_rph;  // thread 0: parity of the next completion of each record barrier (bit s)
     __shared__ __align__(16) uint16_t s_wbuf[kFastThreads / 32][kBitsWin];
@@ -1027,6 +1091,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
     uint32_t *ckey = reinterpret_cast<uint32_t *>(smem + lay.ckey);
     uint8_t *has_hi = smem + lay.has_hi;
     uint32_t *sel = reinterpret_cast<uint32_t *>(smem + lay.sel);
+    uint16_t *wlist = reinterpret_cast<uint16_t *>(smem + lay.wlist);
 
     if ((smem_u32(buf0) | smem_u32(buf1)) & 127u) {
         if (threadIdx.x == 0) atomicOr(b.err, kErrDecode);
@@ -1083,6 +1148,9 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
                 } else { atomicOr(b.err, kErrTimeout); s_abort = 1; }
             }
             cnt[cur ^ 1][0] = cnt[cur ^ 1][1] = cnt[cur ^ 1][2] = cnt[cur ^ 1][3] = 0;
+            // the lists of the previous tile were last read before its closing
+            // barrier; this tile's are built after a barrier that follows this
+            s_nlist[0] = s_nlist[1] = 0;
         }
         uint8_t *const tb = cur ? buf1 : buf0;
         // the box and the projections (every tile waits: the projections
@@ -1159,6 +1227,15 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
                 }
                 bs_transpose(a, z, reinterpret_cast<uint4 *>(planes) + r * ru + 2 * kc);
             }
+            // cells skipped by the proposal: pass 0 runs over the items that
+            // hold a pixel of a cell that is not (states are complete: skip
+            // mode has a barrier after them)
+            if (R.skip && C[1] > 0) {
+                const int plo = max(border - x0, 0), phi = min(W - border - x0, R.tw);
+                list_items(wlist, &s_nlist[0], max(r1 - r0, 0) * nch, nch, (65536u + nch - 1) / nch, r0, plo, phi,
+                           has_hi, ncx, R.tw, c, (uint32_t)R.cinv, lane, warp,
+                           [](uint8_t st) { return st != 2; });
+            }
         }
         }
         __syncthreads();
@@ -1177,30 +1254,39 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
         const int plo = max(border - x0, 0), phi = min(W - border - x0, tw);
         const int r0 = max(border - y0, 0), r1 = min(Hh - border - y0, R.th);
         const int nch = (tw + 31) >> 5, sb = R.delta + 4, ru = bs_row_units(nch);
+        const uint32_t nchinv = (65536u + nch - 1) / nch;  // item / nch by a multiply (item < 2^9)
         const int items = max(r1 - r0, 0) * nch;
         const uint8_t *tbytes = tb + R.delta;  // pixel (x, y) at (y - y0 + 3) * rowb + (x - x0 + 4)
         for (int pass = 0; pass < 2 && !all_skipped; ++pass) {
             const int eps = pass == 0 ? R.eps_hi : R.eps_lo;
             // fallback pass only while an open cell got no corner
             if (pass == 1 && (eps <= 0 || C[3] >= C[2])) break;
-            for (int base = warp * 32; base < items; base += kFastThreads) {
-                const int itm = base + lane;
+            // pass 0 covers every item, or the listed ones when cells are
+            // skipped; pass 1 lists the items holding a pixel of a cell still
+            // without a corner (cell states are final after pass 0's barrier)
+            const bool listed = pass == 1 || some_skipped;
+            if (pass == 1) {
+                list_items(wlist, &s_nlist[1], items, nch, nchinv, r0, plo, phi, has_hi, ncx, tw, c, cinv, lane, warp,
+                           [](uint8_t st) { return st == 0; });
+                __syncthreads();
+            }
+            const int n_work = listed ? s_nlist[pass] : items;
+            for (int base = warp * 32; base < n_work; base += kFastThreads) {
+                const int w = base + lane;
                 uint32_t bits = 0;
                 int py = 0, px0 = 0;
-                if (itm < items) {
-                    const int rr = itm / nch, m = itm - rr * nch;
+                if (w < n_work) {
+                    const int itm = listed ? (int)wlist[w] : w;
+                    const int rr = div_small(itm, nchinv), m = itm - rr * nch;
                     py = r0 + rr;
                     px0 = 32 * m;
-                    const int lo = min(max(plo - px0, 0), 32), hi = min(max(phi - px0, 0), 32);
-                    uint32_t valid = (hi >= 32 ? 0xFFFFFFFFu : ((1u << hi) - 1u)) & (lo >= 32 ? 0u : (0xFFFFFFFFu << lo));
+                    uint32_t valid = border_bits(px0, plo, phi);
                     const uint8_t *strow = has_hi + div_small(py, cinv) * ncx;
                     if (pass == 1 && valid)  // only cells without a corner (and not skipped)
                         valid &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st == 0; });
-                    if (valid) {
-                        bits = bs_corners(planes, ru, py, m, sb, eps) & valid;
-                        if (bits && pass == 0 && some_skipped)
-                            bits &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st != 2; });
-                    }
+                    else if (some_skipped && valid)  // not in a skipped cell
+                        valid &= cell_bits(strow, px0, tw, c, cinv, [](uint8_t st) { return st != 2; });
+                    if (valid) bits = bs_corners(planes, ru, py, m, sb, eps) & valid;
                 }
                 // the warp's corners in order, scored through windows of kBitsWin entries
                 const int nb = __popc(bits);
@@ -1245,7 +1331,8 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
                         const int e = wbuf[i];
                         const int cy_ = e >> 7, cx_ = e & 127;
                         const uint8_t *pp = tbytes + (cy_ + 3) * rowb + (cx_ + 4);
-                        const int r = ring_sad(pp, rowb);
+                        const int r = b.prm.resp_arc ? ring_arc(pp, rowb, eps, b.prm.p_min, b.prm.p_max)
+                                                     : ring_sad(pp, rowb);
                         const int ccy = div_small(cy_, cinv), ccx = div_small(cx_, cinv);
                         const uint32_t inidx = (uint32_t)((cy_ - ccy * c) * c + (cx_ - ccx * c));
                         const uint32_t key = ((uint32_t)r << 16) | (0xFFFFu - inidx);
@@ -1318,10 +1405,19 @@ cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream)
         cached_smem = b.fast_smem;
         cached_bits = b.fast_bits;
     }
-    const int grid = std::min(b.fast_tiles, std::max(1, cached_blocks) * n_sm);
+    int per_sm = std::max(1, cached_blocks);
+    if (b.fast_ctas_per_sm > 0) per_sm = std::min(per_sm, b.fast_ctas_per_sm);
+    const int grid = std::min(b.fast_tiles, per_sm * n_sm);
     if (b.fast_bits) k_fast_bits<<<grid, kFastThreads, b.fast_smem, stream>>>(b);
     else k_fast_cull<<<grid, kFastThreads, b.fast_smem, stream>>>(b);
     return cudaGetLastError();
+}
+
+// Detection CTAs of this batch's launch that fit on one SM at once.
+cudaError_t detect_ctas_that_fit(const Batch &b, int *per_sm)
+{
+    return b.fast_bits ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_fast_bits, kFastThreads, b.fast_smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_fast_cull, kFastThreads, b.fast_smem);
 }
 
 cudaError_t configure_kernels()

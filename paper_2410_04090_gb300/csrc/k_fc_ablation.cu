@@ -18,6 +18,7 @@
 //            response << 16 | (0xFFFF - index in cell) (0 for no corner), so
 //            ties resolve as in the fused kernel and the oracle.
 #include "jslam_internal.h"
+#include "ring_response.cuh"
 
 namespace jslam {
 
@@ -51,7 +52,7 @@ __global__ void __launch_bounds__(256) k_crf(Batch b, uint16_t *crf, const uint6
         }
         const uint32_t cb = (__ldg(b.corner_lut + (mb >> 5)) >> (mb & 31)) & 1u;
         const uint32_t cd = (__ldg(b.corner_lut + (md >> 5)) >> (md & 31)) & 1u;
-        if (cb | cd) out = (uint16_t)r;
+        if (cb | cd) out = (uint16_t)(b.prm.resp_arc ? ring_arc(p, L.pitch, eps, b.prm.p_min, b.prm.p_max) : r);
     }
     crf[off[li] + pix] = out;
 }

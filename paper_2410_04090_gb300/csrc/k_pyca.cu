@@ -182,7 +182,9 @@ cudaError_t launch_pfa_nms(const Batch &b, cudaStream_t stream)
 {
     if (b.n_segments == 0) return cudaSuccess;
     constexpr int per = kNmsThreads / 32;
-    if (b.max_segment <= 32) {
+    if (b.nms_kernel == 1) {
+        k_pfa_nms<<<b.n_segments, kNmsThreads, 0, stream>>>(b);
+    } else if (b.max_segment <= 32) {
         k_pfa_nms_warp<1><<<(b.n_segments + per - 1) / per, kNmsThreads, 0, stream>>>(b);
     } else if (b.max_segment <= 64) {
         k_pfa_nms_warp<2><<<(b.n_segments + per - 1) / per, kNmsThreads, 0, stream>>>(b);
@@ -223,8 +225,15 @@ __device__ __forceinline__ int block_excl_scan(int v, int *ws, int *total)
     return pre + x - v;
 }
 
+// Cap priorities of the first kFinPrioCache canonical survivors, kept in
+// shared memory for the four radix passes and the compaction (32 KB; two
+// CTAs still fit an SM).  Images with more survivors read the rest through
+// their slots.
+constexpr int kFinPrioCache = 8192;
+
 __global__ void __launch_bounds__(kFinThreads, 2) k_pfa_finalize(Batch b)
 {
+    __shared__ uint32_t s_prio[kFinPrioCache];
     __shared__ int ws[32];
     __shared__ int hist[256];
     __shared__ int sh_digit, sh_need;
@@ -276,6 +285,9 @@ __global__ void __launch_bounds__(kFinThreads, 2) k_pfa_finalize(Batch b)
         const uint32_t K = b.slot_k[gs];
         return ((K >> 16) << 27) | ((K & 0xFFFFu) << 12) | (b.slots[gs] >> 16);
     };
+    for (int g = threadIdx.x; g < min(S, kFinPrioCache); g += kFinThreads) s_prio[g] = prio(g);
+    __syncthreads();
+    auto prio_c = [&](int g) -> uint32_t { return g < kFinPrioCache ? s_prio[g] : prio(g); };
     const bool capped = S > I.max_feats;
     uint32_t T = 0;
     int quota = 0;
@@ -286,18 +298,39 @@ __global__ void __launch_bounds__(kFinThreads, 2) k_pfa_finalize(Batch b)
             for (int i = threadIdx.x; i < 256; i += kFinThreads) hist[i] = 0;
             __syncthreads();
             for (int g = threadIdx.x; g < S; g += kFinThreads) {
-                const uint32_t P = prio(g);
+                const uint32_t P = prio_c(g);
                 if ((P & mask) == prefix) atomicAdd(&hist[(P >> sh) & 255u], 1);
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                int cum = 0, d = 255;
-                for (; d > 0; --d) {
-                    if (cum + hist[d] >= need) break;
-                    cum += hist[d];
+            // the largest digit d whose count, added to the counts of the
+            // larger digits, reaches `need` (which never exceeds the total):
+            // lane l holds digits 255 - 8 l down to 248 - 8 l, a warp scan
+            // gives the counts above each lane, and the one lane where the
+            // running count crosses `need` walks its eight digits
+            if (threadIdx.x < 32) {
+                const int lane = threadIdx.x;
+                int cnt8[8], s8 = 0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    cnt8[j] = hist[255 - 8 * lane - j];
+                    s8 += cnt8[j];
                 }
-                sh_digit = d;
-                sh_need = need - cum;
+                int incl = s8;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                int cum = incl - s8;
+                if (cum < need && incl >= need) {
+                    int j = 0;
+                    for (; j < 7; ++j) {
+                        if (cum + cnt8[j] >= need) break;
+                        cum += cnt8[j];
+                    }
+                    sh_digit = 255 - 8 * lane - j;
+                    sh_need = need - cum;
+                }
             }
             __syncthreads();
             prefix |= (uint32_t)sh_digit << sh;
@@ -317,7 +350,7 @@ __global__ void __launch_bounds__(kFinThreads, 2) k_pfa_finalize(Batch b)
     for (int base = 0; base < S; base += kFinThreads) {
         const int g = base + threadIdx.x;
         const bool valid = g < S;
-        const uint32_t P = valid ? prio(g) : 0u;
+        const uint32_t P = valid ? prio_c(g) : 0u;
         int tot;
         const int tie_rank = carry_tie + block_excl_scan<kFinThreads>(valid && capped && P == T, ws, &tot);
         carry_tie += tot;
@@ -348,6 +381,7 @@ __global__ void __launch_bounds__(kFinThreads, 2) k_pfa_finalize(Batch b)
         for (int l = kMaxLevels - 1; l >= 0; --l) lstart[l] = min(lstart[l], lstart[l + 1]);
         for (int l = 0; l <= kMaxLevels; ++l) I.level_start[l] = lstart[l];
         *I.count = keep;
+        *I.count_hdr = keep;
     }
 }
 

@@ -36,7 +36,8 @@ class Config(C.Structure):
                 ("max_feats", C.c_int32), ("max_pairs", C.c_int32), ("fast_thresh_lo", C.c_int32),
                 ("p_min", C.c_int32), ("p_max", C.c_int32), ("k_per_cell", C.c_int32),
                 ("nms_q", C.c_int32), ("border", C.c_int32), ("max_disp", C.c_int32),
-                ("row_band_px", C.c_int32), ("match_max_dist", C.c_int32), ("pfa_rule", C.c_int32)]
+                ("row_band_px", C.c_int32), ("match_max_dist", C.c_int32), ("pfa_rule", C.c_int32),
+                ("response_mode", C.c_int32), ("pyramid_mode", C.c_int32)]
 
 
 class Image(C.Structure):
@@ -50,7 +51,11 @@ class StereoJob(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("tile_w_px", C.c_int32), ("tile_h_px", C.c_int32)]
+    _fields_ = [("tile_w_px", C.c_int32), ("tile_h_px", C.c_int32), ("nms_kernel", C.c_int32),
+                ("detect_ctas_per_sm", C.c_int32)]
+
+    def as_tuple(self) -> tuple:
+        return self.tile_w_px, self.tile_h_px, self.nms_kernel, self.detect_ctas_per_sm
 
 
 class SkipView(C.Structure):
@@ -96,7 +101,9 @@ SYMBOLS = ("jslam_default_config", "jslam_create", "jslam_extract", "jslam_extra
            "jslam_download", "jslam_result_view", "jslam_destroy", "jslam_status_str", "jslam_pattern_table",
            "jslam_level_geometry", "jslam_project", "jslam_match_band", "jslam_enable_stage_timing",
            "jslam_stage_times", "jslam_pfa_scores_static", "jslam_corner_table", "jslam_set_tuning",
-           "jslam_autotune", "jslam_graph_capture", "jslam_graph_launch", "jslam_set_skip_model",
+           "jslam_autotune", "jslam_autotune_cached", "jslam_tune_key", "jslam_tune_cache_get",
+           "jslam_tune_cache_put", "jslam_graph_capture", "jslam_graph_launch", "jslam_graph_launch_jobs",
+           "jslam_set_skip_model",
            "jslam_get_skip_view", "jslam_result_range", "jslam_download_range", "jslam_refine_matches",
            "jslam_get_refined", "jslam_result_refined_view", "jslam_track", "jslam_fc_ablation",
            "jslam_fc_ablation_view", "jslam_fc_ablation_times", "jslam_crf_view", "jslam_selftest_wait")
@@ -185,10 +192,22 @@ def lib():
         L.jslam_set_tuning.restype = st
         L.jslam_autotune.argtypes = [C.c_void_p, C.POINTER(StereoJob), C.c_int32, C.POINTER(Tuning)]
         L.jslam_autotune.restype = st
+        L.jslam_autotune_cached.argtypes = [C.c_void_p, C.POINTER(StereoJob), C.c_int32, C.c_char_p,
+                                            C.POINTER(Tuning), C.POINTER(C.c_int32)]
+        L.jslam_autotune_cached.restype = st
+        L.jslam_tune_key.argtypes = [C.c_char_p, C.c_int32, C.POINTER(Config), C.POINTER(StereoJob), C.c_int32,
+                                     C.c_char_p, C.c_size_t]
+        L.jslam_tune_key.restype = st
+        L.jslam_tune_cache_get.argtypes = [C.c_char_p, C.c_char_p, C.POINTER(Tuning), C.POINTER(C.c_int32)]
+        L.jslam_tune_cache_get.restype = st
+        L.jslam_tune_cache_put.argtypes = [C.c_char_p, C.c_char_p, C.POINTER(Tuning), C.c_float]
+        L.jslam_tune_cache_put.restype = st
         L.jslam_graph_capture.argtypes = [C.c_void_p, C.POINTER(StereoJob), C.c_int32]
         L.jslam_graph_capture.restype = st
         L.jslam_graph_launch.argtypes = [C.c_void_p]
         L.jslam_graph_launch.restype = st
+        L.jslam_graph_launch_jobs.argtypes = [C.c_void_p, C.POINTER(StereoJob), C.c_int32]
+        L.jslam_graph_launch_jobs.restype = st
         L.jslam_corner_table.argtypes = [C.c_int32, C.c_int32, C.c_void_p]
         L.jslam_corner_table.restype = st
         L.jslam_enable_stage_timing.argtypes = [C.c_void_p, C.c_int32]
@@ -239,6 +258,36 @@ def corner_table(p_min: int = 9, p_max: int = 13) -> np.ndarray:
 
 def match_band(level: int, scale: float, row_band_px: int) -> int:
     return lib().jslam_match_band(level, scale, row_band_px)
+
+
+# ------------------------------------------------------------ tuning cache (host only)
+
+def tune_key(gpu_name: str, sm_count: int, config: dict, jobs) -> str:
+    """Key of a batch in the tuning cache (jslam_tune_key; no device work).
+    `config` holds jslam_config fields (defaults for the rest); `jobs` are
+    Job objects whose images may be numpy arrays."""
+    cfg = Config()
+    lib().jslam_default_config(C.byref(cfg))
+    for k, v in config.items():
+        setattr(cfg, k, v)
+    pb = PreparedBatch(jobs)
+    buf = C.create_string_buffer(1 << 16)
+    _check(lib().jslam_tune_key(gpu_name.encode(), sm_count, C.byref(cfg), pb.array, pb.n, buf, len(buf)),
+           "jslam_tune_key")
+    return buf.value.decode()
+
+
+def tune_cache_get(path: str, key: str):
+    """The cached pick (tile_w_px, tile_h_px, nms_kernel, detect_ctas_per_sm) or None."""
+    t, found = Tuning(), C.c_int32(0)
+    _check(lib().jslam_tune_cache_get(os.fsencode(path), key.encode(), C.byref(t), C.byref(found)),
+           "jslam_tune_cache_get")
+    return t.as_tuple() if found.value else None
+
+
+def tune_cache_put(path: str, key: str, tuning, stage_ms: float = 0.0) -> None:
+    t = Tuning(*tuning)
+    _check(lib().jslam_tune_cache_put(os.fsencode(path), key.encode(), C.byref(t), stage_ms), "jslam_tune_cache_put")
 
 
 # ------------------------------------------------------------ no-allocation PFA scores
@@ -482,24 +531,42 @@ class Frontend:
         return {"logits": _device_view(v.logits, (v.h8, v.w8), np.float32, self.device),
                 "skip": _device_view(v.skip, (v.cells_y, v.cells_x), np.uint8, self.device)}
 
-    def set_tuning(self, tile_w_px: int, tile_h_px: int):
-        t = Tuning(tile_w_px, tile_h_px)
+    def set_tuning(self, tile_w_px: int, tile_h_px: int, nms_kernel: int = 0, detect_ctas_per_sm: int = 0):
+        t = Tuning(tile_w_px, tile_h_px, nms_kernel, detect_ctas_per_sm)
         _check(lib().jslam_set_tuning(self._h, C.byref(t)), "jslam_set_tuning")
 
-    def autotune(self, jobs) -> tuple:
+    def autotune(self, jobs, cache: str | None = None) -> tuple:
+        """Tune the launch shapes on `jobs`; returns (tile_w_px, tile_h_px,
+        nms_kernel, detect_ctas_per_sm).  With `cache` (a JSON file path) a
+        stored pick for this GPU and batch is applied without tuning, and a new
+        pick is stored; `last_tune_hit` tells which happened."""
         pb = jobs if isinstance(jobs, PreparedBatch) else PreparedBatch(jobs)
         self._keep = pb
         t = Tuning()
-        _check(lib().jslam_autotune(self._h, pb.array, pb.n, C.byref(t)), "jslam_autotune")
-        return t.tile_w_px, t.tile_h_px
+        if cache is None:
+            _check(lib().jslam_autotune(self._h, pb.array, pb.n, C.byref(t)), "jslam_autotune")
+            self.last_tune_hit = None
+        else:
+            hit = C.c_int32(0)
+            _check(lib().jslam_autotune_cached(self._h, pb.array, pb.n, os.fsencode(cache), C.byref(t),
+                                               C.byref(hit)), "jslam_autotune_cached")
+            self.last_tune_hit = bool(hit.value)
+        return t.as_tuple()
 
     def graph_capture(self, jobs):
         pb = jobs if isinstance(jobs, PreparedBatch) else PreparedBatch(jobs)
         self._graph_keep = pb
         _check(lib().jslam_graph_capture(self._h, pb.array, pb.n), "jslam_graph_capture")
 
-    def graph_launch(self):
-        _check(lib().jslam_graph_launch(self._h), "jslam_graph_launch")
+    def graph_launch(self, jobs=None):
+        """Replay the captured graph; with `jobs` (the captured batch shape,
+        device images), on those frames instead of the captured ones."""
+        if jobs is None:
+            _check(lib().jslam_graph_launch(self._h), "jslam_graph_launch")
+            return
+        pb = jobs if isinstance(jobs, PreparedBatch) else PreparedBatch(jobs)
+        self._keep = pb
+        _check(lib().jslam_graph_launch_jobs(self._h, pb.array, pb.n), "jslam_graph_launch_jobs")
 
     def sync(self):
         _check(lib().jslam_sync(self._h), "jslam_sync")

@@ -19,7 +19,8 @@ def frontend_for(J, p, max_width=1920, max_height=1080, max_pairs=16, max_feats=
                       max_feats=max_feats or max(p.max_feats, 4000), max_pairs=max_pairs,
                       fast_thresh_lo=p.fast_thresh_lo, p_min=p.p_min, p_max=p.p_max,
                       k_per_cell=p.k_per_cell, nms_q=p.nms_q, border=p.border, max_disp=p.max_disp,
-                      row_band_px=p.row_band_px, match_max_dist=p.match_max_dist, pfa_rule=p.pfa_rule)
+                      row_band_px=p.row_band_px, match_max_dist=p.match_max_dist, pfa_rule=p.pfa_rule,
+                      response_mode=p.response_mode, pyramid_mode=p.pyramid_mode)
 
 
 def gpu_pair(J, fe, left, right, p, host=False):

@@ -13,11 +13,13 @@ PAST = [dict(max_pairs=0), dict(max_pairs=129), dict(max_width=0), dict(max_widt
         dict(fast_thresh_lo=255), dict(p_min=0), dict(p_max=17), dict(p_min=14, p_max=13), dict(k_per_cell=0),
         dict(k_per_cell=9), dict(nms_q=0), dict(nms_q=2), dict(nms_q=9), dict(border=15), dict(border=513),
         dict(max_disp=-1), dict(max_disp=4097), dict(row_band_px=-1), dict(row_band_px=65),
-        dict(match_max_dist=-1), dict(pfa_rule=-1), dict(pfa_rule=2)]
+        dict(match_max_dist=-1), dict(pfa_rule=-1), dict(pfa_rule=2), dict(response_mode=-1),
+        dict(response_mode=2), dict(pyramid_mode=-1), dict(pyramid_mode=2)]
 AT = [dict(max_pairs=1), dict(max_pairs=128), dict(max_width=4096, max_height=4096), dict(max_levels=8),
       dict(max_feats=1 << 20), dict(fast_thresh_lo=254), dict(p_min=1, p_max=16), dict(k_per_cell=8),
       dict(nms_q=1), dict(nms_q=7), dict(border=16), dict(border=512), dict(max_disp=0), dict(max_disp=4096),
-      dict(row_band_px=64), dict(match_max_dist=0), dict(pfa_rule=1)]
+      dict(row_band_px=64), dict(match_max_dist=0), dict(pfa_rule=1), dict(response_mode=1),
+      dict(pyramid_mode=1)]
 
 
 def _create(**kw):

@@ -44,6 +44,15 @@ def test_path_bytes_per_pair():
     assert two == pytest.approx((want - 48 * 1000 + 2 * (p2[0] + (A2 - p2[0]) + A2) + 48 * 2400) / 2)
 
 
+def test_algorithmic_ops_per_pixel():
+    """Eq. 1-3 in scalar form: 16 differences, 2 x 16 labels, 2 x 16 mask bits
+    and 3 for the table test per pixel; 31 + 1 more per corner (response and
+    cell maximum)."""
+    assert bench.alg_ops_per_pixel(0.0) == 83
+    assert bench.alg_ops_per_pixel(0.5) == pytest.approx(83 + 16)
+    assert "83" in bench.ALG_OPS_DEFINITION
+
+
 def test_code_hash_ignores_comments_and_whitespace(tmp_path):
     a = tmp_path / "a.cu"
     b = tmp_path / "b.cu"
@@ -72,7 +81,7 @@ def test_emitted_line_carries_the_contract(monkeypatch, capsys):
     clocks = types.SimpleNamespace(summary=lambda: {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []})
     e2e = {"value": 43000.0, "unit": bench.UNIT, "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1}
     bench.emit(args, 1, len(pairs), 47800.0, 2.09 * 50, {"graph_streams4": 47800.0},
-               {k: v * 50 for k, v in stage.items()}, [2000] * 4, pairs, params, lo, e2e, clocks, (128, 128),
+               {k: v * 50 for k, v in stage.items()}, [2000] * 4, pairs, params, lo, e2e, clocks, (128, 128, 0, 0),
                None, 0)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -91,3 +100,5 @@ def test_emitted_line_carries_the_contract(monkeypatch, capsys):
     assert roof["traffic"] == bench.profile_number(prof, "dram_bytes_per_launch_full_workload")
     assert roof["hbm"]["algorithmic_bytes_per_launch"] == bench.algorithmic_bytes("detect", pairs, params, [1])
     assert line["path_hbm"]["frac"] > 0 and line["cpu_baseline"] is None
+    assert line["path_hbm"]["by_mode"]["graph_streams4"]["frac"] == line["path_hbm"]["frac"]
+    assert line["config"]["tuning"] == {"nms_kernel": 0, "detect_ctas_per_sm": 0, "source": "--tile"}

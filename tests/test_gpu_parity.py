@@ -415,6 +415,117 @@ def _check_batch(J, oracle, fe, pairs, specs):
         compare_matches(J.to_numpy(fe.matches(i)), om, f"pair {i}")
 
 
+def test_graph_replay_on_new_device_frames(J, oracle):
+    """jslam_graph_launch_jobs: the captured graph replayed on new device
+    frames (new tensors, not the captured buffers), two replays in flight
+    before one sync, each followed by a download of its results; then the
+    refusals: another batch shape, a host image, a rebuilt plan."""
+    import torch
+    specs = scenes.MIXED_STREAMS[::4]  # one stream of each size
+    fe = frontend_for(J, params_from(oracle, fast_thresh_lo=7), max_pairs=4, stream=torch.cuda.Stream())
+    _, jobs0 = _mixed_streams(J, specs, 0)
+    fe.graph_capture(jobs0)
+    frames = {f: _mixed_streams(J, specs, f) for f in (1, 2)}
+    torch.cuda.synchronize()  # the uploads (torch's stream) land before the context's stream reads them
+    total, offs = fe.result_range(0, len(specs))
+    blocks = {}
+    for f, (_, jobs) in frames.items():  # no sync between the replays
+        fe.graph_launch(jobs)
+        blocks[f] = torch.empty(total, dtype=torch.uint8).pin_memory()
+        fe.download_range(0, len(specs), blocks[f])
+    fe.sync()
+    _check_batch(J, oracle, fe, frames[2][0], specs)  # device views: the last replay
+    for f, (pairs, _) in frames.items():
+        for i, (pr, sp) in enumerate(zip(pairs, specs)):
+            p = params_from(oracle, levels=sp["levels"], max_feats=sp["max_feats"], fast_thresh_lo=7)
+            ol, orr, om = oracle.extract_pair(pr.left, pr.right, p)
+            blk = blocks[f][offs[i]:].clone()
+            compare_keypoints(fe.result_view(i, blk, 0), ol, f"frame {f} pair {i} left")
+            compare_keypoints(fe.result_view(i, blk, 1), orr, f"frame {f} pair {i} right")
+    # refusals
+    _, jobs1 = frames[1]
+    with pytest.raises(J.JslamError) as e:
+        fe.graph_launch(jobs1[:3])  # fewer pairs
+    assert e.value.status == J.ERR_ARG
+    other = list(jobs1)
+    other[0] = J.Job(other[0].left, other[0].right, other[0].levels - 1, 1.2, 20, 32, other[0].max_feats)
+    with pytest.raises(J.JslamError) as e:
+        fe.graph_launch(other)  # another depth
+    assert e.value.status == J.ERR_ARG
+    host = list(jobs1)
+    host[1] = J.Job(other[1].left.cpu().numpy(), other[1].right, other[1].levels, 1.2, 20, 32, other[1].max_feats)
+    with pytest.raises(J.JslamError) as e:
+        fe.graph_launch(host)  # a host image
+    assert e.value.status == J.ERR_ARG
+    fe.extract_batch(jobs1[:2])  # another batch shape rebuilds the plan: the graph is stale
+    with pytest.raises(J.JslamError) as e:
+        fe.graph_launch()
+    assert e.value.status == J.ERR_STATE
+    with pytest.raises(J.JslamError) as e:
+        fe.graph_launch(jobs1)
+    assert e.value.status == J.ERR_STATE
+    fe.sync()
+    fe.close()
+
+
+def _batch_outputs(J, fe, n):
+    return [(J.to_numpy(fe.keypoints(i, 0)), J.to_numpy(fe.keypoints(i, 1)), J.to_numpy(fe.matches(i)))
+            for i in range(n)]
+
+
+def test_every_tuning_gives_identical_results(J, oracle):
+    """Every launch shape the tuner can pick -- detection tile, persistent
+    CTAs per SM, NMS kernel -- gives the same keypoints, descriptors and
+    matches, bit for bit (the default's equal the oracle's)."""
+    import torch
+    specs = scenes.MIXED_STREAMS[::4]
+    fe = frontend_for(J, params_from(oracle, fast_thresh_lo=7), max_pairs=4)
+    pairs, jobs = _mixed_streams(J, specs, 0)
+    torch.cuda.synchronize()
+    fe.extract_batch(jobs); fe.match(); fe.sync()
+    _check_batch(J, oracle, fe, pairs, specs)
+    ref = _batch_outputs(J, fe, len(specs))
+    for tw, th in ((128, 64), (128, 32), (128, 128), (64, 64), (64, 128), (96, 48)):
+        for nms in (0, 1):
+            for ctas in (0, 1, 2):
+                fe.set_tuning(tw, th, nms, ctas)
+                fe.extract_batch(jobs); fe.match(); fe.sync()
+                for i, (a, b) in enumerate(zip(ref, _batch_outputs(J, fe, len(specs)))):
+                    what = f"tile {tw}x{th} nms {nms} ctas {ctas} pair {i}"
+                    for side in (0, 1):
+                        assert a[side]["count"] == b[side]["count"], what
+                        for f in ("x", "y", "X", "Y", "level", "response", "k_levels", "k_resp", "angle_bin",
+                                  "desc", "angle"):
+                            assert np.array_equal(a[side][f], b[side][f]), (what, side, f)
+                    for f in ("right_idx", "disparity", "dist"):
+                        assert np.array_equal(a[2][f], b[2][f]), (what, f)
+    fe.close()
+
+
+def test_autotune_cache_hits_on_a_new_context(J, oracle, tmp_path):
+    import json
+    import torch
+    specs = scenes.MIXED_STREAMS[::4]
+    pairs, jobs = _mixed_streams(J, specs, 0)
+    torch.cuda.synchronize()
+    path = str(tmp_path / "tune.json")
+    fe = frontend_for(J, params_from(oracle, fast_thresh_lo=7), max_pairs=4)
+    pick = fe.autotune(jobs, cache=path)
+    assert fe.last_tune_hit is False
+    entries = json.load(open(path))["entries"]
+    assert len(entries) == 1 and list(entries.values())[0]["stage_ms"] > 0
+    fe.close()
+    fe2 = frontend_for(J, params_from(oracle, fast_thresh_lo=7), max_pairs=4)
+    assert fe2.autotune(jobs, cache=path) == pick and fe2.last_tune_hit is True
+    fe2.extract_batch(jobs); fe2.match(); fe2.sync()
+    _check_batch(J, oracle, fe2, pairs, specs)
+    fe2.close()
+    fe3 = frontend_for(J, params_from(oracle, fast_thresh_lo=7, k_per_cell=2), max_pairs=4)
+    fe3.autotune(jobs, cache=path)  # another configuration: a miss, a second entry
+    assert fe3.last_tune_hit is False and len(json.load(open(path))["entries"]) == 2
+    fe3.close()
+
+
 def test_mixed_sixteen_streams(J, oracle):
     """The mixed multi-stream batch: 4 streams each of 640x480 (4 levels),
     752x480 (5), 1241x376 (6) and 1920x1080 (8), autotuned, in one launch set."""
@@ -422,7 +533,7 @@ def test_mixed_sixteen_streams(J, oracle):
     fe = frontend_for(J, params_from(oracle, fast_thresh_lo=7), max_pairs=16)
     pairs, jobs = _mixed_streams(J, specs, 0)
     tile = fe.autotune(jobs)
-    assert tile[0] in (64, 128) and tile[1] in (32, 64, 128)
+    assert tile[0] in (64, 128) and tile[1] in (32, 64, 128) and tile[2] in (0, 1) and 0 <= tile[3] <= 8
     fe.extract_batch(jobs)
     fe.match()
     fe.sync()

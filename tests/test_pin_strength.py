@@ -252,6 +252,31 @@ MUTANTS = [
      "int ok = bd <= max_dist && (sd == 0x7fffffff || 10 * bd <= 8 * sd);", 0),
     ("track_second_not_updated", "if (d < bd) { sd = bd; bd = d; best = k; }", "if (d < bd) { bd = d; best = k; }", 0),
     ("track_window_unscaled", "volatile float r = radius * zf;", "volatile float r = radius;", 0),
+    # the arc response (alternative reading of the Sec. III response)
+    ("arc_positions_shorter_runs", "while (len < n && ((mask >> ((start + len) % 16)) & 1u)) ++len;",
+     "while (len < n - 1 && ((mask >> ((start + len) % 16)) & 1u)) ++len;", 0),
+    ("arc_positions_skip_wrap", "for (int32_t j = 0; j < n; ++j) on |= 1u << ((start + j) % 16);",
+     "for (int32_t j = 0; j < n; ++j) on |= 1u << ((start + j) & 7);", 0),
+    ("arc_response_no_eps", "if ((on >> k) & 1u) sum += (d[k] < 0 ? -d[k] : d[k]) - eps;",
+     "if ((on >> k) & 1u) sum += (d[k] < 0 ? -d[k] : d[k]);", 0),
+    ("arc_response_sums_polarities", "if (sum > best) best = sum;", "best += sum;", 0),
+    ("arc_response_ignores_p_max", "if (n < p_min || n > p_max) continue;", "if (n < p_min) continue;", 0),
+    ("fast_arc_dark_not_strict", "if (d[k] < -eps) Bd |= 1u << k;", "if (d[k] <= -eps) Bd |= 1u << k;", 0),
+    ("fast_arc_centre_shifted", "int32_t ic = img[(size_t)y * pitch + x];",
+     "int32_t ic = img[(size_t)y * pitch + x + 1];", 1),
+    ("arc_fallback_ranked_by_primary", "if (!hi[q]) resp[q] = resp_arc[q];", "if (hi[q]) resp[q] = resp_arc[q];", 0),
+    ("arc_mode_keeps_circle_sad",
+     "or_fast_arc(raw[n], W[n], H[n], W[n], p->fast_thresh, p->p_min, p->p_max, p->border, hi, resp);",
+     "or_fast(raw[n], W[n], H[n], W[n], p->fast_thresh, p->p_min, p->p_max, p->border, hi, resp);", 0),
+    # the cascaded pyramid (alternative reading of the resampling)
+    ("cascade_from_level_zero",
+     "or_pyramid_level(raw[n - 1], W[n - 1], H[n - 1], W[n - 1], p->scale, 1, raw[n], W[n], H[n], W[n]);",
+     "or_pyramid_level(raw[0], W[0], H[0], W[0], p->scale, 1, raw[n], W[n], H[n], W[n]);", 0),
+    ("cascade_by_zeta_n",
+     "or_pyramid_level(raw[n - 1], W[n - 1], H[n - 1], W[n - 1], p->scale, 1, raw[n], W[n], H[n], W[n]);",
+     "or_pyramid_level(raw[n - 1], W[n - 1], H[n - 1], W[n - 1], p->scale, n, raw[n], W[n], H[n], W[n]);", 0),
+    ("mode_check_accepts_2", "if (p->response_mode < 0 || p->response_mode > 1 || p->pyramid_mode < 0 || p->pyramid_mode > 1) return -1;",
+     "if (p->response_mode < 0 || p->response_mode > 2 || p->pyramid_mode < 0 || p->pyramid_mode > 2) return -1;", 0),
 ]
 
 # Mutants that change no output over the oracle's domain (checked below):
