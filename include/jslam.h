@@ -164,7 +164,9 @@ jslam_status jslam_refine_matches(jslam_ctx *ctx, int32_t half_window, int32_t s
  * another candidate exists, 10 best <= 9 second (ratio 0.9 against the
  * second-smallest distance).  Writes out_idx (canonical keypoint index, -1
  * none or rejected) and out_dist (best distance, 0xFFFF: no candidate),
- * caller-owned device arrays of n entries.  Levels >= 8 have no candidates.
+ * caller-owned device arrays of n entries.  The band is clipped to the
+ * frame's levels, so a query one level past the deepest meets that level and
+ * deeper queries meet none.
  * Enqueued on the context stream.  JSLAM_ERR_ARG for bad sizes, pointers,
  * radius (< 0) or max_dist (outside 0..256); JSLAM_ERR_STATE before an
  * extraction; n == 0 returns JSLAM_OK. */

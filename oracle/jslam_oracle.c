@@ -931,7 +931,8 @@ void or_track(const or_keypoints *Kf, float scale, const float *u, const float *
               int32_t *idx_out, uint16_t *dist_out)
 {
     for (int32_t q = 0; q < n; ++q) {
-        if (lvl[q] >= OR_MAX_LEVELS) { idx_out[q] = -1; dist_out[q] = 0xFFFF; continue; }
+        /* the band n - 1 .. n + 1 holds only the frame's levels: a query one
+         * level past the deepest still meets that level, deeper ones none */
         float zf = (float)or_level_scale(scale, lvl[q]);
         volatile float r = radius * zf;  /* one float rounding, no contraction */
         int32_t best = -1, bd = 0x7fffffff, sd = 0x7fffffff;

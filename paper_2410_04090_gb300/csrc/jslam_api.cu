@@ -1025,7 +1025,7 @@ jslam_status jslam_track(jslam_ctx *ctx, int32_t pair, int32_t side, const float
     a.n = n;
     a.max_dist = max_dist;
     a.radius = radius;
-    for (int l = 0; l < kMaxLevels; ++l) a.zeta_f[l] = static_cast<float>(zeta_pow(ctx->pair_scale[pair], l));
+    for (int l = 0; l <= kMaxLevels; ++l) a.zeta_f[l] = static_cast<float>(zeta_pow(ctx->pair_scale[pair], l));
     a.u = u; a.v = v; a.level = level; a.desc = desc;
     a.out_idx = out_idx; a.out_dist = out_dist;
     const NvtxRange range("jslam track");

@@ -211,7 +211,7 @@ cudaError_t launch_refine(const Batch &b, int w, int L, double bf, cudaStream_t 
 struct TrackArgs {
     int32_t image, n, max_dist;
     float radius;
-    float zeta_f[kMaxLevels];  // zeta^n rounded to float
+    float zeta_f[kMaxLevels + 1];  // zeta^n rounded to float, n = 0..kMaxLevels
     const float *u, *v;
     const uint8_t *level;
     const uint32_t *desc;

@@ -247,7 +247,10 @@ __global__ void __launch_bounds__(256) k_track(Batch b, TrackArgs a)
     const int lv = a.level[q];
     unsigned long long best = ~0ull;   // distance << 32 | index
     uint32_t second = 0xFFFFFFFFu;
-    if (lv < kMaxLevels) {
+    // the band lv - 1 .. lv + 1 clipped to the frame's levels: a query one
+    // level past the deepest meets that level (its window scaled by
+    // zeta^lv), a deeper one meets none
+    if (lv <= kMaxLevels) {
         const float u = a.u[q], v = a.v[q];
         const float r = __fmul_rn(a.radius, a.zeta_f[lv]);
         uint32_t dq[8];

@@ -115,7 +115,12 @@ def test_ratio_bound_second_best_and_scaled_window(oracle):
     assert q(far, 0, 100.0) == (-1, 0xFFFF)         # level 0 +- 1 does not admit level 2
     deep = kps([100], [7], [bits(2)])
     assert q(deep, 7, 1.0) == (0, 2)
-    assert q(deep, 8, 1.0) == (-1, 0xFFFF)          # levels >= 8 have no candidates
+    # the band rule at any level: 8 +- 1 admits level 7 with r = zeta^8 = 4.30, 9 +- 1 admits none
+    assert q(deep, 8, 1.0) == (0, 2)
+    assert q(deep, 9, 1.0) == (-1, 0xFFFF)
+    deep4 = kps([104], [7], [bits(2)])              # |dx| = 4 at level 7
+    assert q(deep4, 8, 1.0) == (0, 2)               # r = 4.30 >= 4
+    assert q(deep4, 8, 0.9) == (-1, 0xFFFF)         # r = 3.87 < 4
     assert q(kps([100], [3], [bits(2)]), 4, 1.0) == (0, 2)   # level 4 - 1 is in the band
     one = kps([100], [0], [bits(3)])
     t = lambda v, md: tuple(int(a[0]) for a in oracle.track(one, 1.2, [100.0], [v], [0], [z], 5.0, md))

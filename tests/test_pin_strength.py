@@ -237,8 +237,11 @@ MUTANTS = [
      "depth_out[i] = bf > 0.0 ? (float)(bf * (disp > 0.01 ? disp : 0.01)) : 0.0f;", 0),
     ("subpixel_minimum_at_minus_L_kept", "if (ts == -L || ts == L) continue;", "if (ts == L) continue;", 0),
     # tracking (NEXT-2)
-    ("track_level_8_searched", "if (lvl[q] >= OR_MAX_LEVELS) { idx_out[q] = -1; dist_out[q] = 0xFFFF; continue; }",
-     "if (lvl[q] > OR_MAX_LEVELS) { idx_out[q] = -1; dist_out[q] = 0xFFFF; continue; }", 0),
+    ("track_stops_at_level_8", "float zf = (float)or_level_scale(scale, lvl[q]);",
+     "if (lvl[q] >= OR_MAX_LEVELS) { idx_out[q] = -1; dist_out[q] = 0xFFFF; continue; }\n        "
+     "float zf = (float)or_level_scale(scale, lvl[q]);", 0),
+    ("track_band_two_levels_up", "if (m < (int32_t)lvl[q] - 1 || m > (int32_t)lvl[q] + 1) continue;",
+     "if (m < (int32_t)lvl[q] - 1 || m > (int32_t)lvl[q] + 2) continue;", 0),
     ("track_same_level_only", "if (m < (int32_t)lvl[q] - 1 || m > (int32_t)lvl[q] + 1) continue;",
      "if (m != (int32_t)lvl[q]) continue;", 0),
     ("track_lower_level_dropped", "if (m < (int32_t)lvl[q] - 1 || m > (int32_t)lvl[q] + 1) continue;",
