@@ -102,3 +102,24 @@ def test_emitted_line_carries_the_contract(monkeypatch, capsys):
     assert line["path_hbm"]["frac"] > 0 and line["cpu_baseline"] is None
     assert line["path_hbm"]["by_mode"]["graph_streams4"]["frac"] == line["path_hbm"]["frac"]
     assert line["config"]["tuning"] == {"nms_kernel": 0, "detect_ctas_per_sm": 0, "source": "--tile"}
+
+
+def test_results_table_covers_every_config(capsys):
+    """The committed bench lines under results/ hold all five workloads, each
+    a contract line with every mode's throughput and its whole-path HBM share,
+    and the table generator prints a row for each."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("make_table", os.path.join(ROOT, "results", "make_table.py"))
+    mt = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mt)
+    rows = mt.load()
+    assert [w for w, _ in rows] == mt.ORDER
+    for w, d in rows:
+        assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["n_gpus"] == 1
+        assert d["value"] > 0 and d["clocks"]["sm_mhz"] and not set(d["clocks"]["reasons"]) & {
+            "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+        for m in ("graph_streams4", "batched", "plain", "learned_skip"):
+            assert d["modes"][m] > 0 and d["path_hbm"]["by_mode"][m]["frac"] > 0, (w, m)
+    mt.main()
+    out = capsys.readouterr().out
+    assert all(f"| {w} " in out for w in mt.ORDER)
