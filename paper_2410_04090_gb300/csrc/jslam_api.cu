@@ -388,7 +388,9 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     size_t skip_off = 0;
     const size_t slot_words = (size_t)n_slots + 64;
     const size_t seg_words = (size_t)n_segs + 64;
-    const size_t scratch_bytes = slot_words * 4 * 4 + seg_words * 4 * 2;
+    size_t row_words = 64;  // row index of each image's canonical list: levels x (H0 + 1)
+    for (int p = 0; p < n; ++p) row_words += 2 * (size_t)geo[p].levels * (geo[p].H[0] + 1);
+    const size_t scratch_bytes = slot_words * 4 * 4 + seg_words * 4 * 2 + row_words * 4;
     if ((e = ctx->scratch.ensure(scratch_bytes, false, nullptr)) != cudaSuccess) return fail(ctx, e);
 
     // Host tables: [images][levels][pairs][pyr base][fast base][seg level][taps/proj ...]
@@ -428,7 +430,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     auto seg_level = reinterpret_cast<int32_t *>(host.data() + o_seg);
     auto ftile_level = reinterpret_cast<int32_t *>(host.data() + o_ftl);
     auto ptile_level = reinterpret_cast<int32_t *>(host.data() + o_ptl);
-    size_t t_off = o_tables, lvl_off = 0, map_off = 0, stage_off = 0;
+    size_t t_off = o_tables, lvl_off = 0, map_off = 0, stage_off = 0, row_off = 0;
     int li = 0, slot = 0, seg = 0, pyr = 0, fast = 0;
     ctx->staging_off.assign(n_img, 0);
     int32_t *dcounts = ctx->counts.as<int32_t>();
@@ -468,6 +470,8 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
                 skip_off += align_up((size_t)I.skip_cells_x * I.skip_cells_y, 256);
             }
             I.level_start = reinterpret_cast<int32_t *>(dplan + o_lstart) + img * (kMaxLevels + 1);
+            I.row_first = ctx->scratch.as<int32_t>(4 * (slot_words * 4 + seg_words * 2) + row_off);
+            row_off += 4 * (size_t)g.levels * (g.H[0] + 1);
             const SideLayout &sl = pl.side[s];
             I.out.capacity = pl.capacity;
             I.out.desc = reinterpret_cast<uint32_t *>(rblock + sl.desc);

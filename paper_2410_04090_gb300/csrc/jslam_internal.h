@@ -96,6 +96,10 @@ struct ImageDesc {
     int32_t *count;          // keypoint count written by finalisation
     int32_t *count_hdr;      // the same count in the header of the pair's result block
     int32_t *level_start;    // kMaxLevels + 1 entries
+    // row index of the canonical list, per level H0 + 1 entries: entry v is
+    // the first index of the level whose Y is >= v (the level's end if none);
+    // written by k_pfa_finalize for levels with keypoints, read by k_match
+    int32_t *row_first;
     KpOut out;
     // learned cell-skip (skip == nullptr: exact mode)
     float *skip_logits;      // skip_h8 x skip_w8 logits at 1/8 scale

@@ -14,10 +14,11 @@
 //                comparisons read the patch 32 at a time and are packed into
 //                words by a ballot.
 // k_match        one warp per left keypoint: for each right level within one
-//                of the keypoint's level, binary-searches the s0 row band in
-//                the canonical (level, y, x) list (Y is non-decreasing in y),
-//                scans the band with the lanes, and keeps the smallest
-//                (Hamming distance, disparity, index) by a warp min-reduction.
+//                of the keypoint's level, takes the s0 row band of the
+//                canonical (level, y, x) list (Y is non-decreasing in y) from
+//                the row index (two independent loads per level), scans the
+//                band with the lanes, and keeps the smallest (Hamming
+//                distance, disparity, index) by a warp min-reduction.
 #include "jslam_internal.h"
 
 namespace jslam {
@@ -195,10 +196,25 @@ __global__ void __launch_bounds__(256) k_match(Batch b)
 
     unsigned long long best = ~0ull;
     const int m_lo = max(0, n - 1), m_hi = min(Ir.levels - 1, n + 1);
-    for (int m = m_lo; m <= m_hi; ++m) {
-        const int s = Ir.level_start[m], e = Ir.level_start[m + 1];
-        const int a = warp_lower_bound_Y(orr.Y, s, e, Y - band, lane);
-        const int z = warp_lower_bound_Y(orr.Y, a, e, Y + band + 1, lane);
+    // the band [Y - band, Y + band] of each level: lower bounds of Y - band
+    // and Y + band + 1 from the row index (rows clamped to [0, H0]; a level
+    // without keypoints has an empty band and an unwritten table)
+    const int va = min(max(Y - band, 0), Ir.H0), vz = min(max(Y + band + 1, 0), Ir.H0);
+    int ra[3], rz[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int m = m_lo + q;
+        ra[q] = rz[q] = 0;
+        if (m <= m_hi) {
+            const int s = __ldg(Ir.level_start + m), e = __ldg(Ir.level_start + m + 1);
+            const int32_t *rf = Ir.row_first + (size_t)m * (Ir.H0 + 1);
+            ra[q] = e > s ? __ldg(rf + va) : s;
+            rz[q] = e > s ? __ldg(rf + vz) : s;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int a = ra[q], z = rz[q];
         for (int j = a + lane; j < z; j += 32) {
             const int disp = X - (int)orr.X[j];
             if (disp < 0 || disp > b.prm.max_disp) continue;

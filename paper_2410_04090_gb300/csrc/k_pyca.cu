@@ -231,6 +231,30 @@ __device__ __forceinline__ int block_excl_scan(int v, int *ws, int *total)
 // their slots.
 constexpr int kFinPrioCache = 8192;
 
+// Row index of an image's canonical list, for the stereo matching (all
+// threads of the finalisation's CTA, after its barrier: the keypoints'
+// levels and Y and the level starts in lstart, kMaxLevels + 1 entries whose
+// last is the count, are complete).  Keypoint j of level l owns the entries
+// (Y[j - 1], Y[j]] of the level's table, the level's first keypoint the
+// entries up to its Y and its last one those after its Y (they hold the
+// level's end), so every level with keypoints gets all H0 + 1 entries.
+// Not inlined: its registers stay out of the finalisation's allocation.
+__device__ __noinline__ void fill_row_index(const ImageDesc &I, const int *lstart)
+{
+    const int rows = I.H0 + 1, keep = lstart[kMaxLevels];
+    const KpOut &o = I.out;
+    for (int j = threadIdx.x; j < keep; j += kFinThreads) {
+        const int l = o.level[j];
+        const int s = lstart[l], e = lstart[l + 1];
+        const int Yj = o.Y[j];
+        const int prev = j == s ? -1 : (int)o.Y[j - 1];
+        int32_t *rf = I.row_first + (size_t)l * rows;
+        for (int v = prev + 1; v <= Yj; ++v) rf[v] = j;
+        if (j == e - 1)
+            for (int v = Yj + 1; v < rows; ++v) rf[v] = e;
+    }
+}
+
 __global__ void __launch_bounds__(kFinThreads, 2) k_pfa_finalize(Batch b)
 {
     __shared__ uint32_t s_prio[kFinPrioCache];
@@ -383,6 +407,8 @@ __global__ void __launch_bounds__(kFinThreads, 2) k_pfa_finalize(Batch b)
         *I.count = keep;
         *I.count_hdr = keep;
     }
+    __syncthreads();
+    fill_row_index(b.images[img], lstart);
 }
 
 cudaError_t launch_pfa_finalize(const Batch &b, cudaStream_t stream)
