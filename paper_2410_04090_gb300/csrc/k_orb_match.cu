@@ -156,27 +156,6 @@ cudaError_t launch_orient_desc(const Batch &b, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-// First index in [lo, hi) whose Y is >= v (Y non-decreasing on the range),
-// found by the whole warp: each round the 32 lanes probe 32 evenly spaced
-// positions and the ballot narrows the range 32-fold (a few dependent loads
-// instead of one per halving).  Every lane returns the same index.
-__device__ __forceinline__ int warp_lower_bound_Y(const uint16_t *Y, int lo, int hi, int v, int lane)
-{
-    while (hi - lo > 32) {
-        const int n = hi - lo;
-        // probe k marks the end of slice k: position lo + (n * (k + 1)) / 32 - 1
-        const int pos = lo + (int)(((long long)n * (lane + 1)) >> 5) - 1;
-        const uint32_t below = __ballot_sync(0xFFFFFFFFu, (int)__ldg(Y + pos) < v);
-        const int c = __popc(below);  // slices 0..c-1 lie entirely below v
-        const int nlo = c == 0 ? lo : lo + (int)(((long long)n * c) >> 5);
-        const int nhi = c == 32 ? hi : lo + (int)(((long long)n * (c + 1)) >> 5);
-        lo = nlo;
-        hi = nhi;
-    }
-    const bool below = lo + lane < hi && (int)__ldg(Y + lo + lane) < v;
-    return lo + __popc(__ballot_sync(0xFFFFFFFFu, below));
-}
-
 __global__ void __launch_bounds__(256) k_match(Batch b)
 {
     const int pair = blockIdx.y;
@@ -250,7 +229,7 @@ __global__ void __launch_bounds__(256) k_match(Batch b)
 }
 
 // Feature tracking by projection (middle-end): one warp per query.  For each
-// level of the band the warp search narrows the frame's canonical list to a
+// level of the band the row index narrows the frame's canonical list to a
 // conservative Y range; lanes take the exact float window test and the
 // Hamming distance, and a warp reduction keeps the smallest (distance,
 // index) and the second-smallest distance.
@@ -275,10 +254,14 @@ __global__ void __launch_bounds__(256) k_track(Batch b, TrackArgs a)
         const KpOut &o = I.out;
         const int m_lo = max(0, lv - 1), m_hi = min(I.levels - 1, lv + 1);
         const int ylo = (int)floorf(v - r) - 1, yhi = (int)ceilf(v + r) + 1;  // covers every Y that can pass
+        // rows of the row index, clamped to [0, H0] (64-bit: yhi may be INT_MAX)
+        const int va = (int)min(max((long long)ylo, 0ll), (long long)I.H0);
+        const int vz = (int)min(max((long long)yhi + 1, 0ll), (long long)I.H0);
         for (int m = m_lo; m <= m_hi; ++m) {
             const int s = I.level_start[m], e = I.level_start[m + 1];
-            const int z0 = warp_lower_bound_Y(o.Y, s, e, ylo, lane);
-            const int z1 = warp_lower_bound_Y(o.Y, z0, e, yhi + 1, lane);
+            const int32_t *rf = I.row_first + (size_t)m * (I.H0 + 1);
+            const int z0 = e > s ? __ldg(rf + va) : s;
+            const int z1 = e > s ? max(__ldg(rf + vz), z0) : s;
             for (int j = z0 + lane; j < z1; j += 32) {
                 const float dx = __fsub_rn((float)o.X[j], u), dy = __fsub_rn((float)o.Y[j], v);
                 if (fabsf(dx) > r || fabsf(dy) > r) continue;
