@@ -234,24 +234,30 @@ constexpr int kFinPrioCache = 8192;
 // Row index of an image's canonical list, for the stereo matching (all
 // threads of the finalisation's CTA, after its barrier: the keypoints'
 // levels and Y and the level starts in lstart, kMaxLevels + 1 entries whose
-// last is the count, are complete).  Keypoint j of level l owns the entries
-// (Y[j - 1], Y[j]] of the level's table, the level's first keypoint the
-// entries up to its Y and its last one those after its Y (they hold the
-// level's end), so every level with keypoints gets all H0 + 1 entries.
-// Not inlined: its registers stay out of the finalisation's allocation.
+// last is the count, are complete).  Entry v of level l's table is the
+// first index of the level whose Y is >= v, else the level's end: keypoint
+// j owns the entries (Y[j - 1], Y[j]] when it is not the level's first;
+// the entries up to the first keypoint's Y (the level's start) and after
+// the last one's (its end) are spread over the CTA.  Every level with
+// keypoints gets all H0 + 1 entries.  Not inlined: its registers stay out
+// of the finalisation's allocation.
 __device__ __noinline__ void fill_row_index(const ImageDesc &I, const int *lstart)
 {
     const int rows = I.H0 + 1, keep = lstart[kMaxLevels];
     const KpOut &o = I.out;
     for (int j = threadIdx.x; j < keep; j += kFinThreads) {
         const int l = o.level[j];
-        const int s = lstart[l], e = lstart[l + 1];
+        if (j == lstart[l]) continue;
         const int Yj = o.Y[j];
-        const int prev = j == s ? -1 : (int)o.Y[j - 1];
         int32_t *rf = I.row_first + (size_t)l * rows;
-        for (int v = prev + 1; v <= Yj; ++v) rf[v] = j;
-        if (j == e - 1)
-            for (int v = Yj + 1; v < rows; ++v) rf[v] = e;
+        for (int v = (int)o.Y[j - 1] + 1; v <= Yj; ++v) rf[v] = j;
+    }
+    for (int t = threadIdx.x; t < I.levels * rows; t += kFinThreads) {
+        const int l = t / rows, v = t - l * rows;
+        const int s = lstart[l], e = lstart[l + 1];
+        if (s == e) continue;
+        if (v <= (int)o.Y[s]) I.row_first[t] = s;
+        else if (v > (int)o.Y[e - 1]) I.row_first[t] = e;
     }
 }
 
