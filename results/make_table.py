@@ -3,7 +3,7 @@
 one JSON line each, as `python bench.py --workload <w> --steps 30` printed
 them on a GB300): stereo pairs/s of every mode, the whole path's share of
 the measured HBM bandwidth per mode, the detection kernel's roofline and the
-CPU oracle.  Prints the tables that the design doc section 9 carries."""
+CPU oracle, as two markdown tables."""
 import glob
 import json
 import os

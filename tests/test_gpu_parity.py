@@ -2,6 +2,8 @@
 keypoints, scores, sectors, descriptors and matches, angles within 1e-4 rad.
 Sizes span several tiles with ragged edges; the full workload shapes are
 compared in full (the oracle finishes them in seconds)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -556,4 +558,58 @@ def test_graph_replay_follows_new_frames(J, oracle):
         fe.graph_launch()
         fe.sync()
         _check_batch(J, oracle, fe, nxt, specs)
+    fe.close()
+
+
+def test_largest_batch_equals_pairs_alone(J, oracle):
+    """The largest batch a context accepts (128 pairs, 256 images: the limit
+    of the by-value input table) of pairs of nine sizes, depths 1..6, two
+    scene kinds and two thresholds: every pair's keypoints, descriptors and
+    matches equal those of the same pair extracted alone, bit for bit, and
+    four sampled pairs equal the oracle's.  Two pairs have flat images (no
+    keypoints on either side, or on the right side only)."""
+    import torch
+    sizes = [(96, 64), (160, 120), (203, 157), (256, 96), (128, 200), (333, 111), (64, 64), (300, 180), (177, 143)]
+    pairs, jobs, ps = [], [], []
+    for i in range(128):
+        w, h = sizes[i % len(sizes)]
+        pr = scenes.stereo_pair("planes" if i % 3 else "euroc", w, h, frame=i, stream=i % 5, config_id=7)
+        if i in (50, 51):  # flat frames: no keypoints on both sides (50) or on the right (51)
+            flat = np.full((h, w), 128, np.uint8)
+            pr = dataclasses.replace(pr, left=flat if i == 50 else pr.left, right=flat)
+        p = params_from(oracle, levels=1 + i % 6, max_feats=150 + 7 * i, fast_thresh=20 if i % 4 else 12,
+                        fast_thresh_lo=7, cell=16 if i % 2 else 32)
+        while p.levels > 1:  # the deepest level must still hold a pixel inside the border
+            W, H, _ = oracle.level_geometry(w, h, p.levels, p.scale, p.cell)
+            if min(W[-1], H[-1]) >= 2 * p.border + 1:
+                break
+            p.levels -= 1
+        pairs.append(pr)
+        ps.append(p)
+        jobs.append(J.Job(torch.from_numpy(pr.left).cuda(), torch.from_numpy(pr.right).cuda(), p.levels, p.scale,
+                          p.fast_thresh, p.cell, p.max_feats))
+    torch.cuda.synchronize()
+    base = params_from(oracle, fast_thresh_lo=7)
+    fe = frontend_for(J, base, max_width=333, max_height=200, max_pairs=128, max_feats=1100)
+    fe.extract_batch(jobs)
+    fe.match()
+    fe.sync()
+    batch = [(J.to_numpy(fe.keypoints(i, 0)), J.to_numpy(fe.keypoints(i, 1)), J.to_numpy(fe.matches(i)))
+             for i in range(128)]
+    one = frontend_for(J, base, max_width=333, max_height=200, max_pairs=1, max_feats=1100)
+    for i, (pr, p) in enumerate(zip(pairs, ps)):
+        got = gpu_pair(J, one, pr.left, pr.right, p)
+        for side in (0, 1):
+            assert batch[i][side]["count"] == got[side]["count"], (i, side)
+            for f in ("x", "y", "X", "Y", "level", "response", "k_levels", "k_resp", "angle_bin", "desc", "angle"):
+                assert np.array_equal(batch[i][side][f], got[side][f]), (i, side, f)
+        for f in ("right_idx", "disparity", "dist"):
+            assert np.array_equal(batch[i][2][f], got[2][f]), (i, f)
+    assert batch[50][0]["count"] == 0 and batch[51][1]["count"] == 0 and batch[51][0]["count"] > 0
+    for i in (0, 51, 67, 127):
+        ol, orr, om = oracle.extract_pair(pairs[i].left, pairs[i].right, ps[i])
+        compare_keypoints(batch[i][0], ol, f"pair {i} left")
+        compare_keypoints(batch[i][1], orr, f"pair {i} right")
+        compare_matches(batch[i][2], om, f"pair {i}")
+    one.close()
     fe.close()
