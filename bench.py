@@ -447,7 +447,7 @@ def main():
     jobs = fe.prepare_batch([jslam.Job(l, r, **p) for l, r, p in zip(lefts, rights, params)])
     if args.tile:
         fe.set_tuning(*args.tile)
-        tuning = tuple(args.tile) + (0, 0)
+        tuning = tuple(args.tile) + (0, 0, 0)
         tune_source = "--tile"
     else:
         tuning = fe.autotune(jobs, cache=TUNE_CACHE)
@@ -868,6 +868,7 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
             "config": {"workload": f"{args.workload}: {WORKLOAD_DESC[args.workload]}",
                        "pairs_per_step": n, "mode": args.mode, "detect_tile_px": list(tuning[:2]),
                        "tuning": {"nms_kernel": tuning[2], "detect_ctas_per_sm": tuning[3],
+                                  "tile_order": tuning[4],
                                   "source": tune_source},
                        "parallelism": f"replicas x{world}", "l2": "flushed before every step (256 MB write)"},
             "modes": mode_values, "learned_skip": skip_quality, "refine": refine, "track": track,

@@ -394,10 +394,13 @@ typedef struct {
                                   * segment always */
     int32_t detect_ctas_per_sm;  /* persistent detection CTAs per SM: 0 as many as fit (default), 1..8 at most
                                   * that many (never more than fit) */
+    int32_t tile_order;          /* order in which the persistent detection CTAs take the tiles: 0 by image,
+                                  * level and tile row (default); 1 by decreasing work (evaluated rows x
+                                  * 32-pixel chunks), so the last rounds hold the smallest tiles */
 } jslam_tuning;
 
 /* Use `t` for the following extractions (plans are rebuilt when the tile
- * changes).  Launch-shape tuning has no counterpart in the paper (its MLPT /
+ * or the tile order changes).  Launch-shape tuning has no counterpart in the paper (its MLPT /
  * TEWA thread allocation, Sec. II-C-1, is fixed per cell size).
  * JSLAM_ERR_ARG for values outside the ranges above. */
 jslam_status jslam_set_tuning(jslam_ctx *ctx, const jslam_tuning *t);
@@ -405,7 +408,8 @@ jslam_status jslam_set_tuning(jslam_ctx *ctx, const jslam_tuning *t);
 /* Tune the launch shapes on the batch `jobs` (n pairs, as for
  * jslam_extract_batch), timing the stages with the stage events: the
  * detection tile among five shapes, then the number of persistent detection
- * CTAs per SM, then (when every segment fits a warp) the NMS kernel.  Keeps
+ * CTAs per SM, then (when every segment fits a warp) the NMS kernel, then the
+ * tile order.  Keeps
  * the fastest for the context and returns it in *out (may be NULL).  Runs the
  * batch several times; results are unaffected.  No counterpart in the paper
  * (an autotuner in place of the fixed thread allocation of Sec. II-C-1). */

@@ -1,8 +1,10 @@
 // C ABI of libjslam: context, grow-only device buffers, batch plans and the
 // launch sequence of the stereo frontend.
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 #include <cudaTypedefs.h>
@@ -229,8 +231,8 @@ struct jslam_ctx {
     bool plan_skip = false;  // the current plan has skip buffers
 
     // launch-shape tuning and the captured graph
-    jslam_tuning tune{128, 64, 0, 0};
-    jslam_tuning plan_tune{0, 0, 0, 0};  // tuning the current plan was built with (tile fields)
+    jslam_tuning tune{128, 64, 0, 0, 0};
+    jslam_tuning plan_tune{0, 0, 0, 0, 0};  // tuning the current plan was built with (tile fields)
     cudaGraphExec_t graph = nullptr;
     cudaGraph_t graph_src = nullptr;    // the captured graph (its node handles address `graph`)
     // its pyramid launches (one, or one per level in the cascaded pyramid):
@@ -318,7 +320,8 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
         for (int s = 0; s < 2; ++s) k.mem[s] = im[s]->memory;
     }
     if (keys == ctx->keys && ctx->plan_tune.tile_w_px == ctx->tune.tile_w_px &&
-        ctx->plan_tune.tile_h_px == ctx->tune.tile_h_px && ctx->plan_skip == ctx->skip_on)
+        ctx->plan_tune.tile_h_px == ctx->tune.tile_h_px && ctx->plan_tune.tile_order == ctx->tune.tile_order &&
+        ctx->plan_skip == ctx->skip_on)
         return JSLAM_OK;
     ++ctx->plan_gen;
 
@@ -618,6 +621,26 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
             R.pad_ = 0;
             R.raw = L.raw; R.tmap = L.tmap; R.map = I.map; R.skip = I.skip;
         }
+    }
+    // Tile order 1: the persistent detection CTAs take records t, t + grid,
+    // t + 2 grid, ...; ordered by decreasing work (evaluated rows x 32-pixel
+    // chunks, the items of a threshold pass) the grid's last rounds hold the
+    // smallest tiles.  Each record is self-contained (its tile's geometry,
+    // slots and buffers), so the order changes no result; which order is
+    // faster depends on the batch (the autotuner measures both).
+    if (ctx->tune.tile_order == 1) {
+        const int border = cfg.border;
+        std::vector<std::pair<int, int>> work(fast);
+        for (int t = 0; t < fast; ++t) {
+            const TileRec &R = trec[t];
+            const int rows = std::max(std::min(R.H - border - R.y0, R.th) - std::max(border - R.y0, 0), 0);
+            work[t] = { -rows * ((R.tw + 31) >> 5), t };
+        }
+        std::stable_sort(work.begin(), work.end(),
+                         [](const std::pair<int, int> &a, const std::pair<int, int> &b) { return a.first < b.first; });
+        std::vector<TileRec> sorted(fast);
+        for (int t = 0; t < fast; ++t) sorted[t] = trec[work[t].second];
+        std::copy(sorted.begin(), sorted.end(), trec);
     }
 
     // pyramid tiles by level number (the cascaded pyramid launches level
@@ -1409,6 +1432,7 @@ jslam_status jslam_set_tuning(jslam_ctx *ctx, const jslam_tuning *t)
     if (t->tile_h_px < 8 || t->tile_h_px > kFastMaxTile) return JSLAM_ERR_ARG;
     if (t->nms_kernel < 0 || t->nms_kernel > 1 || t->detect_ctas_per_sm < 0 || t->detect_ctas_per_sm > 8)
         return JSLAM_ERR_ARG;
+    if (t->tile_order < 0 || t->tile_order > 1) return JSLAM_ERR_ARG;
     ctx->tune = *t;
     return JSLAM_OK;
 }
@@ -1444,6 +1468,7 @@ jslam_status jslam_autotune(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_
     jslam_tuning best = ctx->tune;
     best.nms_kernel = 0;
     best.detect_ctas_per_sm = 0;
+    best.tile_order = 0;
     // 1. the detection tile
     float best_ms = -1.0f;
     for (const auto &tl : tiles) {
@@ -1484,6 +1509,17 @@ jslam_status jslam_autotune(jslam_ctx *ctx, const jslam_stereo_job *jobs, int32_
             st = time_stage(ctx, jobs, n, JSLAM_STAGE_PFA_NMS, 3, &nms_ms[v]);
         }
         if (st == JSLAM_OK) best.nms_kernel = nms_ms[1] < nms_ms[0] ? 1 : 0;
+    }
+    // 4. the tile order (a replan each), against the detection time of the
+    // pick so far
+    if (st == JSLAM_OK) {
+        ctx->tune = best;
+        ctx->tune.tile_order = 1;
+        float ms;
+        if ((st = time_stage(ctx, jobs, n, JSLAM_STAGE_DETECT, 3, &ms)) == JSLAM_OK && ms < best_ms) {
+            best_ms = ms;
+            best.tile_order = 1;
+        }
     }
     ctx->tune = best;
     ctx->tune_ms = best_ms;

@@ -9,7 +9,8 @@
 //     "version": 1,
 //     "entries": {
 //       "<key>": {"tile_w_px": 128, "tile_h_px": 128, "nms_kernel": 0,
-//                 "detect_ctas_per_sm": 0, "stage_ms": 0.8612},
+//                 "detect_ctas_per_sm": 0, "tile_order": 0, "stage_ms": 0.8612},
+//       (an entry without "tile_order" reads as 0)
 //       ...
 //     }
 //   }
@@ -110,12 +111,13 @@ bool parse_entry(Parser &p, Entry *e)
         double v = 0.0;
         if (!p.str(&k) || !p.lit(':')) return false;
         if (k == "tile_w_px" || k == "tile_h_px" || k == "nms_kernel" || k == "detect_ctas_per_sm" ||
-            k == "stage_ms") {
+            k == "tile_order" || k == "stage_ms") {
             if (!p.num(&v)) return false;
             if (k == "tile_w_px") e->t.tile_w_px = (int32_t)v;
             else if (k == "tile_h_px") e->t.tile_h_px = (int32_t)v;
             else if (k == "nms_kernel") e->t.nms_kernel = (int32_t)v;
             else if (k == "detect_ctas_per_sm") e->t.detect_ctas_per_sm = (int32_t)v;
+            else if (k == "tile_order") e->t.tile_order = (int32_t)v;
             else e->ms = v;
         } else if (!p.skip_value()) {
             return false;
@@ -158,7 +160,7 @@ bool tuning_ok(const jslam_tuning &t)
 {
     return t.tile_w_px >= 32 && t.tile_w_px <= 128 && t.tile_w_px % 4 == 0 && t.tile_h_px >= 8 &&
            t.tile_h_px <= 128 && t.nms_kernel >= 0 && t.nms_kernel <= 1 && t.detect_ctas_per_sm >= 0 &&
-           t.detect_ctas_per_sm <= 8;
+           t.detect_ctas_per_sm <= 8 && t.tile_order >= 0 && t.tile_order <= 1;
 }
 
 }  // namespace
@@ -218,9 +220,10 @@ jslam_status jslam_tune_cache_put(const char *path, const char *key, const jslam
     for (const auto &kv : m) {
         ok = ok && std::fprintf(f,
                                 "%s\n    \"%s\": {\"tile_w_px\": %d, \"tile_h_px\": %d, \"nms_kernel\": %d, "
-                                "\"detect_ctas_per_sm\": %d, \"stage_ms\": %.6f}",
+                                "\"detect_ctas_per_sm\": %d, \"tile_order\": %d, \"stage_ms\": %.6f}",
                                 i++ ? "," : "", kv.first.c_str(), kv.second.t.tile_w_px, kv.second.t.tile_h_px,
-                                kv.second.t.nms_kernel, kv.second.t.detect_ctas_per_sm, kv.second.ms) > 0;
+                                kv.second.t.nms_kernel, kv.second.t.detect_ctas_per_sm, kv.second.t.tile_order,
+                                kv.second.ms) > 0;
     }
     ok = ok && std::fprintf(f, "\n  }\n}\n") > 0;
     ok = (std::fclose(f) == 0) && ok;

@@ -52,10 +52,10 @@ class StereoJob(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("tile_w_px", C.c_int32), ("tile_h_px", C.c_int32), ("nms_kernel", C.c_int32),
-                ("detect_ctas_per_sm", C.c_int32)]
+                ("detect_ctas_per_sm", C.c_int32), ("tile_order", C.c_int32)]
 
     def as_tuple(self) -> tuple:
-        return self.tile_w_px, self.tile_h_px, self.nms_kernel, self.detect_ctas_per_sm
+        return self.tile_w_px, self.tile_h_px, self.nms_kernel, self.detect_ctas_per_sm, self.tile_order
 
 
 class SkipView(C.Structure):
@@ -278,7 +278,8 @@ def tune_key(gpu_name: str, sm_count: int, config: dict, jobs) -> str:
 
 
 def tune_cache_get(path: str, key: str):
-    """The cached pick (tile_w_px, tile_h_px, nms_kernel, detect_ctas_per_sm) or None."""
+    """The cached pick (tile_w_px, tile_h_px, nms_kernel, detect_ctas_per_sm,
+    tile_order) or None."""
     t, found = Tuning(), C.c_int32(0)
     _check(lib().jslam_tune_cache_get(os.fsencode(path), key.encode(), C.byref(t), C.byref(found)),
            "jslam_tune_cache_get")
@@ -531,13 +532,14 @@ class Frontend:
         return {"logits": _device_view(v.logits, (v.h8, v.w8), np.float32, self.device),
                 "skip": _device_view(v.skip, (v.cells_y, v.cells_x), np.uint8, self.device)}
 
-    def set_tuning(self, tile_w_px: int, tile_h_px: int, nms_kernel: int = 0, detect_ctas_per_sm: int = 0):
-        t = Tuning(tile_w_px, tile_h_px, nms_kernel, detect_ctas_per_sm)
+    def set_tuning(self, tile_w_px: int, tile_h_px: int, nms_kernel: int = 0, detect_ctas_per_sm: int = 0,
+                   tile_order: int = 0):
+        t = Tuning(tile_w_px, tile_h_px, nms_kernel, detect_ctas_per_sm, tile_order)
         _check(lib().jslam_set_tuning(self._h, C.byref(t)), "jslam_set_tuning")
 
     def autotune(self, jobs, cache: str | None = None) -> tuple:
         """Tune the launch shapes on `jobs`; returns (tile_w_px, tile_h_px,
-        nms_kernel, detect_ctas_per_sm).  With `cache` (a JSON file path) a
+        nms_kernel, detect_ctas_per_sm, tile_order).  With `cache` (a JSON file path) a
         stored pick for this GPU and batch is applied without tuning, and a new
         pick is stored; `last_tune_hit` tells which happened."""
         pb = jobs if isinstance(jobs, PreparedBatch) else PreparedBatch(jobs)

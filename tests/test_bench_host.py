@@ -81,7 +81,7 @@ def test_emitted_line_carries_the_contract(monkeypatch, capsys):
     clocks = types.SimpleNamespace(summary=lambda: {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []})
     e2e = {"value": 43000.0, "unit": bench.UNIT, "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1}
     bench.emit(args, 1, len(pairs), 47800.0, 2.09 * 50, {"graph_streams4": 47800.0},
-               {k: v * 50 for k, v in stage.items()}, [2000] * 4, pairs, params, lo, e2e, clocks, (128, 128, 0, 0),
+               {k: v * 50 for k, v in stage.items()}, [2000] * 4, pairs, params, lo, e2e, clocks, (128, 128, 0, 0, 0),
                None, 0)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
@@ -101,7 +101,7 @@ def test_emitted_line_carries_the_contract(monkeypatch, capsys):
     assert roof["hbm"]["algorithmic_bytes_per_launch"] == bench.algorithmic_bytes("detect", pairs, params, [1])
     assert line["path_hbm"]["frac"] > 0 and line["cpu_baseline"] is None
     assert line["path_hbm"]["by_mode"]["graph_streams4"]["frac"] == line["path_hbm"]["frac"]
-    assert line["config"]["tuning"] == {"nms_kernel": 0, "detect_ctas_per_sm": 0, "source": "--tile"}
+    assert line["config"]["tuning"] == {"nms_kernel": 0, "detect_ctas_per_sm": 0, "tile_order": 0, "source": "--tile"}
 
 
 def test_results_table_covers_every_config(capsys):

@@ -477,8 +477,9 @@ def _batch_outputs(J, fe, n):
 
 def test_every_tuning_gives_identical_results(J, oracle):
     """Every launch shape the tuner can pick -- detection tile, persistent
-    CTAs per SM, NMS kernel -- gives the same keypoints, descriptors and
-    matches, bit for bit (the default's equal the oracle's)."""
+    CTAs per SM, NMS kernel, tile order -- gives the same keypoints,
+    descriptors and matches, bit for bit (the default's equal the
+    oracle's)."""
     import torch
     specs = scenes.MIXED_STREAMS[::4]
     fe = frontend_for(J, params_from(oracle, fast_thresh_lo=7), max_pairs=4)
@@ -489,11 +490,11 @@ def test_every_tuning_gives_identical_results(J, oracle):
     ref = _batch_outputs(J, fe, len(specs))
     for tw, th in ((128, 64), (128, 32), (128, 128), (64, 64), (64, 128), (96, 48)):
         for nms in (0, 1):
-            for ctas in (0, 1, 2):
-                fe.set_tuning(tw, th, nms, ctas)
+            for ctas, order in ((0, 0), (1, 0), (2, 0), (0, 1), (2, 1)):
+                fe.set_tuning(tw, th, nms, ctas, order)
                 fe.extract_batch(jobs); fe.match(); fe.sync()
                 for i, (a, b) in enumerate(zip(ref, _batch_outputs(J, fe, len(specs)))):
-                    what = f"tile {tw}x{th} nms {nms} ctas {ctas} pair {i}"
+                    what = f"tile {tw}x{th} nms {nms} ctas {ctas} order {order} pair {i}"
                     for side in (0, 1):
                         assert a[side]["count"] == b[side]["count"], what
                         for f in ("x", "y", "X", "Y", "level", "response", "k_levels", "k_resp", "angle_bin",
@@ -536,6 +537,7 @@ def test_mixed_sixteen_streams(J, oracle):
     pairs, jobs = _mixed_streams(J, specs, 0)
     tile = fe.autotune(jobs)
     assert tile[0] in (64, 128) and tile[1] in (32, 64, 128) and tile[2] in (0, 1) and 0 <= tile[3] <= 8
+    assert tile[4] in (0, 1)
     fe.extract_batch(jobs)
     fe.match()
     fe.sync()
