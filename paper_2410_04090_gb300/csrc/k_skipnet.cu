@@ -214,7 +214,10 @@ __global__ void __launch_bounds__(kSkipThreads) k_skipnet(Batch b, const SkipMod
         const int o = (k >> 3) * 128 + n * 8 + (k & 7);
         B1[o] = k < 9 ? m.w1[n * 9 + k] : (uint16_t)0;
     }
-    for (int i = threadIdx.x; i < 9 * 256; i += kSkipThreads) {
+    static_assert(kSkipThreads == 256, "one tap matrix element per thread and tap");
+#pragma unroll
+    for (int t9 = 0; t9 < 9; ++t9) {  // unrolled: the 18 weight loads of a thread in flight together
+        const int i = t9 * 256 + threadIdx.x;
         const int t = i >> 8, n = (i >> 4) & 15, k = i & 15;
         const int o = t * 256 + (k >> 3) * 128 + n * 8 + (k & 7);
         B2[o] = m.w2[(n * kSkipC + k) * 9 + t];
@@ -228,7 +231,10 @@ __global__ void __launch_bounds__(kSkipThreads) k_skipnet(Batch b, const SkipMod
 
     // X: box means of 8x8 level-0 blocks on the input grid (row iy, column ix
     // is 1/8-map position (ty0 - 3 + iy, tx0 - 3 + ix)); zero outside the map
-    for (int i = threadIdx.x; i < kXRows * kSkipP; i += kSkipThreads) {
+#pragma unroll
+    for (int j = 0; j < (kXRows * kSkipP + kSkipThreads - 1) / kSkipThreads; ++j) {
+        const int i = j * kSkipThreads + threadIdx.x;
+        if (i >= kXRows * kSkipP) break;
         const int iy = i / kSkipP, ix = i - iy * kSkipP;
         const int gy = ty0 - 3 + iy, gx = tx0 - 3 + ix;
         float v = 0.0f;
@@ -237,10 +243,16 @@ __global__ void __launch_bounds__(kSkipThreads) k_skipnet(Batch b, const SkipMod
             const int y1 = min(y0 + 8, H0), x1 = min(x0 + 8, W0);
             uint32_t sum = 0;
             if (x1 - x0 == 8) {
-                for (int y = y0; y < y1; ++y) {
-                    const uint2 w = __ldg(reinterpret_cast<const uint2 *>(raw + (size_t)y * pitch + x0));
-                    sum = __vsadu4(w.x, 0u) + __vsadu4(w.y, 0u) + sum;
-                }
+                // the block's rows requested together (the loop is unrolled
+                // with a guard), then summed: one memory latency per block
+                const uint8_t *col = raw + (size_t)y0 * pitch + x0;
+                uint2 w[8];
+#pragma unroll
+                for (int dy = 0; dy < 8; ++dy)
+                    w[dy] = y0 + dy < y1 ? __ldg(reinterpret_cast<const uint2 *>(col + (size_t)dy * pitch))
+                                         : make_uint2(0u, 0u);
+#pragma unroll
+                for (int dy = 0; dy < 8; ++dy) sum = __vsadu4(w[dy].x, 0u) + __vsadu4(w[dy].y, 0u) + sum;
             } else {
                 for (int y = y0; y < y1; ++y) {
                     const uint8_t *row = raw + (size_t)y * pitch;
