@@ -386,6 +386,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
             skip_max_tiles = std::max(skip_max_tiles, ((w8 + kSkipTileW - 1) / kSkipTileW) * ((h8 + kSkipTileH - 1) / kSkipTileH));
             skip_max_cells = std::max(skip_max_cells, cx * cy);
         }
+        skip_bytes += align_up(sizeof(int32_t) * (size_t)(2 * n), 256);  // per image: any cell skipped
         if ((e = ctx->skipbuf.ensure(skip_bytes + 256, false, nullptr)) != cudaSuccess) return fail(ctx, e);
     }
     size_t skip_off = 0;
@@ -618,7 +619,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
             R.prj_off_y = (int)(ay - by0) / 2;
             R.prj_bytes_x = (int)align_up((size_t)(ax - bx0) + 2 * (size_t)R.tw, 16);
             R.prj_bytes_y = (int)align_up((size_t)(ay - by0) + 2 * (size_t)R.th, 16);
-            R.pad_ = 0;
+            R.image = L.image;
             R.raw = L.raw; R.tmap = L.tmap; R.map = I.map; R.skip = I.skip;
         }
     }
@@ -681,6 +682,7 @@ jslam_status build_plan(jslam_ctx *ctx, const jslam_stereo_job *jobs, int n)
     b.fast_smem = fast_smem_bytes(max_box, max_px, max_cells, k, b.fast_bits ? max_planes : 0);
     b.corner_lut = ctx->d_lut;
     b.skip_max_tiles = skip_max_tiles;
+    b.skip_any = ctx->skip_on ? ctx->skipbuf.as<int32_t>(skip_off) : nullptr;
     b.skip_max_cells = skip_max_cells;
     uint32_t *sw = ctx->scratch.as<uint32_t>();
     b.slots = sw;

@@ -152,7 +152,7 @@ struct __align__(16) TileRec {
     int32_t eps_hi, eps_lo, W0, skip_c0, skip_cells_x;
     int32_t prj_bytes_x, prj_bytes_y;  // bulk copy sizes (multiples of 16)
     int32_t prj_off_x, prj_off_y;      // element offset of x0 / y0 in the staged copies
-    int32_t pad_;
+    int32_t image;                     // the tile's image
     const uint8_t *raw;
     const CUtensorMap *tmap;           // nullptr: the box is loaded with plain loads
     const uint16_t *prj_src_x, *prj_src_y;
@@ -196,6 +196,7 @@ struct Batch {
     uint32_t *err;
     Params prm;
     int32_t skip_max_tiles, skip_max_cells;  // learned cell-skip launch shape
+    int32_t *skip_any;              // learned skip: per image, nonzero once its proposal skipped a cell
     int32_t nms_kernel;             // 0: a warp per segment where segments allow, 1: a CTA per segment
     int32_t fast_ctas_per_sm;       // persistent detection CTAs per SM (0: as many as fit)
     Inputs in;

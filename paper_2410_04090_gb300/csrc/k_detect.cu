@@ -1169,6 +1169,10 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
         // before a barrier are not carried across it
         const int c = R.c, W = R.W, Hh = R.H, x0 = R.x0, y0 = R.y0, rowb = R.box_w;
         const int ncx = R.ncx, cells = ncx * R.ncy;
+        // learned skip: the image's proposal skipped at least one cell (an
+        // image with none takes the exact path: no per-cell flags, no extra
+        // barrier)
+        const bool tskip = R.skip != nullptr && __ldg(b.skip_any + R.image) != 0;
         if (!R.tmap) {
             // levels whose tiles cannot start on a word boundary: plain loads
             // (box rows of box_w bytes, delta = 0)
@@ -1191,12 +1195,12 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
             const int cx0 = (R.ccx0 + lcx) * c, cy0 = (R.ccy0 + lcy) * c;
             const bool evaluated = cx0 + c > border && cx0 < W - border && cy0 + c > border && cy0 < Hh - border;
             uint8_t st = evaluated ? 0 : 3;
-            if (R.skip && evaluated) {
+            if (tskip && evaluated) {
                 const int px = min(cx0 + c / 2, W - 1), py = min(cy0 + c / 2, Hh - 1);
                 const int X = prj[R.prj_off_x + px - x0], Y = prj[kPrjBytes / 2 + R.prj_off_y + py - y0];
                 st = R.skip[(Y / R.skip_c0) * R.skip_cells_x + X / R.skip_c0] ? 2 : 0;
             }
-            if (R.skip && st != 0) { st = 2; ++my_skipped; }
+            if (tskip && st != 0) { st = 2; ++my_skipped; }
             my_open += st == 0;
             has_hi[i] = st;
         }
@@ -1205,8 +1209,8 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
         if (my_open) atomicAdd(&C[2], my_open);
         // a box loaded with plain loads, the cell states and, in skip mode,
         // the skipped count are complete before the planes
-        if (!R.tmap || R.skip) __syncthreads();
-        all_skipped = R.skip && C[1] == cells;
+        if (!R.tmap || tskip) __syncthreads();
+        all_skipped = tskip && C[1] == cells;
 
         // bit-planes of the box rows [r0, r1 + 6) that the evaluated rows
         // [r0, r1) read, chunks 0..nch (an item of chunk m reads m and m + 1),
@@ -1230,7 +1234,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
             // cells skipped by the proposal: pass 0 runs over the items that
             // hold a pixel of a cell that is not (states are complete: skip
             // mode has a barrier after them)
-            if (R.skip && C[1] > 0) {
+            if (tskip && C[1] > 0) {
                 const int plo = max(border - x0, 0), phi = min(W - border - x0, R.tw);
                 list_items(wlist, &s_nlist[0], max(r1 - r0, 0) * nch, nch, (65536u + nch - 1) / nch, r0, plo, phi,
                            has_hi, ncx, R.tw, c, (uint32_t)R.cinv, lane, warp,

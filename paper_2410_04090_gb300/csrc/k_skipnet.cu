@@ -386,6 +386,7 @@ __global__ void k_skipcells(Batch b, float thresh)
     for (int y = y0; y < y1; ++y)
         for (int x = x0; x < x1; ++x) best = fmaxf(best, I.skip_logits[(size_t)y * I.skip_w8 + x]);
     I.skip[cell] = best < thresh ? 1 : 0;
+    if (best < thresh) atomicOr(b.skip_any + img, 1);  // zeroed before the launch
 }
 
 int skipnet_smem_bytes() { return kSkipSmem; }
@@ -397,6 +398,7 @@ cudaError_t launch_skipnet(const Batch &b, const SkipModelDev &m, float thresh, 
     k_skipnet<<<grid, kSkipThreads, kSkipSmem, stream>>>(b, m);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.skip_any, 0, sizeof(int32_t) * (size_t)b.n_images, stream)) != cudaSuccess) return e;
     dim3 g2((b.skip_max_cells + 255) / 256, b.n_images);
     k_skipcells<<<g2, 256, 0, stream>>>(b, thresh);
     return cudaGetLastError();
