@@ -1068,6 +1068,7 @@ __device__ __forceinline__ void drain_bits(const Batch &b, uint64_t *bars, int t
 // for the top-k rounds); a barrier ends each pass and one the tile.  The
 // counters of a tile live in one of two sets by tile parity, so the set of
 // the next tile is cleared while the current one is in use.
+template <bool kArc>  // the corner response: the arc's (opt-in reading) or the whole ring's SAD
 __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -1335,7 +1336,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
                         const int e = wbuf[i];
                         const int cy_ = e >> 7, cx_ = e & 127;
                         const uint8_t *pp = tbytes + (cy_ + 3) * rowb + (cx_ + 4);
-                        const int r = b.prm.resp_arc ? ring_arc(pp, rowb, eps, b.prm.p_min, b.prm.p_max)
+                        const int r = kArc ? ring_arc(pp, rowb, eps, b.prm.p_min, b.prm.p_max)
                                                      : ring_sad(pp, rowb);
                         const int ccy = div_small(cy_, cinv), ccx = div_small(cx_, cinv);
                         const uint32_t inidx = (uint32_t)((cy_ - ccy * c) * c + (cx_ - ccx * c));
@@ -1390,43 +1391,55 @@ int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, int max_plane
                           : fast_layout(max_box, max_px, max_cells, k).total;
 }
 
+// The detection kernel of a batch: the bit-sliced test for the default run
+// bounds (with the whole ring's or, opt-in, the arc's response), else the
+// per-pixel test.
+static const void *detect_kernel_of(const Batch &b)
+{
+    if (!b.fast_bits) return reinterpret_cast<const void *>(k_fast_cull);
+    return b.prm.resp_arc ? reinterpret_cast<const void *>(k_fast_bits<true>)
+                          : reinterpret_cast<const void *>(k_fast_bits<false>);
+}
+
 cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream)
 {
     if (b.fast_tiles == 0) return cudaSuccess;
-    static int cached_smem = -1, cached_blocks = 0, n_sm = 0, cached_bits = -1;
+    static int cached_smem = -1, cached_blocks = 0, n_sm = 0;
+    static const void *cached_fn = nullptr;
     cudaError_t e;
     if (n_sm == 0) {
         int dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     }
-    if (cached_smem != b.fast_smem || cached_bits != b.fast_bits) {
-        e = b.fast_bits ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, k_fast_bits, kFastThreads,
-                                                                         b.fast_smem)
-                        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, k_fast_cull, kFastThreads,
-                                                                         b.fast_smem);
-        if (e != cudaSuccess) return e;
+    const void *fn = detect_kernel_of(b);
+    if (cached_smem != b.fast_smem || cached_fn != fn) {
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cached_blocks, fn, kFastThreads, b.fast_smem)) !=
+            cudaSuccess)
+            return e;
         cached_smem = b.fast_smem;
-        cached_bits = b.fast_bits;
+        cached_fn = fn;
     }
     int per_sm = std::max(1, cached_blocks);
     if (b.fast_ctas_per_sm > 0) per_sm = std::min(per_sm, b.fast_ctas_per_sm);
     const int grid = std::min(b.fast_tiles, per_sm * n_sm);
-    if (b.fast_bits) k_fast_bits<<<grid, kFastThreads, b.fast_smem, stream>>>(b);
-    else k_fast_cull<<<grid, kFastThreads, b.fast_smem, stream>>>(b);
+    if (!b.fast_bits) k_fast_cull<<<grid, kFastThreads, b.fast_smem, stream>>>(b);
+    else if (b.prm.resp_arc) k_fast_bits<true><<<grid, kFastThreads, b.fast_smem, stream>>>(b);
+    else k_fast_bits<false><<<grid, kFastThreads, b.fast_smem, stream>>>(b);
     return cudaGetLastError();
 }
 
 // Detection CTAs of this batch's launch that fit on one SM at once.
 cudaError_t detect_ctas_that_fit(const Batch &b, int *per_sm)
 {
-    return b.fast_bits ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_fast_bits, kFastThreads, b.fast_smem)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_fast_cull, kFastThreads, b.fast_smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, detect_kernel_of(b), kFastThreads, b.fast_smem);
 }
 
 cudaError_t configure_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fast_bits, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_fast_bits<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fast_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_fast_cull, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
