@@ -1068,7 +1068,10 @@ __device__ __forceinline__ void drain_bits(const Batch &b, uint64_t *bars, int t
 // for the top-k rounds); a barrier ends each pass and one the tile.  The
 // counters of a tile live in one of two sets by tile parity, so the set of
 // the next tile is cleared while the current one is in use.
-template <bool kArc>  // the corner response: the arc's (opt-in reading) or the whole ring's SAD
+// Compile-time variants: kArc, the corner response (the arc's, an opt-in
+// reading, or the whole ring's SAD); kSkip, the learned cell-skip mode;
+// kTop1, one keypoint per cell (k = 1, the default) or the top-k rounds.
+template <bool kArc, bool kSkip, bool kTop1>
 __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -1082,7 +1085,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
     __shared__ __align__(16) TileRec recs[3];
     __shared__ __align__(16) uint8_t s_prj[2][2 * kPrjBytes];  // per box: x range, y range
     __shared__ __align__(8) uint64_t bars[5];                   // [0..1] boxes, [2..4] records
-    const int k = b.prm.k, border = b.prm.border;
+    const int k = kTop1 ? 1 : b.prm.k, border = b.prm.border;
     const BitsLayout lay = bits_layout(b.fast_max_box, b.fast_max_px, b.fast_max_cells, k, b.fast_max_planes);
     uint8_t *const buf0 = smem + lay.buf0, *const buf1 = smem + lay.buf1;
     uint32_t *planes = reinterpret_cast<uint32_t *>(smem + lay.planes);
@@ -1173,7 +1176,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
         // learned skip: the image's proposal skipped at least one cell (an
         // image with none takes the exact path: no per-cell flags, no extra
         // barrier)
-        const bool tskip = R.skip != nullptr && __ldg(b.skip_any + R.image) != 0;
+        const bool tskip = kSkip && R.skip != nullptr && __ldg(b.skip_any + R.image) != 0;
         if (!R.tmap) {
             // levels whose tiles cannot start on a word boundary: plain loads
             // (box rows of box_w bytes, delta = 0)
@@ -1391,14 +1394,26 @@ int fast_smem_bytes(int max_box, int max_px, int max_cells, int k, int max_plane
                           : fast_layout(max_box, max_px, max_cells, k).total;
 }
 
+// The bit-sliced detection kernel for a batch's response kind, skip mode and
+// keypoints per cell (index kArc * 4 + kSkip * 2 + kTop1).
+static const void *const kFastBitsVariants[8] = {
+    reinterpret_cast<const void *>(k_fast_bits<false, false, false>),
+    reinterpret_cast<const void *>(k_fast_bits<false, false, true>),
+    reinterpret_cast<const void *>(k_fast_bits<false, true, false>),
+    reinterpret_cast<const void *>(k_fast_bits<false, true, true>),
+    reinterpret_cast<const void *>(k_fast_bits<true, false, false>),
+    reinterpret_cast<const void *>(k_fast_bits<true, false, true>),
+    reinterpret_cast<const void *>(k_fast_bits<true, true, false>),
+    reinterpret_cast<const void *>(k_fast_bits<true, true, true>),
+};
+
 // The detection kernel of a batch: the bit-sliced test for the default run
-// bounds (with the whole ring's or, opt-in, the arc's response), else the
+// bounds (in the variant of its response, skip mode and k), else the
 // per-pixel test.
 static const void *detect_kernel_of(const Batch &b)
 {
     if (!b.fast_bits) return reinterpret_cast<const void *>(k_fast_cull);
-    return b.prm.resp_arc ? reinterpret_cast<const void *>(k_fast_bits<true>)
-                          : reinterpret_cast<const void *>(k_fast_bits<false>);
+    return kFastBitsVariants[(b.prm.resp_arc ? 4 : 0) + (b.skip_any ? 2 : 0) + (b.prm.k == 1 ? 1 : 0)];
 }
 
 cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream)
@@ -1423,10 +1438,8 @@ cudaError_t launch_fast_cull(const Batch &b, cudaStream_t stream)
     int per_sm = std::max(1, cached_blocks);
     if (b.fast_ctas_per_sm > 0) per_sm = std::min(per_sm, b.fast_ctas_per_sm);
     const int grid = std::min(b.fast_tiles, per_sm * n_sm);
-    if (!b.fast_bits) k_fast_cull<<<grid, kFastThreads, b.fast_smem, stream>>>(b);
-    else if (b.prm.resp_arc) k_fast_bits<true><<<grid, kFastThreads, b.fast_smem, stream>>>(b);
-    else k_fast_bits<false><<<grid, kFastThreads, b.fast_smem, stream>>>(b);
-    return cudaGetLastError();
+    void *args[] = { const_cast<Batch *>(&b) };
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kFastThreads), args, (size_t)b.fast_smem, stream);
 }
 
 // Detection CTAs of this batch's launch that fit on one SM at once.
@@ -1437,9 +1450,9 @@ cudaError_t detect_ctas_that_fit(const Batch &b, int *per_sm)
 
 cudaError_t configure_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_fast_bits<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fast_bits<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < 8 && e == cudaSuccess; ++v)
+        e = cudaFuncSetAttribute(kFastBitsVariants[v], cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_fast_cull, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
