@@ -1254,7 +1254,7 @@ __global__ void __launch_bounds__(kFastThreads, 3) k_fast_bits(Batch b)
             }
             return;
         }
-        const bool some_skipped = C[1] > 0;
+        const bool some_skipped = kSkip && C[1] > 0;  // constant false outside skip mode
 
         {
         const int c = R.c, W = R.W, Hh = R.H, x0 = R.x0, y0 = R.y0, tw = R.tw, rowb = R.box_w, ncx = R.ncx;
