@@ -28,10 +28,21 @@
 namespace jslam {
 
 __constant__ int32_t c_blur_w[7];
+// The same weights as bytes for the 2-way dot products of the horizontal
+// pass: {0, w0, w1, w2}, {w3, w4, w5, w6}, {w0, w1, w2, w3}, {w4, w5, w6, 0}
+// (byte 0 first; every weight is below 256).
+__constant__ uint32_t c_blur_pk[4];
 
 cudaError_t set_blur_weights(const int32_t w[7])
 {
-    return cudaMemcpyToSymbol(c_blur_w, w, sizeof(int32_t) * 7);
+    cudaError_t e = cudaMemcpyToSymbol(c_blur_w, w, sizeof(int32_t) * 7);
+    if (e != cudaSuccess) return e;
+    const auto B = [](int b0, int b1, int b2, int b3) {
+        return (uint32_t)b0 | ((uint32_t)b1 << 8) | ((uint32_t)b2 << 16) | ((uint32_t)b3 << 24);
+    };
+    const uint32_t pk[4] = { B(0, w[0], w[1], w[2]), B(w[3], w[4], w[5], w[6]), B(w[0], w[1], w[2], w[3]),
+                             B(w[4], w[5], w[6], 0) };
+    return cudaMemcpyToSymbol(c_blur_pk, pk, sizeof(pk));
 }
 
 // ---------------------------------------------------------------- pyramid
@@ -207,39 +218,32 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
     }
     __syncthreads();
     // horizontal 7-tap on the column sums: a thread owns a row and a run of
-    // 4 quads (16 output pixels) and slides along it
+    // 4 quads (16 output pixels).  The 16-bit sums sit two to a word (word i:
+    // columns 2i, 2i + 1 of the run), so each output is four 2-way byte dot
+    // products over aligned words, with the weights packed for its parity
+    // (the same integer sum as the 7 products; one rounding at the end).
     {
         constexpr int kQuadRun = 4, kRunsPerRow = (kPyrTW / 4) / kQuadRun;
         static_assert(kPyrTH * kRunsPerRow == kPyrThreads, "one run per thread");
         const int r = threadIdx.x / kRunsPerRow, q0 = (threadIdx.x % kRunsPerRow) * kQuadRun;
         const int gy = y0 + r;
         const uint32_t *src = reinterpret_cast<const uint32_t *>(&V[r][4 * q0]);
-        uint32_t v[12];
+        const uint32_t A = c_blur_pk[0], Bw = c_blur_pk[1], Cw = c_blur_pk[2], Dw = c_blur_pk[3];
+        uint32_t u[2 * kQuadRun + 4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const uint32_t p = src[j];
-            v[2 * j] = p & 0xFFFFu;
-            v[2 * j + 1] = p >> 16;
-        }
+        for (int j = 0; j < 2 * kQuadRun + 4; ++j) u[j] = src[j];
 #pragma unroll
         for (int k = 0; k < kQuadRun; ++k) {
-            // v[0..7] hold columns 4 (q0 + k) .. + 7; fetch the next 4
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const uint32_t p = src[2 * k + 4 + j];
-                v[8 + 2 * j] = p & 0xFFFFu;
-                v[9 + 2 * j] = p >> 16;
-            }
-            uint32_t out = 0;
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const uint32_t sm = blur7_sym(v[m + 1], v[m + 2], v[m + 3], v[m + 4], v[m + 5], v[m + 6], v[m + 7]);
-                out |= ((sm + 32768u) >> 16) << (8 * m);
-            }
+            // output m of the quad reads columns 4 k + m + 1 .. 4 k + m + 7
+            const uint32_t *w = u + 2 * k;
+            const uint32_t s0 = __dp2a_hi(w[3], Bw, __dp2a_lo(w[2], Bw, __dp2a_hi(w[1], A, __dp2a_lo(w[0], A, 0u))));
+            const uint32_t s1 = __dp2a_hi(w[4], Dw, __dp2a_lo(w[3], Dw, __dp2a_hi(w[2], Cw, __dp2a_lo(w[1], Cw, 0u))));
+            const uint32_t s2 = __dp2a_hi(w[4], Bw, __dp2a_lo(w[3], Bw, __dp2a_hi(w[2], A, __dp2a_lo(w[1], A, 0u))));
+            const uint32_t s3 = __dp2a_hi(w[5], Dw, __dp2a_lo(w[4], Dw, __dp2a_hi(w[3], Cw, __dp2a_lo(w[2], Cw, 0u))));
+            const uint32_t out = ((s0 + 32768u) >> 16) | (((s1 + 32768u) >> 16) << 8) |
+                                 (((s2 + 32768u) >> 16) << 16) | (((s3 + 32768u) >> 16) << 24);
             const int gx = x0 + 4 * (q0 + k);
             if (gy < H && gx < W) *reinterpret_cast<uint32_t *>(L.blur + (size_t)gy * L.blur_pitch + gx) = out;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = v[j + 4];
         }
     }
 }
