@@ -168,11 +168,13 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
             const uint32_t w = wb[r], w0 = 256u - w;
             const uint2 ha = *reinterpret_cast<const uint2 *>(&Hs[ia[r]][4 * q]);
             const uint2 hb = *reinterpret_cast<const uint2 *>(&Hs[ib[r]][4 * q]);
-            const uint32_t v0 = (w0 * (ha.x & 0xFFFFu) + w * (hb.x & 0xFFFFu) + 32768u) >> 16;
-            const uint32_t v1 = (w0 * (ha.x >> 16) + w * (hb.x >> 16) + 32768u) >> 16;
-            const uint32_t v2 = (w0 * (ha.y & 0xFFFFu) + w * (hb.y & 0xFFFFu) + 32768u) >> 16;
-            const uint32_t v3 = (w0 * (ha.y >> 16) + w * (hb.y >> 16) + 32768u) >> 16;
-            *reinterpret_cast<uint32_t *>(&raw[r][4 * q]) = v0 | (v1 << 8) | (v2 << 16) | (v3 << 24);
+            // rounded sums below 2^24: the result is byte 2 of each, packed by byte permutes
+            const uint32_t v0 = w0 * (ha.x & 0xFFFFu) + w * (hb.x & 0xFFFFu) + 32768u;
+            const uint32_t v1 = w0 * (ha.x >> 16) + w * (hb.x >> 16) + 32768u;
+            const uint32_t v2 = w0 * (ha.y & 0xFFFFu) + w * (hb.y & 0xFFFFu) + 32768u;
+            const uint32_t v3 = w0 * (ha.y >> 16) + w * (hb.y >> 16) + 32768u;
+            *reinterpret_cast<uint32_t *>(&raw[r][4 * q]) =
+                __byte_perm(__byte_perm(v0, v1, 0x0062), __byte_perm(v2, v3, 0x0062), 0x5410);
         }
     }
     __syncthreads();
@@ -236,12 +238,15 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
         for (int k = 0; k < kQuadRun; ++k) {
             // output m of the quad reads columns 4 k + m + 1 .. 4 k + m + 7
             const uint32_t *w = u + 2 * k;
-            const uint32_t s0 = __dp2a_hi(w[3], Bw, __dp2a_lo(w[2], Bw, __dp2a_hi(w[1], A, __dp2a_lo(w[0], A, 0u))));
-            const uint32_t s1 = __dp2a_hi(w[4], Dw, __dp2a_lo(w[3], Dw, __dp2a_hi(w[2], Cw, __dp2a_lo(w[1], Cw, 0u))));
-            const uint32_t s2 = __dp2a_hi(w[4], Bw, __dp2a_lo(w[3], Bw, __dp2a_hi(w[2], A, __dp2a_lo(w[1], A, 0u))));
-            const uint32_t s3 = __dp2a_hi(w[5], Dw, __dp2a_lo(w[4], Dw, __dp2a_hi(w[3], Cw, __dp2a_lo(w[2], Cw, 0u))));
-            const uint32_t out = ((s0 + 32768u) >> 16) | (((s1 + 32768u) >> 16) << 8) |
-                                 (((s2 + 32768u) >> 16) << 16) | (((s3 + 32768u) >> 16) << 24);
+            // words i .. i + 3 against the weight words P (first two) and Q (last
+            // two); the rounding term starts each sum, the sums stay below 2^24,
+            // so each result is byte 2 of its sum, packed by byte permutes
+            const auto dot7 = [&](int i, uint32_t P, uint32_t Q) {
+                const uint32_t lo = __dp2a_hi(w[i + 1], P, __dp2a_lo(w[i], P, 32768u));
+                return __dp2a_hi(w[i + 3], Q, __dp2a_lo(w[i + 2], Q, lo));
+            };
+            const uint32_t s0 = dot7(0, A, Bw), s1 = dot7(1, Cw, Dw), s2 = dot7(1, A, Bw), s3 = dot7(2, Cw, Dw);
+            const uint32_t out = __byte_perm(__byte_perm(s0, s1, 0x0062), __byte_perm(s2, s3, 0x0062), 0x5410);
             const int gx = x0 + 4 * (q0 + k);
             if (gy < H && gx < W) *reinterpret_cast<uint32_t *>(L.blur + (size_t)gy * L.blur_pitch + gx) = out;
         }
