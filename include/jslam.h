@@ -56,7 +56,9 @@ typedef struct jslam_ctx jslam_ctx;
 /* Where the bytes of a jslam_image live. */
 enum { JSLAM_MEM_DEVICE = 0, JSLAM_MEM_HOST = 1 };
 
-/* One 8-bit grayscale image, row-major with `pitch` bytes between rows.
+/* One 8-bit grayscale image, row-major with `pitch` bytes between rows
+ * (pitch >= width, and pitch x height below 4 GiB: the kernels address an
+ * image with 32-bit offsets; larger spans are refused with JSLAM_ERR_ARG).
  * memory == JSLAM_MEM_DEVICE: `data` is device memory of the context's
  *   device and is read in place.
  * memory == JSLAM_MEM_HOST: `data` is host memory (pinned memory makes the

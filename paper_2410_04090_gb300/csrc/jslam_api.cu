@@ -265,6 +265,7 @@ bool image_ok(const jslam_image &im, const jslam_config &cfg)
 {
     if (!im.data || im.width < 1 || im.height < 1) return false;
     if (im.pitch < im.width) return false;
+    if ((int64_t)im.pitch * im.height > (int64_t)UINT32_MAX) return false;  // kernels take 32-bit offsets
     if (im.width > cfg.max_width || im.height > cfg.max_height) return false;
     if (im.memory != JSLAM_MEM_DEVICE && im.memory != JSLAM_MEM_HOST) return false;
     return true;

@@ -154,10 +154,12 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyramid(Batch b)
                 wa[k] = 256u - wbx[k];
             }
             for (int j = slot; j < ns; j += kRowSlots) {
-                const uint8_t *row = L0 + (size_t)src_row[j] * pitch0;
+                // 32-bit offsets from the image's base (images are below 4 GB)
+                const uint32_t ro = (uint32_t)src_row[j] * (uint32_t)pitch0;
                 uint32_t h[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) h[k] = wa[k] * __ldg(row + xa[k]) + wbx[k] * __ldg(row + xb[k]);
+                for (int k = 0; k < 4; ++k)
+                    h[k] = wa[k] * __ldg(L0 + (ro + (uint32_t)xa[k])) + wbx[k] * __ldg(L0 + (ro + (uint32_t)xb[k]));
                 *reinterpret_cast<uint2 *>(&Hs[j][4 * q]) = make_uint2(h[0] | (h[1] << 16), h[2] | (h[3] << 16));
             }
         }
