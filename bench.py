@@ -734,7 +734,7 @@ def main():
 
     e2e = None
     if not args.only_batched:
-        e2e = run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, stream)
+        e2e = run_e2e(args, pairs, params, jslam, torch, dist, dev, pairs_done, dims, tuning)
     if rank == 0:
         emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks,
              tuning, skip_quality, dev.index, refine, track, fc_abl, br_rep, tune_source)
@@ -747,13 +747,22 @@ def main():
         dist.destroy_process_group()
 
 
-def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, stream):
+E2E_ROUTES = (("graph_parts4", 4, True), ("graph", 1, True), ("extract", 1, False))
+
+
+def run_e2e(args, pairs, params, jslam, torch, dist, dev, pairs_done, dims, tuning):
     """End to end through the C ABI: every step uploads that step's frames
     from pinned host memory (one buffer holding all frames back to back, so
-    the library moves them with one copy), extracts, matches and downloads
-    all result blocks (one ranged copy).  Two contexts on two streams take
-    alternate steps, so one step's copies overlap the other's kernels; the
-    single-context figure (no overlap) is reported beside it."""
+    the library moves each part's frames with one copy), extracts, matches
+    and downloads the result blocks (one ranged copy per part), timed by the
+    wall clock.  Routes: `extract` calls jslam_extract_batch + jslam_match
+    per step; `graph` replays a graph captured on the host frames (the
+    upload copy is a node of the graph, so every replay copies the frames
+    again); `graph_parts4` splits the step's pairs over four such graphs on
+    four streams.  Each route has two sets of contexts that take alternate
+    steps, so one step's copies overlap the other's kernels; the headline
+    is the first route, the others and a single-context figure (the
+    extract route, one set, no overlap) ride along."""
     n = len(pairs)
     sizes = [(f.left.shape, f.right.shape) for f in pairs]
     total = sum(a[0] * a[1] + b[0] * b[1] for a, b in sizes)
@@ -768,45 +777,72 @@ def run_e2e(args, fe, pairs, params, jslam, torch, dist, dev, pairs_done, dims, 
             pv.append(v)
             off += img.size
         views.append(pv)
-    stream2 = torch.cuda.Stream(device=dev)
-    fe2 = jslam.Frontend(device=dev.index, stream=stream2, **dims)
-    ctxs = [fe, fe2]
-    hjobs = [c.prepare_batch([jslam.Job(v[0], v[1], **p) for v, p in zip(views, params)]) for c in ctxs]
-    outs = []
-    for c, hj in zip(ctxs, hjobs):
-        c.extract_batch(hj); c.match(); c.sync()
-        nb, _ = c.result_range(0, n)
-        outs.append(torch.empty(nb, dtype=torch.uint8).pin_memory())
 
-    def step(k):
-        c = ctxs[k]
-        c.extract_batch(hjobs[k])
-        c.match()
-        c.download_range(0, n, outs[k])
+    def make_route(parts, use_graph, sets=2):
+        bounds = [round(i * n / parts) for i in range(parts + 1)]
+        groups = []
+        for _ in range(sets):
+            g = []
+            for i in range(parts):
+                sl = slice(bounds[i], bounds[i + 1])
+                if sl.start == sl.stop:
+                    continue
+                c = jslam.Frontend(device=dev.index, stream=torch.cuda.Stream(device=dev),
+                                   **dict(dims, max_pairs=sl.stop - sl.start))
+                c.set_tuning(*tuning)
+                hj = c.prepare_batch([jslam.Job(v[0], v[1], **p) for v, p in zip(views[sl], params[sl])])
+                if use_graph:
+                    c.graph_capture(hj)
+                else:
+                    c.extract_batch(hj); c.match()
+                c.sync()
+                nb, _ = c.result_range(0, sl.stop - sl.start)
+                g.append((c, hj, sl.stop - sl.start, torch.empty(nb, dtype=torch.uint8).pin_memory()))
+            groups.append(g)
 
-    def run(steps, contexts):
-        for i in range(steps):
-            step(i % contexts)
-        for c in ctxs[:contexts]:
-            c.sync()
+        def step(k):
+            for c, hj, m, out in groups[k % len(groups)]:
+                if use_graph:
+                    c.graph_launch()
+                else:
+                    c.extract_batch(hj); c.match()
+                c.download_range(0, m, out)
 
-    run(args.warmup, 2)
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    run(args.steps, 2)
-    e2e_s = time.perf_counter() - t0
-    t1 = time.perf_counter()
-    run(args.steps, 1)
-    serial_s = time.perf_counter() - t1
-    e2e_s, serial_s = max_over_ranks(dist, [e2e_s, serial_s], dev)
-    nb, _ = fe.result_range(0, n)
-    fe2.close()
-    return {"value": pairs_done / e2e_s, "unit": UNIT,
-            "h2d_bytes_per_step": total, "d2h_bytes_per_step": nb,
-            "how": "C ABI, pinned host frames (one buffer per step, one upload copy), one ranged result "
-                   "download per step, 2 contexts on 2 streams alternating steps; wall clock",
-            "single_context_value": pairs_done / serial_s}
+        def run(steps):
+            for i in range(steps):
+                step(i)
+            for g in groups:
+                for c, _, _, _ in g:
+                    c.sync()
+        return run, sum(out.numel() for _, _, _, out in groups[0]), [c for g in groups for c, _, _, _ in g]
+
+    def timed(route):
+        run, d2h, ctxs = route
+        d2h_bytes.append(d2h)
+        run(args.warmup)
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        run(args.steps)
+        dt = time.perf_counter() - t0
+        for c in ctxs:  # one route's contexts at a time on the device
+            c.close()
+        return dt
+
+    d2h_bytes = []
+    secs = {name: timed(make_route(parts, use_graph)) for name, parts, use_graph in E2E_ROUTES}
+    secs["single_context"] = timed(make_route(1, False, sets=1))
+    names = list(secs)
+    secs = dict(zip(names, max_over_ranks(dist, [secs[k] for k in names], dev)))
+    head = E2E_ROUTES[0][0]
+    res = {"value": pairs_done / secs[head], "unit": UNIT, "h2d_bytes_per_step": total,
+           "d2h_bytes_per_step": d2h_bytes[0],
+           "how": f"C ABI, pinned host frames, route {head}: the step's pairs in four parts, each part one replay "
+                  "of a graph captured on its host frames (one upload copy inside the graph) on its own stream, "
+                  "then one ranged result download per part; two sets of contexts take alternate steps; "
+                  "wall clock",
+           "routes": {k: pairs_done / v for k, v in secs.items()}}
+    return res
 
 
 def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs, params, lo, e2e, clocks, tuning,

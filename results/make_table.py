@@ -25,9 +25,17 @@ def fmt(v, nd=0):
     return "—" if v is None else f"{v:,.{nd}f}".replace(",", " ")
 
 
+def e2e_cell(e):
+    r = e.get("routes")
+    if not r:  # a line from before the graph routes: the extract route and one context
+        return f"— / — / {fmt(e.get('value'))} ({fmt(e.get('single_context_value'))})"
+    return (f"{fmt(r.get('graph_parts4'))} / {fmt(r.get('graph'))} / {fmt(r.get('extract'))} "
+            f"({fmt(r.get('single_context'))})")
+
+
 def main():
     rows = load()
-    print("| Workload (pairs per step) | " + " | ".join(MODES) + " | e2e, 2 ctx (1 ctx) | CPU oracle, cores (1 core) |")
+    print("| Workload (pairs per step) | " + " | ".join(MODES) + " | e2e: graph_parts4 / graph / extract (1 ctx) | CPU oracle, cores (1 core) |")
     print("|---" * (len(MODES) + 3) + "|")
     for w, d in rows:
         m = d["modes"]
@@ -35,7 +43,7 @@ def main():
         c = d.get("cpu_baseline") or {}
         one = (c.get("single_core") or {}).get("value")
         print(f"| {w} ({d['config']['pairs_per_step']}) | " + " | ".join(fmt(m.get(k)) for k in MODES) +
-              f" | {fmt(e.get('value'))} ({fmt(e.get('single_context_value'))}) | "
+              f" | {e2e_cell(e)} | "
               f"{fmt(c.get('value'), 2)}, {c.get('cores', '—')} ({fmt(one, 2)}) |")
     print()
     print("| Workload | path HBM: " + " | ".join(MODES) + " | detect ms | detect roofline | clocks MHz |")

@@ -563,6 +563,53 @@ def test_graph_replay_follows_new_frames(J, oracle):
     fe.close()
 
 
+def test_graph_replay_copies_host_frames(J, oracle):
+    """A graph captured on pinned host frames that lie back to back in one
+    buffer (so their upload is one copy, a node of the graph) copies them
+    again on every replay: new frames written into the same host buffer
+    between replays give the new frames' keypoints and matches, and the
+    ranged download enqueued after each replay holds them too."""
+    import torch
+    specs = scenes.MIXED_STREAMS[::4]  # one stream of each size
+    n = len(specs)
+    fe = frontend_for(J, params_from(oracle, fast_thresh_lo=7), max_pairs=4, stream=torch.cuda.Stream())
+    frames = {f: [scenes.stereo_pair(sp["kind"], sp["width"], sp["height"], frame=f, stream=i, config_id=4)
+                  for i, sp in enumerate(specs)] for f in (0, 1, 2)}
+    total = sum(2 * sp["width"] * sp["height"] for sp in specs)
+    flat = torch.empty(total, dtype=torch.uint8).pin_memory()
+    buf, views, off = flat.numpy(), [], 0
+    for sp in specs:
+        pv = []
+        for _ in range(2):
+            pv.append(buf[off: off + sp["width"] * sp["height"]].reshape(sp["height"], sp["width"]))
+            off += sp["width"] * sp["height"]
+        views.append(pv)
+
+    def fill(pairs):
+        for (vl, vr), pr in zip(views, pairs):
+            vl[...] = pr.left
+            vr[...] = pr.right
+
+    fill(frames[0])
+    jobs = [J.Job(vl, vr, sp["levels"], 1.2, 20, 32, sp["max_feats"]) for (vl, vr), sp in zip(views, specs)]
+    fe.graph_capture(jobs)
+    fe.sync()
+    total_b, offs = fe.result_range(0, n)
+    for f in (1, 2):
+        fill(frames[f])
+        fe.graph_launch()
+        block = torch.empty(total_b, dtype=torch.uint8).pin_memory()
+        fe.download_range(0, n, block)
+        fe.sync()
+        _check_batch(J, oracle, fe, frames[f], specs)
+        for i, (pr, sp) in enumerate(zip(frames[f], specs)):
+            p = params_from(oracle, levels=sp["levels"], max_feats=sp["max_feats"], fast_thresh_lo=7)
+            ol, orr, om = oracle.extract_pair(pr.left, pr.right, p)
+            blk = block[offs[i]:].clone()
+            compare_keypoints(fe.result_view(i, blk, 1), orr, f"frame {f} pair {i} right (downloaded)")
+    fe.close()
+
+
 def test_largest_batch_equals_pairs_alone(J, oracle):
     """The largest batch a context accepts (128 pairs, 256 images: the limit
     of the by-value input table) of pairs of nine sizes, depths 1..6, two
