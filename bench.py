@@ -8,11 +8,11 @@ KITTI-shaped sequence (1241x376 u8, 8 levels, scale 1.2, FAST 20 with
 fallback 7, 32x32 cells, 2000 features per image).
 
 Modes, each timed over the same steps:
-  graph_streams4  the step's pairs split over four contexts on four streams,
-                  each part captured once as a CUDA graph and replayed
-                  (fork/join by events) -- the headline
-  graph_streams2  the same with two parts
-  streams4/2      the same parts as plain batched calls
+  graph_streams8  the step's pairs split over eight contexts on eight
+                  streams, each part captured once as a CUDA graph and
+                  replayed (fork/join by events) -- the headline
+  graph_streams4/2  the same with four and two parts
+  streams8/4/2    the same parts as plain batched calls
   batched         all pairs of the step in one C-ABI call (one launch per stage)
   graph           the batched call captured once as a CUDA graph and replayed
   plain           one C-ABI call per stereo pair
@@ -21,9 +21,9 @@ Modes, each timed over the same steps:
   learned_skip    batched, with the learned cell-skip proposal (approximate;
                   its feature recall against the exact path is reported)
 Inputs are resident in HBM before the timed region; L2 is flushed (256 MB
-write) before every timed step.  `e2e` repeats the batched step through the
-C ABI with pinned host images and downloads every result block, copies
-inside the timed region.
+write) before every timed step.  `e2e` repeats the step through the C ABI
+with pinned host images and downloads every result block, copies inside
+the timed region.
 
 `roofline` is the dominant kernel's algorithmic bytes per launch over its
 CUDA-event time against the measured HBM copy bandwidth; its `alu` entry
@@ -94,8 +94,8 @@ def parse_args():
     ap.add_argument("--workload", default="kitti_1241x376_L8", choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--frames", type=int, default=100, help="pairs per step (sequence workloads)")
     ap.add_argument("--mode", choices=["batched", "graph", "plain", "plain_graph", "streams2", "graph_streams2", "streams4",
-                                       "graph_streams4"],
-                    default="graph_streams4", help="the headline mode (the others are timed beside it)")
+                                       "graph_streams4", "streams8", "graph_streams8"],
+                    default="graph_streams8", help="the headline mode (the others are timed beside it)")
     ap.add_argument("--cpu-pairs", type=int, default=12, help="pairs in the oracle CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tile", type=int, nargs=2, metavar=("W", "H"),
@@ -561,7 +561,7 @@ def main():
         return step_plain_split, step_graph_split
 
     if not args.only_batched:
-        for S in (2, 4):
+        for S in (2, 4, 8):
             if n >= S:
                 modes[f"streams{S}"], modes[f"graph_streams{S}"] = split_modes(S)
     if args.mode not in modes:
@@ -747,7 +747,7 @@ def main():
         dist.destroy_process_group()
 
 
-E2E_ROUTES = (("graph_parts4", 4, True), ("graph", 1, True), ("extract", 1, False))
+E2E_ROUTES = (("graph_parts4", 4, True), ("graph_parts8", 8, True), ("graph", 1, True), ("extract", 1, False))
 
 
 def run_e2e(args, pairs, params, jslam, torch, dist, dev, pairs_done, dims, tuning):
@@ -758,8 +758,8 @@ def run_e2e(args, pairs, params, jslam, torch, dist, dev, pairs_done, dims, tuni
     wall clock.  Routes: `extract` calls jslam_extract_batch + jslam_match
     per step; `graph` replays a graph captured on the host frames (the
     upload copy is a node of the graph, so every replay copies the frames
-    again); `graph_parts4` splits the step's pairs over four such graphs on
-    four streams.  Each route has two sets of contexts that take alternate
+    again); `graph_parts4` and `graph_parts8` split the step's pairs over
+    four and eight such graphs on their own streams.  Each route has two sets of contexts that take alternate
     steps, so one step's copies overlap the other's kernels; the headline
     is the first route, the others and a single-context figure (the
     extract route, one set, no overlap) ride along."""
@@ -897,7 +897,8 @@ def emit(args, world, n, value, total_ms, mode_values, stage_acc, counts, pairs,
                 "plain_graph": LAUNCHES_PER_CALL * n,
                 "learned_skip": LAUNCHES_PER_CALL + 2, "streams2": 2 * LAUNCHES_PER_CALL,
                 "graph_streams2": 2 * LAUNCHES_PER_CALL, "streams4": 4 * LAUNCHES_PER_CALL,
-                "graph_streams4": 4 * LAUNCHES_PER_CALL}
+                "graph_streams4": 4 * LAUNCHES_PER_CALL, "streams8": 8 * LAUNCHES_PER_CALL,
+                "graph_streams8": 8 * LAUNCHES_PER_CALL}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",

@@ -10,7 +10,7 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ORDER = ["single_640x480_L1", "kitti_1241x376_L8", "euroc_752x480_L8", "fhd_1920x1080_L8", "mixed16"]
-MODES = ["graph_streams4", "batched", "graph", "plain", "plain_graph", "learned_skip"]
+MODES = ["graph_streams8", "graph_streams4", "batched", "graph", "plain", "plain_graph", "learned_skip"]
 
 
 def load():
@@ -28,14 +28,14 @@ def fmt(v, nd=0):
 def e2e_cell(e):
     r = e.get("routes")
     if not r:  # a line from before the graph routes: the extract route and one context
-        return f"— / — / {fmt(e.get('value'))} ({fmt(e.get('single_context_value'))})"
-    return (f"{fmt(r.get('graph_parts4'))} / {fmt(r.get('graph'))} / {fmt(r.get('extract'))} "
-            f"({fmt(r.get('single_context'))})")
+        return f"— / — / — / {fmt(e.get('value'))} ({fmt(e.get('single_context_value'))})"
+    return (f"{fmt(r.get('graph_parts4'))} / {fmt(r.get('graph_parts8'))} / {fmt(r.get('graph'))} / "
+            f"{fmt(r.get('extract'))} ({fmt(r.get('single_context'))})")
 
 
 def main():
     rows = load()
-    print("| Workload (pairs per step) | " + " | ".join(MODES) + " | e2e: graph_parts4 / graph / extract (1 ctx) | CPU oracle, cores (1 core) |")
+    print("| Workload (pairs per step) | " + " | ".join(MODES) + " | e2e: graph_parts4 / graph_parts8 / graph / extract (1 ctx) | CPU oracle, cores (1 core) |")
     print("|---" * (len(MODES) + 3) + "|")
     for w, d in rows:
         m = d["modes"]

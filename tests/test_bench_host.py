@@ -73,14 +73,14 @@ def test_emitted_line_carries_the_contract(monkeypatch, capsys):
     import types
     import bench
     monkeypatch.setattr(bench, "alu_peak", lambda dev: (40.3e12, 152, 2070.0))
-    args = types.SimpleNamespace(steps=50, warmup=3, workload="kitti_1241x376_L8", mode="graph_streams4",
+    args = types.SimpleNamespace(steps=50, warmup=3, workload="kitti_1241x376_L8", mode="graph_streams8",
                                  no_cpu_baseline=True)
     pairs, params, lo = bench.make_workload(args.workload, 2)
     stage = {"pyramid": 0.774, "skip": 0.0, "detect": 0.865, "pfa_nms": 0.048, "pfa_final": 0.066, "orb": 0.259,
              "match": 0.172}
     clocks = types.SimpleNamespace(summary=lambda: {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []})
     e2e = {"value": 43000.0, "unit": bench.UNIT, "h2d_bytes_per_step": 1, "d2h_bytes_per_step": 1}
-    bench.emit(args, 1, len(pairs), 47800.0, 2.09 * 50, {"graph_streams4": 47800.0},
+    bench.emit(args, 1, len(pairs), 47800.0, 2.09 * 50, {"graph_streams8": 47800.0},
                {k: v * 50 for k, v in stage.items()}, [2000] * 4, pairs, params, lo, e2e, clocks, (128, 128, 0, 0, 0),
                None, 0)
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
@@ -89,7 +89,7 @@ def test_emitted_line_carries_the_contract(monkeypatch, capsys):
                 "gpu_launches"):
         assert key in line, key
     assert line["config"]["workload"].startswith("kitti_1241x376_L8")
-    assert line["gpu_launches"] == 4 * bench.LAUNCHES_PER_CALL * 50
+    assert line["gpu_launches"] == 8 * bench.LAUNCHES_PER_CALL * 50
     roof = line["roofline"]
     prof = bench.profile_summary("k_fast_bits", "kitti_1241x376_L8")
     assert prof is not None and roof["bound"] == "alu" and roof["kernel"] == "k_fast_bits"
@@ -100,7 +100,7 @@ def test_emitted_line_carries_the_contract(monkeypatch, capsys):
     assert roof["traffic"] == bench.profile_number(prof, "dram_bytes_per_launch_full_workload")
     assert roof["hbm"]["algorithmic_bytes_per_launch"] == bench.algorithmic_bytes("detect", pairs, params, [1])
     assert line["path_hbm"]["frac"] > 0 and line["cpu_baseline"] is None
-    assert line["path_hbm"]["by_mode"]["graph_streams4"]["frac"] == line["path_hbm"]["frac"]
+    assert line["path_hbm"]["by_mode"]["graph_streams8"]["frac"] == line["path_hbm"]["frac"]
     assert line["config"]["tuning"] == {"nms_kernel": 0, "detect_ctas_per_sm": 0, "tile_order": 0, "source": "--tile"}
 
 
@@ -118,7 +118,7 @@ def test_results_table_covers_every_config(capsys):
         assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT and d["n_gpus"] == 1
         assert d["value"] > 0 and d["clocks"]["sm_mhz"] and not set(d["clocks"]["reasons"]) & {
             "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
-        for m in ("graph_streams4", "batched", "plain", "learned_skip"):
+        for m in ("graph_streams8", "batched", "plain", "learned_skip"):
             assert d["modes"][m] > 0 and d["path_hbm"]["by_mode"][m]["frac"] > 0, (w, m)
     mt.main()
     out = capsys.readouterr().out

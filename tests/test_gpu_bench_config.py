@@ -1,7 +1,7 @@
 """Parity in the launch configuration the benchmark times: a 100-pair batch
-(KITTI-shaped, EuRoC-shaped, 1920x1080) split over four contexts on four
+(KITTI-shaped, EuRoC-shaped, 1920x1080) split over eight contexts on eight
 streams, each part replayed as a captured CUDA graph, 128x128 detection
-tiles.  Four sampled pairs (one per context) are compared with the oracle
+tiles.  Eight sampled pairs (one per context) are compared with the oracle
 bit for bit; all 100 pairs are checked against properties that hold at any
 size."""
 import numpy as np
@@ -13,8 +13,8 @@ from parity_util import compare_keypoints, compare_matches, params_from
 pytestmark = pytest.mark.gpu
 
 N = 100
-PARTS = 4
-SAMPLES = (0, 37, 62, 99)
+PARTS = 8
+SAMPLES = (0, 12, 25, 38, 50, 62, 75, 99)  # one per part (parts start at 0, 12, 25, 38, 50, 62, 75, 88)
 
 
 @pytest.fixture(scope="module")
