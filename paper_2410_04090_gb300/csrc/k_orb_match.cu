@@ -194,21 +194,22 @@ __global__ void __launch_bounds__(256, 8) k_match(Batch b)
             rz[q] = e > s ? __ldg(rf + vz) : s;
         }
     }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int a = ra[q], z = rz[q];
-        for (int j = a + lane; j < z; j += 32) {
-            const int disp = X - (int)orr.X[j];
-            if (disp < 0 || disp > b.prm.max_disp) continue;
-            const uint4 *dr = reinterpret_cast<const uint4 *>(orr.desc + (size_t)j * 8);
-            const uint4 r0 = dr[0], r1 = dr[1];
-            const int d = __popc(dl[0] ^ r0.x) + __popc(dl[1] ^ r0.y) + __popc(dl[2] ^ r0.z) +
-                          __popc(dl[3] ^ r0.w) + __popc(dl[4] ^ r1.x) + __popc(dl[5] ^ r1.y) +
-                          __popc(dl[6] ^ r1.z) + __popc(dl[7] ^ r1.w);
-            const unsigned long long key = ((unsigned long long)d << 48) |
-                                           ((unsigned long long)disp << 32) | (unsigned)j;
-            best = key < best ? key : best;
-        }
+    // the three bands as one run of candidates over the lanes (a band of a
+    // level outside the frame, or of an empty level, is empty), so a few
+    // dozen candidates take one pass of loads, not one per level
+    const int c0 = rz[0] - ra[0], c01 = c0 + (rz[1] - ra[1]), T = c01 + (rz[2] - ra[2]);
+    for (int t = lane; t < T; t += 32) {
+        const int j = t < c0 ? ra[0] + t : (t < c01 ? ra[1] + (t - c0) : ra[2] + (t - c01));
+        const int disp = X - (int)orr.X[j];
+        if (disp < 0 || disp > b.prm.max_disp) continue;
+        const uint4 *dr = reinterpret_cast<const uint4 *>(orr.desc + (size_t)j * 8);
+        const uint4 r0 = dr[0], r1 = dr[1];
+        const int d = __popc(dl[0] ^ r0.x) + __popc(dl[1] ^ r0.y) + __popc(dl[2] ^ r0.z) +
+                      __popc(dl[3] ^ r0.w) + __popc(dl[4] ^ r1.x) + __popc(dl[5] ^ r1.y) +
+                      __popc(dl[6] ^ r1.z) + __popc(dl[7] ^ r1.w);
+        const unsigned long long key = ((unsigned long long)d << 48) |
+                                       ((unsigned long long)disp << 32) | (unsigned)j;
+        best = key < best ? key : best;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
