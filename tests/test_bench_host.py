@@ -120,6 +120,12 @@ def test_results_table_covers_every_config(capsys):
             "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
         for m in ("graph_streams8", "batched", "plain", "learned_skip"):
             assert d["modes"][m] > 0 and d["path_hbm"]["by_mode"][m]["frac"] > 0, (w, m)
+        # the end-to-end line: every route timed, the headline is the first route's figure,
+        # and both directions' bytes are counted
+        e = d["e2e"]
+        assert set(e["routes"]) == {r[0] for r in bench.E2E_ROUTES} | {"single_context"}, w
+        assert e["value"] == e["routes"][bench.E2E_ROUTES[0][0]] and e["unit"] == bench.UNIT
+        assert e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     mt.main()
     out = capsys.readouterr().out
     assert all(f"| {w} " in out for w in mt.ORDER)
